@@ -1,0 +1,164 @@
+"""Algorithm 1 (standard BiCGStab) in float64 (test infrastructure only).
+
+The paper's iteration (Sec. III, Algorithm 1), with ``r0`` the fixed shadow
+residual:
+
+    s_i     = A p_i
+    alpha_i = (r0, r_i) / (r0, s_i)
+    q_i     = r_i - alpha_i s_i
+    y_i     = A q_i
+    omega_i = (q_i, y_i) / (y_i, y_i)
+    x_{i+1} = x_i + alpha_i p_i + omega_i q_i
+    r_{i+1} = q_i - omega_i y_i
+    beta_i  = (alpha_i / omega_i) (r0, r_{i+1}) / (r0, r_i)
+    p_{i+1} = r_{i+1} + beta_i (p_i - omega_i s_i)
+
+Readings where the paper is silent or garbled (each is listed in the
+project's design notes):
+
+* The x update is printed with ``x_i`` on both sides; it is read as
+  ``x_{i+1} = x_i + alpha_i p_i + omega_i q_i``.
+* The algorithm starts from ``r0 = b`` (i.e. ``x0 = 0``); for a general
+  ``x0`` the start is ``r_0 = b - A x0``, ``r0_hat = r_0``, ``p_0 = r_0``.
+* No stopping rule is printed.  A solve stops after the full step in which
+  the recurrence residual satisfies ``||r_{i+1}|| / ||b|| <= tol`` (2-norms),
+  or after ``maxit`` steps; ``hist[k] = ||r_k|| / ||b||``.  With ``b = 0``
+  the answer is ``x = 0`` after zero steps.  If ``hist[0] <= tol`` no step is
+  taken.
+* Breakdown (not discussed in the paper): ``(r0, s) = 0``, ``omega = 0``,
+  ``(r0, r_{i+1}) = 0`` before convergence, or any non-finite scalar stops
+  the solve with status BREAKDOWN.  If ``(y, y) = 0`` then ``q = 0``
+  exactly; the half step ``x += alpha p`` is taken and the solve ends as
+  converged if ``||q|| <= tol ||b||``.
+* With ``jacobi=True`` the iteration runs on the diagonally preconditioned
+  system ``D^-1 A x = D^-1 b`` (Sec. IV: the main diagonal is all ones and
+  only six diagonals are stored); ``tol`` and ``hist`` refer to that system.
+
+Status codes follow the library's: 0 converged, 3 breakdown, 4 not
+converged within ``maxit``.
+"""
+
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import stencil
+
+OK, BREAKDOWN, NOTCONV = 0, 3, 4
+
+
+@dataclass
+class Result:
+    x: np.ndarray
+    iters: int
+    hist: np.ndarray          # hist[0..iters]
+    status: int
+    true_resid: float         # ||b~ - A~ x|| / ||b~|| on the solved system
+    true_resid_orig: float    # ||b - A x|| / ||b|| on the raw system
+
+
+def _dot(a, b):
+    return float(np.dot(a, b))
+
+
+def bicgstab(nx, ny, nz, coef, b, x0=None, tol=1e-8, maxit=500,
+             jacobi=True, storage="f64", half_step=False):
+    """Solve ``A x = b`` by Algorithm 1 in float64.
+
+    ``coef`` holds the raw operator (``diag`` and the six directions);
+    ``storage`` is the type the scaled operator is rounded to (the system the
+    GPU path actually holds).  Returns a :class:`Result`.
+    """
+    n = nx * ny * nz
+    b = np.asarray(b, dtype=np.float64)
+    if jacobi:
+        op = stencil.jacobi_scale(nx, ny, nz, coef, storage)
+        bt = stencil.scale_rhs(nx, ny, nz, coef, b)
+    else:
+        op = stencil.rounded(nx, ny, nz, coef, storage)
+        bt = b.copy()
+
+    def A(v):
+        return stencil.apply(nx, ny, nz, op, v)
+
+    x = np.zeros(n) if x0 is None else np.asarray(x0, dtype=np.float64).copy()
+    bnorm = np.sqrt(_dot(bt, bt))
+    hist = [0.0]
+    if bnorm == 0.0:
+        return _finish(nx, ny, nz, coef, op, b, bt, np.zeros(n), 0, [0.0], OK)
+
+    r = bt - A(x)
+    rhat = r.copy()
+    p = r.copy()
+    rho = _dot(rhat, r)
+    hist = [np.sqrt(_dot(r, r)) / bnorm]
+    if hist[0] <= tol:
+        return _finish(nx, ny, nz, coef, op, b, bt, x, 0, hist, OK)
+
+    status = NOTCONV
+    it = 0
+    for i in range(maxit):
+        s = A(p)
+        sigma = _dot(rhat, s)
+        if sigma == 0.0 or not np.isfinite(sigma) or not np.isfinite(rho):
+            status = BREAKDOWN
+            break
+        alpha = rho / sigma
+        q = r - alpha * s
+        if half_step:
+            qn = np.sqrt(_dot(q, q)) / bnorm
+            if qn <= tol:
+                x = x + alpha * p
+                hist.append(qn)
+                it = i + 1
+                status = OK
+                break
+        y = A(q)
+        yy = _dot(y, y)
+        qy = _dot(q, y)
+        if yy == 0.0:
+            x = x + alpha * p
+            qn = np.sqrt(_dot(q, q)) / bnorm
+            hist.append(qn)
+            it = i + 1
+            status = OK if qn <= tol else BREAKDOWN
+            break
+        omega = qy / yy
+        if omega == 0.0 or not np.isfinite(omega):
+            status = BREAKDOWN
+            break
+        x = x + alpha * p + omega * q
+        r = q - omega * y
+        rho_new = _dot(rhat, r)
+        rr = _dot(r, r)
+        hist.append(np.sqrt(rr) / bnorm)
+        it = i + 1
+        if hist[-1] <= tol:
+            status = OK
+            break
+        if rho_new == 0.0 or not np.isfinite(rho_new):
+            status = BREAKDOWN
+            break
+        beta = (alpha / omega) * (rho_new / rho)
+        p = r + beta * (p - omega * s)
+        rho = rho_new
+    return _finish(nx, ny, nz, coef, op, b, bt, x, it, hist, status)
+
+
+def _finish(nx, ny, nz, coef, op, b, bt, x, it, hist, status):
+    def rel(res, rhs):
+        nb = np.linalg.norm(rhs)
+        return float(np.linalg.norm(res) / nb) if nb > 0 else float(np.linalg.norm(res))
+
+    tr = rel(bt - stencil.apply(nx, ny, nz, op, x), bt)
+    tro = rel(b - stencil.apply(nx, ny, nz, coef, x), b)
+    return Result(x, it, np.asarray(hist, dtype=np.float64), status, tr, tro)
+
+
+def true_residual(nx, ny, nz, coef, b, x):
+    """``||b - A x|| / ||b||`` in float64 on the operator ``coef``."""
+    r = np.asarray(b, dtype=np.float64) - stencil.apply(nx, ny, nz, coef, x)
+    nb = np.linalg.norm(b)
+    return float(np.linalg.norm(r) / nb) if nb > 0 else float(np.linalg.norm(r))

@@ -1,0 +1,337 @@
+"""Pins of the FP64 oracle against closed forms, brute force and library
+routines (CPU only).  Each pin is chosen so that a plausible mistake in the
+oracle -- a swapped direction, a wrong sign or index, a dropped term, a
+transposed operand -- fails at least one of them; ``test_planted_*`` plant
+such mistakes in the oracle and check that a pin catches them."""
+
+import math
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import bicgstab as ob
+from oracle import counts, direct, stencil
+from tests.conftest import golden
+
+
+def rand_coef(nx, ny, nz, seed, sym=False):
+    p = synth.varcoef(nx, ny, nz, seed=seed, dtype=np.float64)
+    c = dict(p.coef)
+    if sym:
+        # symmetric operator: pair each minus coefficient with the neighbour's plus
+        t = stencil.transpose_coef(nx, ny, nz, c)
+        for d in stencil.DIRS:
+            c[d] = 0.5 * (np.asarray(c[d]) + t[d])
+    return c, p.b.astype(np.float64)
+
+
+# --------------------------------------------------------------------------
+# operator
+# --------------------------------------------------------------------------
+
+def quadratic_check(nx, ny, nz, coef):
+    """Max relative deviation of A u from the closed form on interior cells.
+
+    For a quadratic u, u(t+1) + u(t-1) = 2u + u'' and u(t+1) - u(t-1) = 2u'
+    hold exactly along each axis, so for constant coefficients
+    (A u) = d u + sum_a [ (m_a + p_a)(u + u_aa/2) + (p_a - m_a) u_a ].
+    """
+    rng = np.random.default_rng(5)
+    q = rng.uniform(-1, 1, 10)   # u = q0 + q1 x + q2 y + q3 z + q4 x^2 + ... + q9 yz
+
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    x = x.astype(float); y = y.astype(float); z = z.astype(float)
+    u = (q[0] + q[1] * x + q[2] * y + q[3] * z + q[4] * x * x + q[5] * y * y
+         + q[6] * z * z + q[7] * x * y + q[8] * x * z + q[9] * y * z)
+    ux = q[1] + 2 * q[4] * x + q[7] * y + q[8] * z
+    uy = q[2] + 2 * q[5] * y + q[7] * x + q[9] * z
+    uz = q[3] + 2 * q[6] * z + q[8] * x + q[9] * y
+    second = {"x": 2 * q[4], "y": 2 * q[5], "z": 2 * q[6]}
+    first = {"x": ux, "y": uy, "z": uz}
+    expect = coef["diag"] * u
+    for a in "xyz":
+        m, p = coef[a + "m"], coef[a + "p"]
+        expect = expect + (m + p) * (u + second[a] / 2) + (p - m) * first[a]
+    got = stencil.apply(nx, ny, nz, coef, u.reshape(-1)).reshape(nz, ny, nx)
+    inner = (slice(1, -1),) * 3
+    return np.max(np.abs(got[inner] - expect[inner]) / (1 + np.abs(expect[inner])))
+
+
+def test_constant_operator_exact_on_quadratics():
+    p = synth.convdiff_constant(9, 7, 6, seed=0)
+    assert quadratic_check(9, 7, 6, p.coef) < 1e-13
+
+
+def test_laplacian_eigenpairs_closed_form():
+    nx, ny, nz = 6, 5, 4
+    lap = synth.laplacian(nx, ny, nz).coef
+    for k in [(1, 1, 1), (2, 3, 1), (6, 5, 4), (3, 1, 2)]:
+        lam, v = direct.laplacian_eigenpair(nx, ny, nz, *k)
+        av = stencil.apply(nx, ny, nz, lap, v)
+        assert np.max(np.abs(av - lam * v)) < 1e-12 * max(1, lam)
+
+
+def test_laplacian_spectrum_matches_dense_eigensolve():
+    nx, ny, nz = 4, 3, 5
+    lap = synth.laplacian(nx, ny, nz).coef
+    a = stencil.assemble_dense(nx, ny, nz, lap)
+    ev = np.sort(np.linalg.eigvalsh(a))
+    closed = np.sort([direct.laplacian_eigenpair(nx, ny, nz, i, j, k)[0]
+                      for i in range(1, nx + 1) for j in range(1, ny + 1)
+                      for k in range(1, nz + 1)])
+    assert np.max(np.abs(ev - closed)) < 1e-12
+
+
+@pytest.mark.parametrize("shape", [(4, 5, 3), (1, 1, 7), (7, 1, 2), (3, 3, 3)])
+def test_apply_matches_dense_assembly(shape):
+    nx, ny, nz = shape
+    coef, _ = rand_coef(nx, ny, nz, seed=11)
+    v = synth.random_vector(nx * ny * nz, 3, 9, np.float64)
+    a = stencil.assemble_dense(nx, ny, nz, coef)
+    assert np.max(np.abs(a @ v - stencil.apply(nx, ny, nz, coef, v))) < 1e-13
+
+
+def test_adjoint_identity_with_independent_transpose():
+    nx, ny, nz = 5, 4, 6
+    coef, _ = rand_coef(nx, ny, nz, seed=12)
+    t = stencil.transpose_coef(nx, ny, nz, coef)
+    n = nx * ny * nz
+    x = synth.random_vector(n, 1, 5, np.float64)
+    y = synth.random_vector(n, 2, 5, np.float64)
+    lhs = np.dot(stencil.apply(nx, ny, nz, coef, x), y)
+    rhs = np.dot(x, stencil.apply(nx, ny, nz, t, y))
+    assert abs(lhs - rhs) < 1e-12 * abs(lhs)
+    # and the transpose agrees with the dense matrix transposed
+    a = stencil.assemble_dense(nx, ny, nz, coef)
+    at = stencil.assemble_dense(nx, ny, nz, t)
+    assert np.array_equal(a.T, at)
+    # the operator is nonsymmetric
+    assert np.max(np.abs(a - a.T)) > 0.1
+
+
+def test_jacobi_scaling_is_row_scaling():
+    nx, ny, nz = 4, 3, 3
+    coef, b = rand_coef(nx, ny, nz, seed=13)
+    sc = stencil.jacobi_scale(nx, ny, nz, coef, "f64")
+    a = stencil.assemble_dense(nx, ny, nz, coef)
+    at = stencil.assemble_dense(nx, ny, nz, sc)
+    d = np.asarray(coef["diag"])
+    assert np.allclose(at, a / d[:, None], rtol=0, atol=1e-15)
+    assert np.all(np.diag(at) == 1.0)
+    # same solution for the scaled and the raw system
+    x1 = np.linalg.solve(a, b)
+    x2 = np.linalg.solve(at, stencil.scale_rhs(nx, ny, nz, coef, b))
+    assert np.allclose(x1, x2, rtol=1e-12, atol=1e-14)
+
+
+def test_abs_apply_bounds_rows():
+    nx, ny, nz = 5, 4, 3
+    coef, _ = rand_coef(nx, ny, nz, seed=14)
+    v = synth.random_vector(nx * ny * nz, 4, 5, np.float64)
+    assert np.all(np.abs(stencil.apply(nx, ny, nz, coef, v))
+                  <= stencil.abs_apply(nx, ny, nz, coef, v) + 1e-15)
+
+
+# --------------------------------------------------------------------------
+# rounding to storage types
+# --------------------------------------------------------------------------
+
+def test_round_f16_matches_numpy_half():
+    rng = np.random.default_rng(0)
+    x = np.concatenate([rng.normal(size=20000),
+                        rng.uniform(-1e-4, 1e-4, 20000),     # subnormal range of binary16
+                        rng.uniform(-2, 2, 20000)])
+    ref = x.astype(np.float16).astype(np.float64)
+    assert np.array_equal(stencil.round_to(x, "f16"), ref)
+
+
+def test_round_bf16_matches_bit_rounding_of_binary32():
+    # for binary32 inputs, RNE to bfloat16 is the classic "add 0x7fff + lsb,
+    # drop 16 bits" on the binary32 bit pattern
+    rng = np.random.default_rng(1)
+    x32 = np.concatenate([rng.normal(size=50000), rng.uniform(-3, 3, 50000)]).astype(np.float32)
+    # include exact ties
+    ties = ((np.arange(0x3F80, 0x3F80 + 200, dtype=np.uint32) << 16) | 0x8000).view(np.float32)
+    x32 = np.concatenate([x32, ties])
+    bits = x32.view(np.uint32).astype(np.uint64)
+    lsb = (bits >> 16) & 1
+    rb = (((bits + 0x7FFF + lsb) >> 16) << 16).astype(np.uint32)
+    ref = rb.view(np.float32).astype(np.float64)
+    assert np.array_equal(stencil.round_to(x32.astype(np.float64), "bf16"), ref)
+
+
+def test_round_f32_is_numpy_single():
+    x = np.random.default_rng(2).normal(size=1000)
+    assert np.array_equal(stencil.round_to(x, "f32"), x.astype(np.float32).astype(np.float64))
+
+
+# --------------------------------------------------------------------------
+# BiCGStab (Algorithm 1)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("shape,seed", [((6, 5, 4), 21), ((8, 8, 8), 22), ((3, 7, 5), 23)])
+def test_bicgstab_matches_dense_lu(shape, seed):
+    nx, ny, nz = shape
+    coef, b = rand_coef(nx, ny, nz, seed)
+    res = ob.bicgstab(nx, ny, nz, coef, b, tol=1e-13, maxit=1000)
+    assert res.status == ob.OK
+    xd = direct.dense_solve(nx, ny, nz, coef, b)
+    a = stencil.assemble_dense(nx, ny, nz, coef)
+    kappa = np.linalg.cond(a)
+    assert np.linalg.norm(res.x - xd) / np.linalg.norm(xd) < 10 * kappa * 1e-13
+    assert res.true_resid_orig < 1e-12
+
+
+def test_bicgstab_constant_convdiff_config_small():
+    p = synth.convdiff_constant(8, 8, 8, seed=0)
+    res = ob.bicgstab(8, 8, 8, p.coef, p.b, tol=1e-8, maxit=500)
+    assert res.status == ob.OK and res.hist[-1] <= 1e-8
+    xd = direct.dense_solve(8, 8, 8, p.coef, p.b)
+    assert np.linalg.norm(res.x - xd) / np.linalg.norm(xd) < 1e-7
+
+
+def test_bicgstab_symmetric_case_equals_cg():
+    nx, ny, nz = 7, 6, 5
+    lap = {"diag": 6.1, **{d: -1.0 for d in stencil.DIRS}}
+    b = synth.random_vector(nx * ny * nz, 0, 1, np.float64, "uniform")
+    res = ob.bicgstab(nx, ny, nz, lap, b, tol=1e-13, maxit=500, jacobi=False)
+    xc = direct.cg(nx, ny, nz, lap, b)
+    assert np.linalg.norm(res.x - xc) / np.linalg.norm(xc) < 1e-11
+
+
+def test_bicgstab_1d_equals_thomas():
+    nz = 40
+    coef, b = rand_coef(1, 1, nz, seed=31)
+    res = ob.bicgstab(1, 1, nz, coef, b, tol=1e-14, maxit=200)
+    lower = np.asarray(coef["zm"]).copy()
+    upper = np.asarray(coef["zp"]).copy()
+    xt = direct.thomas(lower, np.asarray(coef["diag"]), upper, b)
+    assert np.linalg.norm(res.x - xt) / np.linalg.norm(xt) < 1e-11
+
+
+def test_recurrence_and_true_residual_agree():
+    coef, b = rand_coef(12, 10, 9, seed=41)
+    res = ob.bicgstab(12, 10, 9, coef, b, tol=1e-10, maxit=500)
+    assert res.status == ob.OK
+    assert abs(res.hist[-1] - res.true_resid) < 1e-12
+    assert res.true_resid <= 1.01e-10
+    # residual history starts at 1 for x0 = 0
+    assert res.hist[0] == pytest.approx(1.0, abs=1e-15)
+
+
+def test_bicgstab_general_x0():
+    coef, b = rand_coef(6, 6, 6, seed=42)
+    x0 = synth.random_vector(216, 9, 9, np.float64)
+    res = ob.bicgstab(6, 6, 6, coef, b, x0=x0, tol=1e-12, maxit=500)
+    xd = direct.dense_solve(6, 6, 6, coef, b)
+    assert np.linalg.norm(res.x - xd) / np.linalg.norm(xd) < 1e-10
+    assert res.hist[0] != pytest.approx(1.0)
+
+
+def test_bicgstab_degenerate_cases():
+    coef, b = rand_coef(4, 4, 4, seed=43)
+    # b = 0: x = 0 after zero steps
+    r0 = ob.bicgstab(4, 4, 4, coef, np.zeros(64), tol=1e-8)
+    assert r0.iters == 0 and r0.status == ob.OK and not np.any(r0.x)
+    # exact start: no step taken
+    xd = direct.dense_solve(4, 4, 4, coef, b)
+    r1 = ob.bicgstab(4, 4, 4, coef, b, x0=xd, tol=1e-8)
+    assert r1.iters == 0 and r1.status == ob.OK
+    # a single cell: A = [d], one step is exact
+    c1 = {"diag": 2.5, **{d: 0.0 for d in stencil.DIRS}}
+    r2 = ob.bicgstab(1, 1, 1, c1, np.array([5.0]), tol=1e-12)
+    assert r2.status == ob.OK and r2.x[0] == pytest.approx(2.0)
+    # maxit reached: status NOTCONV, history has maxit+1 entries
+    r3 = ob.bicgstab(4, 4, 4, coef, b, tol=1e-30, maxit=3)
+    assert r3.status == ob.NOTCONV and r3.iters == 3 and len(r3.hist) == 4
+
+
+def test_iteration_count_bounded_by_n_on_tiny_mesh():
+    # exact arithmetic ends in <= N steps; in float64 on 2x2x2 it does too
+    coef, b = rand_coef(2, 2, 2, seed=44)
+    res = ob.bicgstab(2, 2, 2, coef, b, tol=1e-12, maxit=50)
+    assert res.status == ob.OK and res.iters <= 8 + 2
+
+
+def test_storage_rounding_changes_system_but_not_much():
+    coef, b = rand_coef(8, 7, 6, seed=45)
+    r64 = ob.bicgstab(8, 7, 6, coef, b, tol=1e-12, storage="f64")
+    r16 = ob.bicgstab(8, 7, 6, coef, b, tol=1e-12, storage="bf16")
+    d = np.linalg.norm(r64.x - r16.x) / np.linalg.norm(r64.x)
+    assert 1e-5 < d < 5e-2
+
+
+# --------------------------------------------------------------------------
+# the paper's printed numbers
+# --------------------------------------------------------------------------
+
+def test_table_I_counts():
+    rows = {r[0]: r for r in golden("table_I_ops.txt")}
+    for k in ("matvec", "dot", "axpy"):
+        sp_add, sp_mul = int(rows[k][2]), int(rows[k][3])
+        assert counts.TABLE_I_SINGLE[k] == (sp_add, sp_mul)
+        assert counts.ops_from_algorithm()[k] == (sp_add, sp_mul)
+        assert counts.TABLE_I_MIXED[k] == tuple(int(v) for v in rows[k][4:7])
+    tot = rows["total"]
+    assert sum(int(v) for v in tot[2:4]) == 44
+    assert sum(int(v) for v in tot[4:7]) == 44
+    assert counts.ops_per_point() == (44, 44)
+
+
+def test_paper_rate_and_storage_arithmetic():
+    g = {r[0]: float(r[1]) for r in golden("paper_numbers.txt")}
+    pf = counts.pflops(g["mesh_x"], g["mesh_y"], g["mesh_z"], g["us_per_iter"] * 1e-6,
+                       int(g["ops_per_point"]))
+    assert round(pf, 2) == g["pflops"]
+    words = counts.paper_storage_words(int(g["mesh_z"]))
+    assert words == g["storage_words_per_z"] * g["mesh_z"]
+    assert round(words * 2 / 1000) == g["storage_kb_at_1536"]     # 16-bit words
+    assert words * 2 < g["core_sram_kb"] * 1024
+
+
+def test_byte_model():
+    assert counts.bytes_per_cell(4, 4, 4) == 116
+    assert counts.bytes_per_cell(2, 2, 4) == 62
+    assert counts.bytes_per_cell(8, 8, 8) == 232
+
+
+# --------------------------------------------------------------------------
+# planted mistakes: each must be caught by a pin above
+# --------------------------------------------------------------------------
+
+def test_planted_swapped_direction_is_caught(monkeypatch):
+    bad = dict(stencil._NEIGH)
+    bad["xm"], bad["xp"] = bad["xp"], bad["xm"]
+    monkeypatch.setattr(stencil, "_NEIGH", bad)
+    p = synth.convdiff_constant(9, 7, 6, seed=0)
+    assert quadratic_check(9, 7, 6, p.coef) > 1e-3
+
+
+def test_planted_transposed_axes_is_caught(monkeypatch):
+    bad = dict(stencil._NEIGH)
+    bad["xm"], bad["zm"] = bad["zm"], bad["xm"]
+    bad["xp"], bad["zp"] = bad["zp"], bad["xp"]
+    monkeypatch.setattr(stencil, "_NEIGH", bad)
+    p = synth.convdiff_constant(9, 7, 6, seed=0)
+    assert quadratic_check(9, 7, 6, p.coef) > 1e-3
+
+
+def test_planted_wrong_omega_sign_is_caught(monkeypatch):
+    real = ob._dot
+    calls = {"n": 0}
+
+    def bad_dot(a, b):
+        # calls: ||b||^2, rho, ||r0||^2, then per step (r0,s), (y,y), (q,y),
+        # (r0,r), (r,r); negate every (q, y), so omega changes sign
+        calls["n"] += 1
+        v = real(a, b)
+        n = calls["n"]
+        return -v if n >= 6 and (n - 6) % 5 == 0 else v
+
+    coef, b = rand_coef(6, 5, 4, seed=21)
+    monkeypatch.setattr(ob, "_dot", bad_dot)
+    res = ob.bicgstab(6, 5, 4, coef, b, tol=1e-13, maxit=200)
+    xd = direct.dense_solve(6, 5, 4, coef, b)
+    assert not (res.status == ob.OK and
+                np.linalg.norm(res.x - xd) / np.linalg.norm(xd) < 1e-8)
