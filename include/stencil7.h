@@ -1,0 +1,202 @@
+/*
+ * stencil7.h -- C ABI of the GB300 BiCGStab library for 7-point stencil systems.
+ *
+ * The library solves A x = b, where A is the nonsymmetric matrix of a
+ * 7-point finite-difference stencil on a structured nx*ny*nz mesh (Fan et al.,
+ * "Fast Stencil-Code Computation on a Wafer-Scale Processor", SC20: Sec. III,
+ * Eq. 1, and Sec. IV), by standard BiCGStab (Algorithm 1).  Every step of the
+ * iteration runs in the library's own CUDA kernels on one GPU.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Layout.  A mesh vector has nx*ny*nz elements stored x-fastest:
+ *   cell (x, y, z) is element i = x + nx*(y + ny*z).
+ * Operator.  Row i of A is
+ *   (A v)_i = diag_i v_i + xm_i v_{i-1}     + xp_i v_{i+1}
+ *                        + ym_i v_{i-nx}    + yp_i v_{i+nx}
+ *                        + zm_i v_{i-nx*ny} + zp_i v_{i+nx*ny},
+ *   the six off-diagonals named by axis and sign as in Sec. IV-A; a
+ *   neighbour outside the mesh contributes zero (homogeneous Dirichlet).
+ * Diagonal preconditioning.  By default the library stores the operator with
+ *   a unit main diagonal, A~ = D^-1 A (Sec. IV: "with diagonal preconditioning
+ *   the main diagonal is all ones", so six diagonals are stored); each
+ *   off-diagonal is divided by its row's diagonal in float64 and rounded once
+ *   (round to nearest even) to the storage type.  Solves then run on
+ *   A~ x = D^-1 b, which has the same solution; tolerances and residual
+ *   histories refer to that scaled system.
+ * Memory.  Every pointer argument may be host memory (pageable or pinned) or
+ *   device memory of the current device; the library tells them apart with
+ *   the CUDA pointer attributes and stages host data itself.  Buffers passed
+ *   in stay owned by the caller; the library keeps no pointer to them after
+ *   the call returns.
+ * Streams.  `stream` is a cudaStream_t passed as void* (NULL = the legacy
+ *   default stream).  Calls that return results to the host (iteration counts,
+ *   norms, histories) synchronise that stream before returning; stencil7_apply
+ *   with device buffers does not.
+ * Errors.  Every entry point returns an S7_* code; nothing aborts.  After a
+ *   non-zero return, s7_last_error() gives a one-line description (per host
+ *   thread).  A handle stays usable after S7_EBREAKDOWN / S7_ENOTCONV.
+ * Threads.  A handle must not be used by two host threads at once.
+ */
+#ifndef STENCIL7_H
+#define STENCIL7_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ---- */
+#define S7_OK          0  /* success (for solves: converged to tol)                  */
+#define S7_EINVAL      1  /* bad argument: size, null pointer, dtype combination      */
+#define S7_ENOMEM      2  /* device (or pinned host) allocation failed                */
+#define S7_EBREAKDOWN  3  /* BiCGStab breakdown: (r0,s)=0, omega=0, (r0,r)=0 or a
+                             non-finite scalar; x and the history up to the last
+                             completed step are returned                              */
+#define S7_ENOTCONV    4  /* maxit steps taken without reaching tol; x and the full
+                             history are valid                                       */
+#define S7_ETIMEOUT    5  /* a bounded wait expired (serving waits)                   */
+#define S7_ECUDA       6  /* a CUDA runtime call failed; see s7_last_error()          */
+#define S7_EAGAIN      7  /* result not ready yet (s7_server_poll)                    */
+#define S7_ECANCELED   8  /* request cancelled                                        */
+
+/* ---- element types ---- */
+typedef enum {
+  S7_F64 = 0,   /* IEEE binary64 */
+  S7_F32 = 1,   /* IEEE binary32 */
+  S7_BF16 = 2,  /* bfloat16 (8 significant bits, binary32 exponent range) */
+  S7_F16 = 3    /* IEEE binary16 (the paper's 16-bit format, Sec. II) */
+} s7_dtype;
+
+typedef struct stencil7_op* stencil7_t;
+
+/* Raw operator coefficients, as the application produced them.
+ * diag and the six directions each point to nx*ny*nz elements of `dtype`
+ * (S7_F64 or S7_F32), or to ONE element each when `constant` is 1 (a
+ * constant-coefficient operator).  Entries that point outside the mesh are
+ * read but multiply zero.  Host or device memory. */
+typedef struct {
+  const void* diag;
+  const void* xm;
+  const void* xp;
+  const void* ym;
+  const void* yp;
+  const void* zm;
+  const void* zp;
+  s7_dtype dtype;
+  int constant;
+} s7_coeffs;
+
+/* Creation options.  Zero-initialise and set what you need; a NULL pointer
+ * means all defaults. */
+typedef struct {
+  s7_dtype storage;  /* type of the stored operator and of the Krylov vectors
+                        r, r0, p, s, y.  S7_F64 computes in float64; S7_F32,
+                        S7_BF16 and S7_F16 compute in float32 with the iterate x
+                        kept in float32.  Default (0) = S7_F64; set explicitly. */
+  int no_jacobi;     /* 1: store the raw seven diagonals instead of D^-1 A    */
+  int keep_true;     /* 1: also keep the raw coefficients in float32, used by
+                        stencil7_residual and bicgstab_solve_refined as the
+                        "true" operator (required for the refined solver when
+                        storage is 16-bit)                                    */
+  int bx, by;        /* sweep tile: bx threads (each 16 bytes of x) by by rows;
+                        0 = tuned default                                     */
+  int zchunk;        /* z planes per thread block in the sweeps; 0 = default  */
+  int check_every;   /* iterations per CUDA-graph launch between host checks
+                        of the device convergence flag; 0 = default            */
+} s7_opts;
+
+/* Create an operator handle.  Copies the coefficients to library-owned device
+ * memory, scaling them to a unit diagonal (unless opts->no_jacobi) in a CUDA
+ * kernel, so the caller may free its copies on return.  nx, ny, nz >= 1 and
+ * nx*ny*nz < 2^40.  Returns S7_EINVAL for bad sizes, a NULL pointer, a
+ * storage/dtype combination not listed above, or a zero diagonal entry;
+ * S7_ENOMEM if device memory runs out (nothing is leaked). */
+int stencil7_create(stencil7_t* out, int nx, int ny, int nz,
+                    const s7_coeffs* coeffs, const s7_opts* opts);
+
+/* Release a handle and all device memory it owns.  NULL is accepted. */
+int stencil7_destroy(stencil7_t h);
+
+/* Mesh sizes, storage type and device bytes held by a handle. */
+int stencil7_info(stencil7_t h, int* nx, int* ny, int* nz, s7_dtype* storage,
+                  size_t* device_bytes);
+
+/* One SpMV with the stored operator: y = A~ x (Sec. IV-A "SpMV (3D)"; with
+ * Jacobi scaling A~ = D^-1 A has a unit diagonal).  x and y hold nx*ny*nz
+ * elements of `dt`, which must equal the handle's storage type; they must not
+ * overlap.  Accumulation is float32 (float64 for S7_F64).  With device
+ * buffers the call is asynchronous on `stream`. */
+int stencil7_apply(stencil7_t h, const void* x, void* y, s7_dtype dt, void* stream);
+
+/* True residual of the raw system, r = b - A x, accumulated in float64 from
+ * the raw float32 coefficients when the handle keeps them (keep_true), else
+ * from the stored operator times the kept diagonal.  b and x hold nx*ny*nz
+ * elements of `dt` (S7_F64 or S7_F32).  r (same type) may be NULL.  Returns
+ * ||r||_2 in *rnorm and ||b||_2 in *bnorm (either may be NULL); synchronous. */
+int stencil7_residual(stencil7_t h, const void* b, const void* x, void* r,
+                      s7_dtype dt, double* rnorm, double* bnorm, void* stream);
+
+/* BiCGStab (Algorithm 1) on A~ x = D^-1 b.
+ *   b      nx*ny*nz elements of dt (S7_F64 or S7_F32); unchanged.
+ *   x      in: start vector x0; out: the last iterate.  Same size and type.
+ *   tol    stop after the first full step with ||r_k|| / ||b~|| <= tol
+ *          (recurrence residual, 2-norms).  No step is taken if the start
+ *          vector already satisfies it; b = 0 gives x = 0 after zero steps.
+ *   maxit  at most this many steps (>= 0).
+ *   iters  out (may be NULL): full steps taken.
+ *   resid_hist  out (host, may be NULL): *iters+1 values, resid_hist[k] =
+ *          ||r_k|| / ||b~|| (caller provides maxit+1 doubles).
+ *   true_resid  out (may be NULL): ||b~ - A~ x|| / ||b~|| recomputed from x at
+ *          the end with float64 accumulation.
+ * Every step runs as three fused sweeps (p update + SpMV + (r0,s); q + SpMV +
+ * (q,y),(y,y); x and r updates + (r0,r),(r,r)), each ending in a
+ * deterministic grid-level combine of per-block partial sums in float64; the
+ * steps are replayed from a captured CUDA graph.  Synchronous.  Returns S7_OK,
+ * S7_ENOTCONV or S7_EBREAKDOWN (x and history valid in all three cases). */
+int bicgstab_solve(stencil7_t h, const void* b, void* x, s7_dtype dt,
+                   double tol, int maxit, int* iters, double* resid_hist,
+                   double* true_resid, void* stream);
+
+/* Mixed-precision solve with float64 iterative refinement.  The paper notes
+ * that 16-bit solves plateau near a relative residual of 1e-2 (Sec. VI-B) and
+ * that they may need a correction scheme such as iterative refinement.  Outer
+ * loop: r = b - A x in float64 on the true operator (keep_true, float32
+ * coefficients); stop when ||r|| / ||b|| <= tol; else solve A~ d = D^-1 r / s
+ * with the handle's storage precision (s = ||r||_2 / sqrt(N), so the inner
+ * right-hand side has unit RMS and stays inside binary16's normal range) to
+ * inner_tol or inner_maxit steps, and update x += s d in float64.
+ *   b, x        float64, nx*ny*nz (x in: x0, out: solution).
+ *   hist        out (host, may be NULL): max_outer+1 true relative residuals.
+ *   outer, inner_total  out (may be NULL): outer steps and summed inner steps.
+ * Returns S7_OK when tol is met, S7_ENOTCONV after max_outer steps,
+ * S7_EBREAKDOWN if an inner solve breaks down before making progress. */
+int bicgstab_solve_refined(stencil7_t h, const double* b, double* x, double tol,
+                           int max_outer, int inner_maxit, double inner_tol,
+                           int* outer, int* inner_total, double* hist, void* stream);
+
+/* Per-kernel timing for benchmarks.  enable = 1 turns timing on for handle
+ * h: solves then launch each kernel directly (not from a captured graph)
+ * with a CUDA event pair around it on the handle's stream; enable = 0 turns
+ * it off.  Every call first copies the totals accumulated since the previous
+ * call into ms[k] (milliseconds) and launches[k] (either may be NULL;
+ * S7_PROF_NKINDS entries each) and resets them.  Kinds, in order: the fused
+ * p-update + SpMV + (r0,s) sweep; the fused q + SpMV + (q,y),(y,y) sweep;
+ * the x/r update with (r0,r),(r,r); the start-residual sweep; the
+ * true-residual sweep; everything else (casts, refinement kernels). */
+#define S7_PROF_NKINDS 6
+int stencil7_profile(stencil7_t h, int enable, double* ms, long long* launches);
+
+/* ---- thread-local error text ---- */
+const char* s7_last_error(void);
+
+/* Library version string. */
+const char* s7_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* STENCIL7_H */

@@ -1,0 +1,353 @@
+"""BiCGStab for 7-point stencil systems on one GB300 GPU.
+
+Python binding of ``libstencil7.so``, whose C ABI is ``include/stencil7.h``.
+The functions here carry the C names and only marshal arguments: every step
+of the solve runs in the library's CUDA kernels.  Buffers may be torch
+tensors (CUDA or CPU) or NumPy arrays; CUDA tensors are passed to the
+library by pointer on the current torch stream, host buffers are staged by
+the library.  There is no CPU fallback: if the library is not built, or no
+GPU is visible, calls raise.
+
+Layout: a mesh vector has ``nx*ny*nz`` elements, x fastest
+(``i = x + nx*(y + ny*z)``).  Coefficients: ``diag`` and the six
+off-diagonals ``xm, xp, ym, yp, zm, zp`` (Sec. IV-A of the paper names them by
+axis and sign).
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _build
+
+__all__ = [
+    "S7_F64", "S7_F32", "S7_BF16", "S7_F16", "S7Error", "Operator", "lib", "EXPORTS",
+    "stencil7_create", "stencil7_destroy", "stencil7_info", "stencil7_apply",
+    "stencil7_residual", "bicgstab_solve", "bicgstab_solve_refined", "stencil7_profile",
+    "s7_last_error", "s7_version",
+]
+
+S7_F64, S7_F32, S7_BF16, S7_F16 = 0, 1, 2, 3
+OK, EINVAL, ENOMEM, EBREAKDOWN, ENOTCONV, ETIMEOUT, ECUDA, EAGAIN, ECANCELED = range(9)
+STATUS_NAMES = {0: "ok", 1: "einval", 2: "enomem", 3: "breakdown", 4: "notconv",
+                5: "timeout", 6: "ecuda", 7: "eagain", 8: "canceled"}
+DIRS = ("xm", "xp", "ym", "yp", "zm", "zp")
+_STORAGE = {"f64": S7_F64, "f32": S7_F32, "bf16": S7_BF16, "f16": S7_F16}
+
+# Entry points declared in include/stencil7.h (checked by the tests).
+EXPORTS = (
+    "stencil7_create", "stencil7_destroy", "stencil7_info", "stencil7_apply",
+    "stencil7_residual", "bicgstab_solve", "bicgstab_solve_refined", "stencil7_profile",
+    "s7_last_error", "s7_version",
+)
+PROF_KINDS = ("spmv_p_dot", "spmv_q_dots", "update_dots", "start_residual", "true_residual",
+              "other")
+
+
+class S7Error(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (STATUS_NAMES.get(code, "?"), code, msg))
+        self.code = code
+
+
+class s7_coeffs(C.Structure):
+    _fields_ = [("diag", C.c_void_p), ("xm", C.c_void_p), ("xp", C.c_void_p),
+                ("ym", C.c_void_p), ("yp", C.c_void_p), ("zm", C.c_void_p),
+                ("zp", C.c_void_p), ("dtype", C.c_int), ("constant", C.c_int)]
+
+
+class s7_opts(C.Structure):
+    _fields_ = [("storage", C.c_int), ("no_jacobi", C.c_int), ("keep_true", C.c_int),
+                ("bx", C.c_int), ("by", C.c_int), ("zchunk", C.c_int),
+                ("check_every", C.c_int)]
+
+
+_lib = None
+
+
+def lib_path():
+    return _build.LIB
+
+
+def lib():
+    """Load the CUDA library (it must have been built; see ``_build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError("libstencil7.so is not built: run __graft_entry__.build() "
+                           "or python -m paper_2010_03660_gb300._build")
+    L = C.CDLL(path)
+    vp, i, d = C.c_void_p, C.c_int, C.c_double
+    P = C.POINTER
+    sig = {
+        "stencil7_create": (i, [P(vp), i, i, i, P(s7_coeffs), P(s7_opts)]),
+        "stencil7_destroy": (i, [vp]),
+        "stencil7_info": (i, [vp, P(i), P(i), P(i), P(i), P(C.c_size_t)]),
+        "stencil7_apply": (i, [vp, vp, vp, i, vp]),
+        "stencil7_residual": (i, [vp, vp, vp, vp, i, P(d), P(d), vp]),
+        "bicgstab_solve": (i, [vp, vp, vp, i, d, i, P(i), P(d), P(d), vp]),
+        "bicgstab_solve_refined": (i, [vp, vp, vp, d, i, i, d, P(i), P(i), P(d), vp]),
+        "stencil7_profile": (i, [vp, i, P(d), P(C.c_longlong)]),
+        "s7_last_error": (C.c_char_p, []),
+        "s7_version": (C.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def s7_last_error():
+    return lib().s7_last_error().decode()
+
+
+def s7_version():
+    return lib().s7_version().decode()
+
+
+def _check(rc, allow=()):
+    if rc != OK and rc not in allow:
+        raise S7Error(rc, s7_last_error())
+    return rc
+
+
+# ---------------------------------------------------------------------------
+# buffer marshalling
+# ---------------------------------------------------------------------------
+
+def _is_torch(a):
+    return type(a).__module__.startswith("torch")
+
+
+def _dtype_code(a):
+    if _is_torch(a):
+        import torch
+        m = {torch.float64: S7_F64, torch.float32: S7_F32, torch.bfloat16: S7_BF16,
+             torch.float16: S7_F16}
+        return m[a.dtype]
+    m = {np.dtype(np.float64): S7_F64, np.dtype(np.float32): S7_F32,
+         np.dtype(np.float16): S7_F16}
+    return m[np.asarray(a).dtype]
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if _is_torch(a):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    if not (isinstance(a, np.ndarray) and a.flags["C_CONTIGUOUS"]):
+        raise ValueError("array must be a C-contiguous numpy array")
+    return a.ctypes.data
+
+
+def _stream(*bufs):
+    for a in bufs:
+        if a is not None and _is_torch(a) and a.is_cuda:
+            import torch
+            return torch.cuda.current_stream(a.device).cuda_stream
+    return None
+
+
+def _numel(a):
+    return a.numel() if _is_torch(a) else np.asarray(a).size
+
+
+def _empty_like(a, dtype_code=None):
+    if _is_torch(a):
+        import torch
+        m = {S7_F64: torch.float64, S7_F32: torch.float32, S7_BF16: torch.bfloat16,
+             S7_F16: torch.float16}
+        return torch.empty(a.shape, dtype=m[dtype_code] if dtype_code is not None else a.dtype,
+                           device=a.device)
+    m = {S7_F64: np.float64, S7_F32: np.float32, S7_F16: np.float16}
+    return np.empty(np.asarray(a).shape, dtype=m[dtype_code] if dtype_code is not None
+                    else np.asarray(a).dtype)
+
+
+# ---------------------------------------------------------------------------
+# the operator handle
+# ---------------------------------------------------------------------------
+
+class Operator:
+    """An owned ``stencil7_t`` (see :func:`stencil7_create`)."""
+
+    def __init__(self, handle, nx, ny, nz, storage):
+        self._h = C.c_void_p(handle)
+        self.nx, self.ny, self.nz = nx, ny, nz
+        self.storage = storage
+
+    @property
+    def n(self):
+        return self.nx * self.ny * self.nz
+
+    @property
+    def handle(self):
+        if not self._h:
+            raise ValueError("operator destroyed")
+        return self._h
+
+    def close(self):
+        if self._h:
+            lib().stencil7_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def stencil7_create(nx, ny, nz, coef, storage="f32", jacobi=True, keep_true=False,
+                    bx=0, by=0, zchunk=0, check_every=0, constant=None):
+    """Create an operator from raw coefficients.
+
+    ``coef`` maps ``diag, xm, xp, ym, yp, zm, zp`` to arrays/tensors of
+    ``nx*ny*nz`` float32 or float64 values (all the same type), or all to
+    Python floats for a constant-coefficient operator.
+    """
+    names = ("diag",) + DIRS
+    if constant is None:
+        constant = all(np.isscalar(coef[k]) for k in names)
+    keep = []
+    ptrs = {}
+    if constant:
+        raw_dt = S7_F64
+        for k in names:
+            a = np.array([float(coef[k])], dtype=np.float64)
+            keep.append(a)
+            ptrs[k] = a.ctypes.data
+    else:
+        raw_dt = _dtype_code(coef["diag"])
+        for k in names:
+            a = coef[k]
+            if _numel(a) != nx * ny * nz:
+                raise ValueError("coefficient %s has %d elements, expected %d"
+                                 % (k, _numel(a), nx * ny * nz))
+            if _dtype_code(a) != raw_dt:
+                raise ValueError("all coefficients must have the same dtype")
+            keep.append(a)
+            ptrs[k] = _ptr(a)
+    cs = s7_coeffs(ptrs["diag"], ptrs["xm"], ptrs["xp"], ptrs["ym"], ptrs["yp"],
+                   ptrs["zm"], ptrs["zp"], raw_dt, 1 if constant else 0)
+    st = _STORAGE[storage] if isinstance(storage, str) else int(storage)
+    op = s7_opts(st, 0 if jacobi else 1, 1 if keep_true else 0, bx, by, zchunk, check_every)
+    h = C.c_void_p()
+    _check(lib().stencil7_create(C.byref(h), nx, ny, nz, C.byref(cs), C.byref(op)))
+    del keep
+    return Operator(h.value, nx, ny, nz, st)
+
+
+def stencil7_destroy(op):
+    op.close()
+
+
+def stencil7_info(op):
+    nx, ny, nz, st = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+    nb = C.c_size_t()
+    _check(lib().stencil7_info(op.handle, C.byref(nx), C.byref(ny), C.byref(nz), C.byref(st),
+                               C.byref(nb)))
+    return {"nx": nx.value, "ny": ny.value, "nz": nz.value, "storage": st.value,
+            "device_bytes": nb.value}
+
+
+def stencil7_apply(op, x, y=None):
+    """``y = A~ x`` with the stored operator; returns y."""
+    if y is None:
+        y = _empty_like(x)
+    _check(lib().stencil7_apply(op.handle, _ptr(x), _ptr(y), _dtype_code(x), _stream(x, y)))
+    return y
+
+
+def stencil7_residual(op, b, x, r=None):
+    """``r = b - A x`` on the raw system; returns ``(rnorm, bnorm)``."""
+    rn, bn = C.c_double(), C.c_double()
+    _check(lib().stencil7_residual(op.handle, _ptr(b), _ptr(x), _ptr(r), _dtype_code(b),
+                                   C.byref(rn), C.byref(bn), _stream(b, x, r)))
+    return rn.value, bn.value
+
+
+def stencil7_profile(op, enable):
+    """Turn per-kernel timing on/off; returns the totals since the last call
+    as ``{kind: (milliseconds, launches)}``."""
+    ms = (C.c_double * 6)()
+    n = (C.c_longlong * 6)()
+    _check(lib().stencil7_profile(op.handle, 1 if enable else 0, ms, n))
+    return {k: (ms[j], n[j]) for j, k in enumerate(PROF_KINDS)}
+
+
+@dataclass
+class SolveResult:
+    x: object
+    iters: int
+    hist: np.ndarray
+    true_resid: float
+    status: int
+
+
+def bicgstab_solve(op, b, x=None, tol=1e-6, maxit=500, history=True, true_resid=True):
+    """BiCGStab (Algorithm 1) on the operator; ``x`` holds x0 and is overwritten.
+
+    Returns a :class:`SolveResult`; breakdown and non-convergence are
+    reported in ``status`` (3, 4), other errors raise :class:`S7Error`.
+    """
+    if x is None:
+        x = _empty_like(b)
+        if _is_torch(x):
+            x.zero_()
+        else:
+            x[...] = 0
+    it = C.c_int()
+    hist = np.zeros(maxit + 1) if history else None
+    tr = C.c_double()
+    rc = lib().bicgstab_solve(op.handle, _ptr(b), _ptr(x), _dtype_code(b), float(tol),
+                              int(maxit), C.byref(it),
+                              hist.ctypes.data_as(C.POINTER(C.c_double)) if history else None,
+                              C.byref(tr) if true_resid else None, _stream(b, x))
+    _check(rc, allow=(EBREAKDOWN, ENOTCONV))
+    return SolveResult(x, it.value, hist[:it.value + 1] if history else None,
+                       tr.value if true_resid else float("nan"), rc)
+
+
+@dataclass
+class RefinedResult:
+    x: object
+    outer: int
+    inner_total: int
+    hist: np.ndarray
+    status: int
+
+
+def bicgstab_solve_refined(op, b, x=None, tol=1e-10, max_outer=30, inner_maxit=200,
+                           inner_tol=1e-2):
+    """Mixed-precision solve with float64 iterative refinement (float64 b, x)."""
+    if x is None:
+        x = _empty_like(b)
+        if _is_torch(x):
+            x.zero_()
+        else:
+            x[...] = 0
+    outer, inner = C.c_int(), C.c_int()
+    hist = np.zeros(max_outer + 1)
+    rc = lib().bicgstab_solve_refined(op.handle, _ptr(b), _ptr(x), float(tol), int(max_outer),
+                                      int(inner_maxit), float(inner_tol), C.byref(outer),
+                                      C.byref(inner), hist.ctypes.data_as(C.POINTER(C.c_double)),
+                                      _stream(b, x))
+    _check(rc, allow=(EBREAKDOWN, ENOTCONV))
+    return RefinedResult(x, outer.value, inner.value, hist[:outer.value + 1], rc)

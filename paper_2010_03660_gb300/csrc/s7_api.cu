@@ -1,0 +1,813 @@
+// C ABI of the library (declared in include/stencil7.h): handle lifetime,
+// workspace management, host/device staging, the solve driver that replays
+// captured CUDA graphs of BiCGStab steps, and float64 iterative refinement.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+
+#include "s7_handle.h"
+#include "s7_sweep.cuh"
+
+using namespace s7;
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+static thread_local char g_err[512] = "";
+
+static int fail(int code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof g_err, fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+static int cuda_fail(cudaError_t e, const char* what) {
+  return fail(e == cudaErrorMemoryAllocation ? S7_ENOMEM : S7_ECUDA, "%s: %s", what,
+              cudaGetErrorString(e));
+}
+
+#define CK(call)                                       \
+  do {                                                 \
+    cudaError_t e_ = (call);                           \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+extern "C" const char* s7_last_error(void) { return g_err; }
+extern "C" const char* s7_version(void) { return "stencil7-gb300 0.1 (sm_103a)"; }
+
+// ---------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------
+static size_t dsize(s7_dtype t) {
+  switch (t) {
+    case S7_F64: return 8;
+    case S7_F32: return 4;
+    case S7_BF16:
+    case S7_F16: return 2;
+  }
+  return 0;
+}
+
+static const Engine* engine_for(s7_dtype t) {
+  switch (t) {
+    case S7_F64: return engine_f64();
+    case S7_F32: return engine_f32();
+    case S7_BF16: return engine_bf16();
+    case S7_F16: return engine_f16();
+  }
+  return nullptr;
+}
+
+static s7_dtype xtype(const Handle* h) { return h->storage == S7_F64 ? S7_F64 : S7_F32; }
+
+// True if p is device (or managed) memory; host memory otherwise.
+static bool on_device(const void* p) {
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+static int dmalloc(Handle* h, void** p, size_t bytes) {
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return fail(S7_ENOMEM, "cudaMalloc(%zu bytes) failed: %s", bytes, cudaGetErrorString(e));
+  }
+  h->bytes += bytes;
+  return S7_OK;
+}
+
+static void dfree(Handle* h, void** p, size_t bytes) {
+  if (*p) {
+    cudaFree(*p);
+    h->bytes -= bytes;
+  }
+  *p = nullptr;
+}
+
+// small kernels of the driver
+__global__ void k_fill_f32(long long n, float* p, float v) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    p[i] = v;
+}
+
+// out = (X) (r / s): the refinement's inner right-hand side
+template <class X>
+__global__ void k_scaled_copy(long long n, const double* r, double inv_s, X* out) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    out[i] = (X)(r[i] * inv_s);
+}
+
+// x += s * d, in float64
+template <class X>
+__global__ void k_axpy_f64(long long n, double s, const X* d, double* x) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    x[i] = fma(s, (double)d[i], x[i]);
+}
+
+static int grid_for(long long n) {
+  long long g = (n + 255) / 256;
+  return (int)std::max(1LL, std::min(g, 152LL * 16));
+}
+
+static int num_sms() {
+  int dev = 0, nsm = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  return nsm;
+}
+
+namespace s7 {
+void default_tile(int nx, int ny, int nz, int vec, int nsm, Tile* t) {
+  const int runs = (nx + vec - 1) / vec;
+  const int ntx = (runs + 31) / 32;
+  int bx = (runs + ntx - 1) / ntx;          // <= 32 runs per row, balanced tiles
+  int by = std::max(1, std::min(ny, 256 / std::max(1, bx)));
+  if (by > 16) by = 16;
+  while (bx * by > 512) --by;
+  const long long tiles = (long long)ntx * ((ny + by - 1) / by);
+  // z chunk: long enough to amortise the two extra planes of each chunk,
+  // short enough to give every SM several blocks
+  const long long target = (long long)nsm * 8;
+  long long zc = (tiles * nz + target - 1) / target;
+  zc = std::max(4LL, std::min(64LL, zc));
+  if (zc > nz) zc = nz;
+  t->bx = bx;
+  t->by = by;
+  t->zchunk = (int)zc;
+}
+}  // namespace s7
+
+// ---------------------------------------------------------------------------
+// create / destroy
+// ---------------------------------------------------------------------------
+static void prof_free(Handle* h);
+
+static void release(Handle* h) {
+  Workspace& w = h->ws;
+  if (w.graph) cudaGraphExecDestroy(w.graph);
+  w.graph = nullptr;
+  const size_t ts = dsize(h->storage), xs = dsize(xtype(h));
+  const size_t n = (size_t)h->n;
+  dfree(h, &w.r, n * ts);
+  dfree(h, &w.rh, n * ts);
+  for (int k = 0; k < 2; ++k) {
+    dfree(h, &w.p[k], n * ts);
+    dfree(h, &w.s[k], n * ts);
+  }
+  dfree(h, &w.y, n * ts);
+  dfree(h, &w.x, n * xs);
+  dfree(h, &w.b, n * xs);
+  dfree(h, &w.stage, n * 8);
+  dfree(h, (void**)&w.parts, w.parts_n * 8);
+  dfree(h, (void**)&w.hist, (size_t)w.hist_cap * 8);
+  dfree(h, (void**)&w.sc, sizeof(Scalars));
+  dfree(h, &w.ref_x, n * 8);
+  dfree(h, &w.ref_b, n * 8);
+  dfree(h, &w.ref_r, n * 8);
+  if (w.h_sc) cudaFreeHost(w.h_sc);
+  w.h_sc = nullptr;
+  w.ready = false;
+  for (int d = 0; d < 6; ++d) dfree(h, &h->c[d], n * ts);
+  dfree(h, &h->diag, n * ts);
+  dfree(h, &h->d, n * dsize(xtype(h)));
+  for (int d = 0; d < 7; ++d) dfree(h, (void**)&h->tc[d], n * 4);
+  dfree(h, &h->small, 256);
+  prof_free(h);
+  if (h->ev) cudaEventDestroy(h->ev);
+  if (h->stream) cudaStreamDestroy(h->stream);
+  h->ev = nullptr;
+  h->stream = nullptr;
+}
+
+static double round_storage(double v, s7_dtype t) {
+  switch (t) {
+    case S7_F64: return v;
+    case S7_F32: return (double)(float)v;
+    case S7_BF16: return (double)__bfloat162float(__double2bfloat16(v));
+    case S7_F16: return (double)__half2float(__double2half(v));
+  }
+  return v;
+}
+
+extern "C" int stencil7_create(stencil7_t* out, int nx, int ny, int nz, const s7_coeffs* c,
+                               const s7_opts* o) {
+  if (!out) return fail(S7_EINVAL, "stencil7_create: out is NULL");
+  *out = nullptr;
+  if (!c) return fail(S7_EINVAL, "stencil7_create: coeffs is NULL");
+  if (nx < 1 || ny < 1 || nz < 1) return fail(S7_EINVAL, "stencil7_create: sizes must be >= 1");
+  const long long n = (long long)nx * ny * nz;
+  if (n >= (1LL << 40)) return fail(S7_EINVAL, "stencil7_create: mesh too large");
+  if (c->dtype != S7_F64 && c->dtype != S7_F32)
+    return fail(S7_EINVAL, "stencil7_create: raw coefficients must be S7_F64 or S7_F32");
+  const void* raw_in[7] = {c->xm, c->xp, c->ym, c->yp, c->zm, c->zp, c->diag};
+  for (int d = 0; d < 7; ++d)
+    if (!raw_in[d]) return fail(S7_EINVAL, "stencil7_create: coefficient pointer %d is NULL", d);
+  s7_opts opts;
+  memset(&opts, 0, sizeof opts);
+  if (o) opts = *o;
+  const Engine* eng = engine_for(opts.storage);
+  if (!eng) return fail(S7_EINVAL, "stencil7_create: unknown storage type %d", (int)opts.storage);
+
+  stencil7_op* h = new (std::nothrow) stencil7_op();
+  if (!h) return fail(S7_ENOMEM, "stencil7_create: host allocation failed");
+  h->nx = nx;
+  h->ny = ny;
+  h->nz = nz;
+  h->n = n;
+  h->storage = opts.storage;
+  h->jacobi = opts.no_jacobi ? 0 : 1;
+  h->keep_true = opts.keep_true ? 1 : 0;
+  h->constant = c->constant ? 1 : 0;
+  cudaGetDevice(&h->device);
+  default_tile(nx, ny, nz, eng->vec, num_sms(), &h->tile);
+  if (opts.bx > 0) h->tile.bx = opts.bx;
+  if (opts.by > 0) h->tile.by = opts.by;
+  if (opts.zchunk > 0) h->tile.zchunk = std::min(opts.zchunk, nz);
+  if (h->tile.bx * h->tile.by > 512) {
+    delete h;
+    return fail(S7_EINVAL, "stencil7_create: bx*by must be <= 512");
+  }
+  // iterations per graph launch: about a millisecond of work per launch
+  {
+    const double est_us = std::max(15.0, 120.0 * (double)n / 6.0e6);
+    int ce = (int)std::min(64.0, std::max(2.0, 1000.0 / est_us));
+    h->check_every = opts.check_every > 0 ? opts.check_every : ce;
+  }
+  if (!eng->smem_ok(h)) {
+    delete h;
+    return fail(S7_EINVAL, "stencil7_create: tile too large for shared memory");
+  }
+
+  int rc = S7_OK;
+  cudaError_t e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    rc = cuda_fail(e, "stream/event creation");
+    release(h);
+    delete h;
+    return rc;
+  }
+  const size_t ts = eng->t_size;
+  if ((rc = dmalloc(h, &h->small, 256))) goto fail_out;
+
+  if (h->constant) {
+    // read the seven scalars (host or device) and scale on the host in float64
+    double v[7];
+    for (int d = 0; d < 7; ++d) {
+      if (c->dtype == S7_F64) {
+        double t;
+        if ((e = cudaMemcpy(&t, raw_in[d], 8, cudaMemcpyDefault)) != cudaSuccess) break;
+        v[d] = t;
+      } else {
+        float t;
+        if ((e = cudaMemcpy(&t, raw_in[d], 4, cudaMemcpyDefault)) != cudaSuccess) break;
+        v[d] = t;
+      }
+    }
+    if (e != cudaSuccess) {
+      rc = cuda_fail(e, "reading constant coefficients");
+      goto fail_out;
+    }
+    if (v[6] == 0.0 || !isfinite(v[6])) {
+      rc = fail(S7_EINVAL, "stencil7_create: zero or non-finite diagonal");
+      goto fail_out;
+    }
+    for (int d = 0; d < 6; ++d)
+      h->cconst[d] = round_storage(h->jacobi ? v[d] / v[6] : v[d], h->storage);
+    h->cconst[6] = h->jacobi ? v[6] : round_storage(v[6], h->storage);
+    if (h->keep_true) {
+      // true operator as float32 arrays (the raw-residual sweep reads arrays)
+      for (int d = 0; d < 7; ++d) {
+        if ((rc = dmalloc(h, (void**)&h->tc[d], (size_t)n * 4))) goto fail_out;
+      }
+    }
+  } else {
+    for (int d = 0; d < 6; ++d)
+      if ((rc = dmalloc(h, &h->c[d], (size_t)n * ts))) goto fail_out;
+    if (!h->jacobi && (rc = dmalloc(h, &h->diag, (size_t)n * ts))) goto fail_out;
+    if (h->jacobi && (rc = dmalloc(h, &h->d, (size_t)n * dsize(xtype(h))))) goto fail_out;
+    if (h->keep_true)
+      for (int d = 0; d < 7; ++d)
+        if ((rc = dmalloc(h, (void**)&h->tc[d], (size_t)n * 4))) goto fail_out;
+  }
+  {
+    // stage raw arrays on the device (each array in turn if it is host memory)
+    const size_t rs = dsize(c->dtype);
+    const void* raw_dev[7];
+    void* stage[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    const long long cnt = h->constant ? 1 : n;
+    for (int d = 0; d < 7 && rc == S7_OK; ++d) {
+      if (!h->constant && on_device(raw_in[d])) {
+        raw_dev[d] = raw_in[d];
+      } else {
+        void* p = nullptr;
+        if ((e = cudaMalloc(&p, (size_t)cnt * rs)) != cudaSuccess) {
+          cudaGetLastError();
+          rc = fail(S7_ENOMEM, "staging coefficients: %s", cudaGetErrorString(e));
+          break;
+        }
+        stage[d] = p;
+        if ((e = cudaMemcpyAsync(p, raw_in[d], (size_t)cnt * rs, cudaMemcpyDefault, h->stream)) !=
+            cudaSuccess) {
+          rc = cuda_fail(e, "copying coefficients");
+          break;
+        }
+        raw_dev[d] = p;
+      }
+    }
+    if (rc == S7_OK && !h->constant) {
+      int bad = 0;
+      rc = eng->scale(h, raw_dev, c->dtype, h->stream, &bad);
+      if (rc) rc = fail(rc, "coefficient scaling failed: %s", cudaGetErrorString(cudaGetLastError()));
+      else if (bad) rc = fail(S7_EINVAL, "stencil7_create: %d zero or non-finite diagonal entries", bad);
+    } else if (rc == S7_OK && h->constant && h->keep_true) {
+      // expand the constants into arrays
+      for (int d = 0; d < 7 && rc == S7_OK; ++d) {
+        float v;
+        if (c->dtype == S7_F64) {
+          double t;
+          cudaMemcpy(&t, raw_in[d], 8, cudaMemcpyDefault);
+          v = (float)t;
+        } else {
+          cudaMemcpy(&v, raw_in[d], 4, cudaMemcpyDefault);
+        }
+        k_fill_f32<<<grid_for(n), 256, 0, h->stream>>>(n, h->tc[d], v);
+        if ((e = cudaGetLastError()) != cudaSuccess) rc = cuda_fail(e, "k_fill_f32");
+      }
+    }
+    cudaStreamSynchronize(h->stream);
+    for (int d = 0; d < 7; ++d)
+      if (stage[d]) cudaFree(stage[d]);
+    if (rc) goto fail_out;
+  }
+  *out = h;
+  return S7_OK;
+
+fail_out:
+  release(h);
+  delete h;
+  return rc;
+}
+
+extern "C" int stencil7_destroy(stencil7_t h) {
+  if (!h) return S7_OK;
+  cudaStreamSynchronize(h->stream);
+  release(h);
+  delete h;
+  return S7_OK;
+}
+
+extern "C" int stencil7_info(stencil7_t h, int* nx, int* ny, int* nz, s7_dtype* storage,
+                             size_t* bytes) {
+  if (!h) return fail(S7_EINVAL, "stencil7_info: NULL handle");
+  if (nx) *nx = h->nx;
+  if (ny) *ny = h->ny;
+  if (nz) *nz = h->nz;
+  if (storage) *storage = h->storage;
+  if (bytes) *bytes = h->bytes;
+  return S7_OK;
+}
+
+// ---------------------------------------------------------------------------
+// workspace
+// ---------------------------------------------------------------------------
+static int ensure_ws(Handle* h, int maxit) {
+  Workspace& w = h->ws;
+  const Engine* eng = engine_for(h->storage);
+  const size_t n = (size_t)h->n, ts = eng->t_size, xs = eng->x_size;
+  int rc;
+  if (!w.ready) {
+    void** vs[7] = {&w.r, &w.rh, &w.p[0], &w.p[1], &w.s[0], &w.s[1], &w.y};
+    for (int k = 0; k < 7; ++k)
+      if ((rc = dmalloc(h, vs[k], n * ts))) return rc;
+    if ((rc = dmalloc(h, &w.x, n * xs))) return rc;
+    if ((rc = dmalloc(h, &w.b, n * xs))) return rc;
+    w.parts_n = eng->parts_needed(h);
+    if ((rc = dmalloc(h, (void**)&w.parts, w.parts_n * 8))) return rc;
+    if ((rc = dmalloc(h, (void**)&w.sc, sizeof(Scalars)))) return rc;
+    CK(cudaMemset(w.sc, 0, sizeof(Scalars)));
+    if (!w.h_sc) CK(cudaMallocHost((void**)&w.h_sc, sizeof(Scalars)));
+    w.ready = true;
+  }
+  if (maxit + 1 > w.hist_cap) {
+    if (w.graph) {  // the graph holds the history pointer
+      cudaGraphExecDestroy(w.graph);
+      w.graph = nullptr;
+    }
+    dfree(h, (void**)&w.hist, (size_t)w.hist_cap * 8);
+    w.hist_cap = 0;
+    const int cap = std::max(maxit + 1, 1024);
+    if ((rc = dmalloc(h, (void**)&w.hist, (size_t)cap * 8))) return rc;
+    w.hist_cap = cap;
+  }
+  return S7_OK;
+}
+
+static int ensure_stage(Handle* h) {
+  if (h->ws.stage) return S7_OK;
+  return dmalloc(h, &h->ws.stage, (size_t)h->n * 8);
+}
+
+// Bring caller data (host or device, type `dt`) into a device buffer of type
+// `want`.  If the caller's buffer is already suitable it is returned as is.
+static int stage_in(Handle* h, const void* src, s7_dtype dt, s7_dtype want, void* dst,
+                    const void** out, cudaStream_t st) {
+  const Engine* eng = engine_for(h->storage);
+  const size_t n = (size_t)h->n;
+  const bool dev = on_device(src);
+  if (dev && dt == want && ((uintptr_t)src & 15u) == 0) {
+    *out = src;
+    return S7_OK;
+  }
+  if (dt == want) {
+    CK(cudaMemcpyAsync(dst, src, n * dsize(dt), cudaMemcpyDefault, st));
+  } else {
+    int rc;
+    if ((rc = ensure_stage(h))) return rc;
+    CK(cudaMemcpyAsync(h->ws.stage, src, n * dsize(dt), cudaMemcpyDefault, st));
+    if ((rc = eng->cast(h->ws.stage, dt, dst, want, (long long)n, st)))
+      return fail(rc, "type conversion failed");
+  }
+  *out = dst;
+  return S7_OK;
+}
+
+// Copy device buffer `src` (type `have`) to caller memory `dst` (type `dt`).
+static int stage_out(Handle* h, const void* src, s7_dtype have, void* dst, s7_dtype dt,
+                     cudaStream_t st) {
+  const Engine* eng = engine_for(h->storage);
+  const size_t n = (size_t)h->n;
+  if (dt == have) {
+    CK(cudaMemcpyAsync(dst, src, n * dsize(dt), cudaMemcpyDefault, st));
+    return S7_OK;
+  }
+  int rc;
+  if ((rc = ensure_stage(h))) return rc;
+  if ((rc = eng->cast(src, have, h->ws.stage, dt, (long long)n, st)))
+    return fail(rc, "type conversion failed");
+  CK(cudaMemcpyAsync(dst, h->ws.stage, n * dsize(dt), cudaMemcpyDefault, st));
+  return S7_OK;
+}
+
+// The caller's stream waits for the handle's stream, or the reverse.
+static int join(cudaStream_t from, cudaStream_t to, cudaEvent_t ev) {
+  if (from == to) return S7_OK;
+  CK(cudaEventRecord(ev, from));
+  CK(cudaStreamWaitEvent(to, ev, 0));
+  return S7_OK;
+}
+
+// ---------------------------------------------------------------------------
+// apply / residual
+// ---------------------------------------------------------------------------
+extern "C" int stencil7_apply(stencil7_t h, const void* x, void* y, s7_dtype dt, void* stream) {
+  if (!h || !x || !y) return fail(S7_EINVAL, "stencil7_apply: NULL argument");
+  if (dt != h->storage)
+    return fail(S7_EINVAL, "stencil7_apply: dt (%d) must equal the storage type (%d)", (int)dt,
+                (int)h->storage);
+  if (x == y) return fail(S7_EINVAL, "stencil7_apply: x and y must not overlap");
+  const Engine* eng = engine_for(h->storage);
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool dx = on_device(x), dy = on_device(y);
+  if (dx && dy) {
+    int rc = eng->apply(h, x, y, st);
+    return rc ? fail(rc, "stencil7_apply: launch failed: %s", cudaGetErrorString(cudaGetLastError()))
+              : S7_OK;
+  }
+  // host buffers: stage through temporary device memory
+  const size_t bytes = (size_t)h->n * eng->t_size;
+  void *tx = nullptr, *ty = nullptr;
+  int rc = S7_OK;
+  if ((rc = dmalloc(h, &tx, bytes)) || (rc = dmalloc(h, &ty, bytes))) {
+    dfree(h, &tx, bytes);
+    return rc;
+  }
+  cudaError_t e = cudaMemcpyAsync(tx, x, bytes, cudaMemcpyDefault, st);
+  if (e == cudaSuccess) {
+    rc = eng->apply(h, tx, ty, st);
+    if (rc == S7_OK) e = cudaMemcpyAsync(y, ty, bytes, cudaMemcpyDefault, st);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  dfree(h, &tx, bytes);
+  dfree(h, &ty, bytes);
+  if (e != cudaSuccess) return cuda_fail(e, "stencil7_apply");
+  return rc ? fail(rc, "stencil7_apply: launch failed") : S7_OK;
+}
+
+// Run the float64 raw-system residual on device buffers; returns norms.
+static int raw_resid_dev(Handle* h, const void* b, const void* x, void* r, s7_dtype dt,
+                         double* rn, double* bn, cudaStream_t st) {
+  const Engine* eng = engine_for(h->storage);
+  int rc = eng->raw_resid(h, b, x, r, dt, st);
+  if (rc) return fail(rc, "residual launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+  CK(cudaMemcpyAsync(h->ws.h_sc, h->ws.sc, sizeof(Scalars), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (rn) *rn = sqrt(h->ws.h_sc->res[0]);
+  if (bn) *bn = sqrt(h->ws.h_sc->res[1]);
+  return S7_OK;
+}
+
+extern "C" int stencil7_residual(stencil7_t h, const void* b, const void* x, void* r, s7_dtype dt,
+                                 double* rnorm, double* bnorm, void* stream) {
+  if (!h || !b || !x) return fail(S7_EINVAL, "stencil7_residual: NULL argument");
+  if (dt != S7_F64 && dt != S7_F32) return fail(S7_EINVAL, "stencil7_residual: dt must be F64 or F32");
+  int rc;
+  if ((rc = ensure_ws(h, 0))) return rc;
+  cudaStream_t us = (cudaStream_t)stream, st = h->stream;
+  if ((rc = join(us, st, h->ev))) return rc;
+  const size_t bytes = (size_t)h->n * dsize(dt);
+  const bool db = on_device(b), dx = on_device(x), dr = !r || on_device(r);
+  void *tb = nullptr, *tx = nullptr, *tr = nullptr;
+  const void *pb = b, *px = x;
+  void* pr = r;
+  if (!db) { if ((rc = dmalloc(h, &tb, bytes))) goto out; CK(cudaMemcpyAsync(tb, b, bytes, cudaMemcpyDefault, st)); pb = tb; }
+  if (!dx) { if ((rc = dmalloc(h, &tx, bytes))) goto out; CK(cudaMemcpyAsync(tx, x, bytes, cudaMemcpyDefault, st)); px = tx; }
+  if (!dr) { if ((rc = dmalloc(h, &tr, bytes))) goto out; pr = tr; }
+  rc = raw_resid_dev(h, pb, px, pr, dt, rnorm, bnorm, st);
+  if (rc == S7_OK && !dr) {
+    cudaError_t e = cudaMemcpyAsync(r, tr, bytes, cudaMemcpyDefault, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) rc = cuda_fail(e, "stencil7_residual: copy out");
+  }
+out:
+  cudaStreamSynchronize(st);
+  dfree(h, &tb, bytes);
+  dfree(h, &tx, bytes);
+  dfree(h, &tr, bytes);
+  if (rc == S7_OK) rc = join(st, us, h->ev);
+  return rc;
+}
+
+// ---------------------------------------------------------------------------
+// per-kernel timing
+// ---------------------------------------------------------------------------
+enum { PK_A = 0, PK_B = 1, PK_C = 2, PK_INIT = 3, PK_RES = 4, PK_OTHER = 5 };
+
+// Fold finished event pairs into the totals (the stream must be idle).
+static void prof_collect(Handle* h) {
+  for (int i = 0; i < h->prof_ev_used; ++i) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, h->prof_ev[2 * i], h->prof_ev[2 * i + 1]) == cudaSuccess) {
+      h->prof_ms[h->prof_kind[i]] += ms;
+      h->prof_n[h->prof_kind[i]] += 1;
+    }
+  }
+  cudaGetLastError();
+  h->prof_ev_used = 0;
+}
+
+static int prof_begin(Handle* h, int kind, cudaStream_t st) {
+  if (!h->prof) return -1;
+  if (h->prof_ev_used == h->prof_ev_cap) {
+    const int cap = std::max(64, 2 * h->prof_ev_cap);
+    cudaEvent_t* ev = new (std::nothrow) cudaEvent_t[2 * cap];
+    int* kd = new (std::nothrow) int[cap];
+    if (!ev || !kd) { delete[] ev; delete[] kd; return -1; }
+    for (int i = 0; i < 2 * h->prof_ev_cap; ++i) ev[i] = h->prof_ev[i];
+    for (int i = 0; i < h->prof_ev_cap; ++i) kd[i] = h->prof_kind[i];
+    for (int i = 2 * h->prof_ev_cap; i < 2 * cap; ++i)
+      if (cudaEventCreate(&ev[i]) != cudaSuccess) { delete[] ev; delete[] kd; return -1; }
+    delete[] h->prof_ev;
+    delete[] h->prof_kind;
+    h->prof_ev = ev;
+    h->prof_kind = kd;
+    h->prof_ev_cap = cap;
+  }
+  const int i = h->prof_ev_used++;
+  h->prof_kind[i] = kind;
+  cudaEventRecord(h->prof_ev[2 * i], st);
+  return i;
+}
+
+static void prof_end(Handle* h, int i, cudaStream_t st) {
+  if (i >= 0) cudaEventRecord(h->prof_ev[2 * i + 1], st);
+}
+
+static void prof_free(Handle* h) {
+  for (int i = 0; i < 2 * h->prof_ev_cap; ++i) cudaEventDestroy(h->prof_ev[i]);
+  delete[] h->prof_ev;
+  delete[] h->prof_kind;
+  h->prof_ev = nullptr;
+  h->prof_kind = nullptr;
+  h->prof_ev_cap = h->prof_ev_used = 0;
+}
+
+extern "C" int stencil7_profile(stencil7_t h, int enable, double* ms, long long* launches) {
+  if (!h) return fail(S7_EINVAL, "stencil7_profile: NULL handle");
+  cudaStreamSynchronize(h->stream);
+  prof_collect(h);
+  for (int k = 0; k < S7_PROF_NKINDS; ++k) {
+    if (ms) ms[k] = h->prof_ms[k];
+    if (launches) launches[k] = h->prof_n[k];
+    h->prof_ms[k] = 0.0;
+    h->prof_n[k] = 0;
+  }
+  h->prof = enable ? 1 : 0;
+  return S7_OK;
+}
+
+// One BiCGStab step: its three kernels, each timed when profiling.
+static int run_step(Handle* h, cudaStream_t st) {
+  const Engine* eng = engine_for(h->storage);
+  for (int k = 0; k < 3; ++k) {
+    const int pi = prof_begin(h, k, st);
+    int rc = eng->step_kernel(h, k, st);
+    prof_end(h, pi, st);
+    if (rc) return rc;
+  }
+  return S7_OK;
+}
+
+// ---------------------------------------------------------------------------
+// the solve driver
+// ---------------------------------------------------------------------------
+static int capture_graph(Handle* h) {
+  Workspace& w = h->ws;
+  const Engine* eng = engine_for(h->storage);
+  if (w.graph) return S7_OK;
+  cudaGraph_t g = nullptr;
+  CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+  int rc = S7_OK;
+  for (int k = 0; k < h->check_every && rc == S7_OK; ++k)
+    for (int j = 0; j < 3 && rc == S7_OK; ++j) rc = eng->step_kernel(h, j, h->stream);
+  cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+  if (rc || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return rc ? fail(rc, "graph capture: step launch failed") : cuda_fail(e, "cudaStreamEndCapture");
+  }
+  e = cudaGraphInstantiate(&w.graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    w.graph = nullptr;
+    return cuda_fail(e, "cudaGraphInstantiate");
+  }
+  w.graph_steps = h->check_every;
+  return S7_OK;
+}
+
+struct SolveOut {
+  int iters;
+  int status;
+  double bnorm;
+};
+
+// Solve A~ x = D^-1 b with the iterate in ws.x (already set to x0) and b a
+// device buffer of the iterate's type.  Leaves the history in ws.hist.
+static int solve_core(Handle* h, const void* bdev, double tol, int maxit, SolveOut* so) {
+  Workspace& w = h->ws;
+  const Engine* eng = engine_for(h->storage);
+  cudaStream_t st = h->stream;
+  Scalars* hs = w.h_sc;
+  memset(hs, 0, sizeof(Scalars));
+  hs->tol = tol;
+  hs->maxit = maxit;
+  hs->status = 4;
+  CK(cudaMemcpyAsync(w.sc, hs, sizeof(Scalars), cudaMemcpyHostToDevice, st));
+  const int pi = prof_begin(h, PK_INIT, st);
+  int rc = eng->init(h, bdev, st);
+  prof_end(h, pi, st);
+  if (rc) return fail(rc, "init launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+  // hist[0] = ||r_0|| / ||b~|| is left in res[2] by the start kernel
+  CK(cudaMemcpyAsync(w.hist, &w.sc->res[2], sizeof(double), cudaMemcpyDeviceToDevice, st));
+  if (!h->prof && (rc = capture_graph(h))) return rc;
+  const int per = std::max(1, h->check_every);
+  const int max_launch = maxit / per + 3;
+  int launches = 0;
+  for (;;) {
+    CK(cudaMemcpyAsync(hs, w.sc, sizeof(Scalars), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (h->prof) prof_collect(h);
+    if (hs->done) break;
+    if (++launches > max_launch)
+      return fail(S7_ECUDA, "solve did not terminate after %d launches", launches - 1);
+    if (h->prof) {
+      for (int k = 0; k < per; ++k)
+        if ((rc = run_step(h, st))) return fail(rc, "step launch failed");
+    } else {
+      CK(cudaGraphLaunch(w.graph, st));
+    }
+  }
+  so->iters = hs->iter;
+  so->status = hs->status;
+  so->bnorm = hs->bnorm;
+  return S7_OK;
+}
+
+extern "C" int bicgstab_solve(stencil7_t h, const void* b, void* x, s7_dtype dt, double tol,
+                              int maxit, int* iters, double* resid_hist, double* true_resid,
+                              void* stream) {
+  if (!h || !b || !x) return fail(S7_EINVAL, "bicgstab_solve: NULL argument");
+  if (dt != S7_F64 && dt != S7_F32) return fail(S7_EINVAL, "bicgstab_solve: dt must be F64 or F32");
+  if (maxit < 0 || !(tol >= 0.0)) return fail(S7_EINVAL, "bicgstab_solve: bad tol or maxit");
+  int rc;
+  if ((rc = ensure_ws(h, maxit))) return rc;
+  Workspace& w = h->ws;
+  const Engine* eng = engine_for(h->storage);
+  const s7_dtype xt = xtype(h);
+  cudaStream_t us = (cudaStream_t)stream, st = h->stream;
+  if ((rc = join(us, st, h->ev))) return rc;
+  const void* bdev = nullptr;
+  if ((rc = stage_in(h, b, dt, xt, w.b, &bdev, st))) return rc;
+  const void* xin = nullptr;
+  if ((rc = stage_in(h, x, dt, xt, w.x, &xin, st))) return rc;
+  if (xin != w.x) CK(cudaMemcpyAsync(w.x, xin, (size_t)h->n * eng->x_size, cudaMemcpyDeviceToDevice, st));
+  SolveOut so;
+  if ((rc = solve_core(h, bdev, tol, maxit, &so))) return rc;
+  if (so.bnorm == 0.0) CK(cudaMemsetAsync(w.x, 0, (size_t)h->n * eng->x_size, st));
+  if (true_resid) {
+    const int pr = prof_begin(h, PK_RES, st);
+    rc = eng->true_resid(h, bdev, st);
+    prof_end(h, pr, st);
+    if (rc) return fail(rc, "true residual launch failed");
+    CK(cudaMemcpyAsync(w.h_sc, w.sc, sizeof(Scalars), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    const double bb = w.h_sc->res[1];
+    *true_resid = bb > 0 ? sqrt(w.h_sc->res[0] / bb) : sqrt(w.h_sc->res[0]);
+  }
+  if (resid_hist)
+    CK(cudaMemcpyAsync(resid_hist, w.hist, (size_t)(so.iters + 1) * 8, cudaMemcpyDeviceToHost, st));
+  if ((rc = stage_out(h, w.x, xt, x, dt, st))) return rc;
+  CK(cudaStreamSynchronize(st));
+  if (resid_hist && so.bnorm == 0.0) resid_hist[0] = 0.0;
+  if (iters) *iters = so.iters;
+  if ((rc = join(st, us, h->ev))) return rc;
+  if (so.status == S7_EBREAKDOWN) return fail(S7_EBREAKDOWN, "BiCGStab breakdown after %d steps", so.iters);
+  if (so.status == S7_ENOTCONV) return fail(S7_ENOTCONV, "not converged in %d steps", so.iters);
+  return S7_OK;
+}
+
+// ---------------------------------------------------------------------------
+// float64 iterative refinement around low-precision inner solves
+// ---------------------------------------------------------------------------
+extern "C" int bicgstab_solve_refined(stencil7_t h, const double* b, double* x, double tol,
+                                      int max_outer, int inner_maxit, double inner_tol,
+                                      int* outer, int* inner_total, double* hist, void* stream) {
+  if (!h || !b || !x) return fail(S7_EINVAL, "bicgstab_solve_refined: NULL argument");
+  if (max_outer < 0 || inner_maxit < 1 || !(tol >= 0) || !(inner_tol > 0))
+    return fail(S7_EINVAL, "bicgstab_solve_refined: bad tolerances or limits");
+  if ((h->storage == S7_BF16 || h->storage == S7_F16) && !h->keep_true)
+    return fail(S7_EINVAL, "bicgstab_solve_refined: 16-bit storage needs keep_true");
+  int rc;
+  if ((rc = ensure_ws(h, inner_maxit))) return rc;
+  Workspace& w = h->ws;
+  const Engine* eng = engine_for(h->storage);
+  const size_t n = (size_t)h->n;
+  cudaStream_t us = (cudaStream_t)stream, st = h->stream;
+  if ((rc = join(us, st, h->ev))) return rc;
+  if (!w.ref_x && (rc = dmalloc(h, &w.ref_x, n * 8))) return rc;
+  if (!w.ref_b && (rc = dmalloc(h, &w.ref_b, n * 8))) return rc;
+  if (!w.ref_r && (rc = dmalloc(h, &w.ref_r, n * 8))) return rc;
+  CK(cudaMemcpyAsync(w.ref_b, b, n * 8, cudaMemcpyDefault, st));
+  CK(cudaMemcpyAsync(w.ref_x, x, n * 8, cudaMemcpyDefault, st));
+  const int grid = grid_for((long long)n);
+  int total = 0, k = 0, status = S7_ENOTCONV;
+  for (k = 0;; ++k) {
+    double rn = 0, bn = 0;
+    if ((rc = raw_resid_dev(h, w.ref_b, w.ref_x, w.ref_r, S7_F64, &rn, &bn, st))) return rc;
+    const double rel = bn > 0 ? rn / bn : rn;
+    if (hist) hist[k] = rel;
+    if (rel <= tol) { status = S7_OK; break; }
+    if (k >= max_outer) { status = S7_ENOTCONV; break; }
+    // inner right-hand side with unit RMS
+    const double s = rn / sqrt((double)n);
+    if (h->storage == S7_F64)
+      k_scaled_copy<double><<<grid, 256, 0, st>>>((long long)n, (const double*)w.ref_r, 1.0 / s, (double*)w.b);
+    else
+      k_scaled_copy<float><<<grid, 256, 0, st>>>((long long)n, (const double*)w.ref_r, 1.0 / s, (float*)w.b);
+    CK(cudaGetLastError());
+    CK(cudaMemsetAsync(w.x, 0, n * eng->x_size, st));
+    SolveOut so;
+    if ((rc = solve_core(h, w.b, inner_tol, inner_maxit, &so))) return rc;
+    total += so.iters;
+    if (so.status == S7_EBREAKDOWN && so.iters == 0) { status = S7_EBREAKDOWN; break; }
+    if (h->storage == S7_F64)
+      k_axpy_f64<double><<<grid, 256, 0, st>>>((long long)n, s, (const double*)w.x, (double*)w.ref_x);
+    else
+      k_axpy_f64<float><<<grid, 256, 0, st>>>((long long)n, s, (const float*)w.x, (double*)w.ref_x);
+    CK(cudaGetLastError());
+  }
+  CK(cudaMemcpyAsync(x, w.ref_x, n * 8, cudaMemcpyDefault, st));
+  CK(cudaStreamSynchronize(st));
+  if (outer) *outer = k;
+  if (inner_total) *inner_total = total;
+  if ((rc = join(st, us, h->ev))) return rc;
+  if (status == S7_EBREAKDOWN) return fail(status, "inner solve broke down at outer step %d", k);
+  if (status == S7_ENOTCONV) return fail(status, "refinement not converged in %d outer steps", k);
+  return S7_OK;
+}

@@ -1,0 +1,196 @@
+// Device helpers shared by the stencil sweeps and the pointwise kernels:
+// element types and conversions, 16-byte vector loads/stores, deterministic
+// block reductions and the last-block grid combine that stands in for the
+// paper's AllReduce (Sec. IV-C): per-block partial sums written to global
+// memory, then summed in a fixed order in float64 by whichever block
+// finishes last.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+namespace s7 {
+
+typedef __nv_bfloat16 bf16;
+typedef __half f16;
+
+// ---------------------------------------------------------------------------
+// conversions (all rounding is round-to-nearest-even)
+// ---------------------------------------------------------------------------
+template <class A> __device__ __forceinline__ A to_acc(float v);
+template <> __device__ __forceinline__ float to_acc<float>(float v) { return v; }
+template <> __device__ __forceinline__ double to_acc<double>(float v) { return (double)v; }
+
+template <class A> __device__ __forceinline__ A to_acc(double v);
+template <> __device__ __forceinline__ double to_acc<double>(double v) { return v; }
+template <> __device__ __forceinline__ float to_acc<float>(double v) { return (float)v; }
+
+template <class A> __device__ __forceinline__ A to_acc(bf16 v) { return (A)__bfloat162float(v); }
+template <class A> __device__ __forceinline__ A to_acc(f16 v) { return (A)__half2float(v); }
+
+template <class T> __device__ __forceinline__ T from_acc(float v);
+template <> __device__ __forceinline__ float from_acc<float>(float v) { return v; }
+template <> __device__ __forceinline__ double from_acc<double>(float v) { return (double)v; }
+template <> __device__ __forceinline__ bf16 from_acc<bf16>(float v) { return __float2bfloat16_rn(v); }
+template <> __device__ __forceinline__ f16 from_acc<f16>(float v) { return __float2half_rn(v); }
+
+template <class T> __device__ __forceinline__ T from_acc(double v);
+template <> __device__ __forceinline__ double from_acc<double>(double v) { return v; }
+template <> __device__ __forceinline__ float from_acc<float>(double v) { return (float)v; }
+template <> __device__ __forceinline__ bf16 from_acc<bf16>(double v) { return __double2bfloat16(v); }
+template <> __device__ __forceinline__ f16 from_acc<f16>(double v) { return __double2half(v); }
+
+// ---------------------------------------------------------------------------
+// vector loads / stores of VEC consecutive elements (VEC*sizeof(T) <= 16 B,
+// address aligned to that size)
+// ---------------------------------------------------------------------------
+template <int BYTES> struct Raw;
+template <> struct Raw<16> { typedef uint4 t; };
+template <> struct Raw<8> { typedef uint2 t; };
+template <> struct Raw<4> { typedef unsigned int t; };
+template <> struct Raw<2> { typedef unsigned short t; };
+
+template <class T> struct Bits { typedef T t; };
+template <> struct Bits<bf16> { typedef unsigned short t; };
+template <> struct Bits<f16> { typedef unsigned short t; };
+
+template <class T, class B> __device__ __forceinline__ T from_bits(B b) { return b; }
+template <> __device__ __forceinline__ bf16 from_bits<bf16, unsigned short>(unsigned short b) {
+  return __ushort_as_bfloat16(b);
+}
+template <> __device__ __forceinline__ f16 from_bits<f16, unsigned short>(unsigned short b) {
+  return __ushort_as_half(b);
+}
+template <class T> __device__ __forceinline__ typename Bits<T>::t to_bits(T v) { return v; }
+template <> __device__ __forceinline__ unsigned short to_bits<bf16>(bf16 v) { return __bfloat16_as_ushort(v); }
+template <> __device__ __forceinline__ unsigned short to_bits<f16>(f16 v) { return __half_as_ushort(v); }
+
+// Cache policy of a load: default (L1+L2), or streaming (read once, evict
+// first) for coefficient arrays that no other block reads.
+enum { LD_DEFAULT = 0, LD_STREAM = 1 };
+
+template <int POL, class R> __device__ __forceinline__ R ld_raw(const R* p) {
+  if (POL == LD_STREAM) return __ldcs(p);
+  return *p;
+}
+
+// Elements per memory transaction: at most 16 bytes.
+template <class T, int VEC> struct Chunk {
+  static constexpr int n = (VEC * (int)sizeof(T) > 16) ? (16 / (int)sizeof(T)) : VEC;
+};
+
+template <class T, int VEC, int POL = LD_DEFAULT, class A>
+__device__ __forceinline__ void ldv(const T* __restrict__ p, A (&o)[VEC]) {
+  constexpr int CH = Chunk<T, VEC>::n;
+  typedef typename Raw<CH * sizeof(T)>::t R;
+  typedef typename Bits<T>::t B;
+#pragma unroll
+  for (int c = 0; c < VEC / CH; ++c) {
+    union { R r; B b[CH]; } u;
+    u.r = ld_raw<POL>(reinterpret_cast<const R*>(p + c * CH));
+#pragma unroll
+    for (int k = 0; k < CH; ++k) o[c * CH + k] = to_acc<A>(from_bits<T>(u.b[k]));
+  }
+}
+
+template <class T, int VEC, bool STREAM = false, class A>
+__device__ __forceinline__ void stv(T* __restrict__ p, const A (&v)[VEC]) {
+  constexpr int CH = Chunk<T, VEC>::n;
+  typedef typename Raw<CH * sizeof(T)>::t R;
+  typedef typename Bits<T>::t B;
+#pragma unroll
+  for (int c = 0; c < VEC / CH; ++c) {
+    union { R r; B b[CH]; } u;
+#pragma unroll
+    for (int k = 0; k < CH; ++k) u.b[k] = to_bits<T>(from_acc<T>(v[c * CH + k]));
+    if (STREAM) __stcs(reinterpret_cast<R*>(p + c * CH), u.r);
+    else *reinterpret_cast<R*>(p + c * CH) = u.r;
+  }
+}
+
+// Element-wise masked variants for rows whose start is not vector aligned.
+template <class T, int VEC, class A>
+__device__ __forceinline__ void lds(const T* __restrict__ p, int nvalid, A (&o)[VEC]) {
+#pragma unroll
+  for (int k = 0; k < VEC; ++k) o[k] = (k < nvalid) ? to_acc<A>(p[k]) : A(0);
+}
+template <class T, int VEC, class A>
+__device__ __forceinline__ void sts(T* __restrict__ p, int nvalid, const A (&v)[VEC]) {
+#pragma unroll
+  for (int k = 0; k < VEC; ++k)
+    if (k < nvalid) p[k] = from_acc<T>(v[k]);
+}
+
+// ---------------------------------------------------------------------------
+// deterministic reductions
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum NV values over the block in a fixed order (float64).  `sh` needs
+// NV * 32 doubles.  The result is valid in thread 0.
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double* sh) {
+  const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+  const int nt = blockDim.x * blockDim.y * blockDim.z;
+  const int lane = tid & 31, warp = tid >> 5, nw = (nt + 31) >> 5;
+#pragma unroll
+  for (int j = 0; j < NV; ++j) v[j] = warp_sum(v[j]);
+  __syncthreads();  // sh may alias memory used just before
+  if (lane == 0)
+#pragma unroll
+    for (int j = 0; j < NV; ++j) sh[j * 32 + warp] = v[j];
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+      double t = lane < nw ? sh[j * 32 + lane] : 0.0;
+      v[j] = warp_sum(t);
+    }
+  }
+}
+
+// Last-block grid combine.  Every block calls this once with its block sums
+// (valid in thread 0).  Block `bid` of `nblocks` stores them to
+// parts[j*nblocks + bid]; the block that arrives last sums all partials in a
+// fixed order (so the totals do not depend on which block is last) and gets
+// true back, with the totals in thread 0's `tot`.  The counter is reset for
+// the next use.  `sh` needs NV * 32 doubles.
+template <int NV>
+__device__ __forceinline__ bool grid_combine(double* parts, unsigned int* counter, int nblocks,
+                                             int bid, const double (&v)[NV], double (&tot)[NV],
+                                             double* sh) {
+  __shared__ int s_last;
+  const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+  const int nt = blockDim.x * blockDim.y * blockDim.z;
+  if (tid == 0) {
+#pragma unroll
+    for (int j = 0; j < NV; ++j) parts[(size_t)j * nblocks + bid] = v[j];
+    __threadfence();
+    unsigned int t = atomicAdd(counter, 1u);
+    s_last = (t == (unsigned int)nblocks - 1u);
+  }
+  __syncthreads();
+  if (!s_last) return false;
+  __threadfence();
+  double acc[NV];
+#pragma unroll
+  for (int j = 0; j < NV; ++j) {
+    acc[j] = 0.0;
+    for (int i = tid; i < nblocks; i += nt) acc[j] += __ldcg(parts + (size_t)j * nblocks + i);
+  }
+  block_sum<NV>(acc, sh);
+  if (tid == 0) {
+#pragma unroll
+    for (int j = 0; j < NV; ++j) tot[j] = acc[j];
+    *counter = 0u;
+  }
+  return true;
+}
+
+}  // namespace s7

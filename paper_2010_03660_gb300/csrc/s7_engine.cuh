@@ -1,0 +1,401 @@
+// Per-precision engine: the pointwise kernels (x/r update with fused inner
+// products, coefficient scaling, casts) and the host functions that launch
+// every kernel of one storage type.  Included once per storage type by
+// s7_engine_<type>.cu, which instantiates EngineImpl for its types.
+#pragma once
+
+#include <algorithm>
+
+#include "s7_handle.h"
+#include "s7_sweep.cuh"
+
+namespace s7 {
+
+// ---------------------------------------------------------------------------
+// x_{i+1} = x_i + alpha p_i + omega q_i;  r_{i+1} = q_i - omega y_i;
+// (r0, r_{i+1}) and (r_{i+1}, r_{i+1}) reduced;  beta_i, rho, history and
+// the stopping test in the last block (Algorithm 1, lines after omega).
+// ---------------------------------------------------------------------------
+__device__ inline void finish_step(Scalars* sc, double rho_new, double rr, double* hist) {
+  const int it = sc->iter + 1;
+  const double h = sqrt(rr) / sc->bnorm;
+  if (hist) hist[it] = h;
+  sc->iter = it;
+  sc->res[2] = h;
+  if (sc->special) {
+    sc->status = (h <= sc->tol) ? 0 : 3;
+    sc->done = 1;
+  } else if (h <= sc->tol) {
+    sc->status = 0;
+    sc->done = 1;
+  } else if (rho_new == 0.0 || !isfinite(rho_new)) {
+    sc->status = 3;
+    sc->done = 1;
+  } else {
+    sc->beta = (sc->alpha / sc->omega) * (rho_new / sc->rho);
+    sc->rho = rho_new;
+    if (it >= sc->maxit) {
+      sc->status = 4;
+      sc->done = 1;
+    }
+  }
+}
+
+template <class T, class X, class A, int VEC>
+__global__ void __launch_bounds__(256) k_update(long long n, const T* p0, const T* p1,
+                                                const T* s0, const T* s1,
+                                                const T* __restrict__ y, const T* __restrict__ rh,
+                                                T* __restrict__ r, X* __restrict__ x, Scalars* sc,
+                                                double* parts, double* hist) {
+  __shared__ double red[32 * 4];
+  if (*((volatile int*)&sc->done)) return;
+  const int it = sc->iter;
+  const T* __restrict__ p = (it & 1) ? p1 : p0;
+  const T* __restrict__ s = (it & 1) ? s1 : s0;
+  const A alpha = (A)sc->alpha, omega = (A)sc->omega;
+  DotAcc<A, 2> acc;
+  acc.init();
+  const long long nvec = n / VEC;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  int cnt = 0;
+  for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < nvec; v += stride) {
+    const long long i = v * VEC;
+    A pv[VEC], sv[VEC], yv[VEC], rv[VEC], hv[VEC], xv[VEC];
+    ldv<T, VEC, LD_STREAM>(r + i, rv);
+    ldv<T, VEC, LD_STREAM>(s + i, sv);
+    ldv<T, VEC, LD_STREAM>(p + i, pv);
+    ldv<T, VEC, LD_STREAM>(y + i, yv);
+    ldv<T, VEC, LD_STREAM>(rh + i, hv);
+    ldv<X, VEC, LD_STREAM>(x + i, xv);
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) {
+      const A q = q_of(rv[k], sv[k], alpha);
+      xv[k] = fma(omega, q, fma(alpha, pv[k], xv[k]));
+      const A rn = as_stored<T>(fma(-omega, yv[k], q));
+      rv[k] = rn;
+      acc.part[0] = fma(hv[k], rn, acc.part[0]);
+      acc.part[1] = fma(rn, rn, acc.part[1]);
+    }
+    stv<X, VEC, true>(x + i, xv);
+    stv<T, VEC, true>(r + i, rv);
+    if (++cnt == 8) {
+      acc.fold();
+      cnt = 0;
+    }
+  }
+  if (blockIdx.x == 0) {
+    for (long long i = nvec * VEC + threadIdx.x; i < n; i += blockDim.x) {
+      const A rv = to_acc<A>(r[i]), sv = to_acc<A>(s[i]);
+      const A q = q_of(rv, sv, alpha);
+      x[i] = from_acc<X>(fma(omega, q, fma(alpha, to_acc<A>(p[i]), to_acc<A>(x[i]))));
+      const A rn = as_stored<T>(fma(-omega, to_acc<A>(y[i]), q));
+      r[i] = from_acc<T>(rn);
+      acc.part[0] = fma(to_acc<A>(rh[i]), rn, acc.part[0]);
+      acc.part[1] = fma(rn, rn, acc.part[1]);
+    }
+  }
+  acc.fold();
+  double vv[2] = {acc.tot[0], acc.tot[1]}, tot[2];
+  block_sum<2>(vv, red);
+  if (grid_combine<2>(parts, &sc->counter[CNT_C], gridDim.x, blockIdx.x, vv, tot, red) &&
+      threadIdx.x == 0)
+    finish_step(sc, tot[0], tot[1], hist);
+}
+
+// Coefficient scaling to a unit diagonal (Sec. IV): out = c / diag computed
+// in float64 and rounded once to the storage type; or a plain rounding when
+// the raw operator is kept.
+template <class RT, class T>
+__global__ void k_scale(long long n, const RT* __restrict__ c, const RT* __restrict__ diag,
+                        T* __restrict__ out, int jacobi) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const double cv = (double)c[i];
+    out[i] = from_acc<T>(jacobi ? cv / (double)diag[i] : cv);
+  }
+}
+
+// Kept diagonal (for b~ = D^-1 b) and a count of unusable entries.
+template <class RT, class DT>
+__global__ void k_keep_diag(long long n, const RT* __restrict__ diag, DT* __restrict__ out,
+                            unsigned int* bad) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  unsigned int nbad = 0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const double dv = (double)diag[i];
+    if (dv == 0.0 || !isfinite(dv)) ++nbad;
+    if (out) out[i] = from_acc<DT>(dv);
+  }
+  if (nbad) atomicAdd(bad, nbad);
+}
+
+template <class S, class D>
+__global__ void k_cast(long long n, const S* __restrict__ src, D* __restrict__ dst) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+    dst[i] = from_acc<D>(to_acc<double>(src[i]));
+}
+
+template <class V> __global__ void k_fill(long long n, V* dst, V v) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) dst[i] = v;
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+inline int pointwise_grid(long long n, int per_thread) {
+  int dev = 0, nsm = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  long long want = (n + 256LL * per_thread - 1) / (256LL * per_thread);
+  long long cap = (long long)nsm * 8;
+  return (int)std::max(1LL, std::min(want, cap));
+}
+
+inline Geom make_geom(const Handle* h, int vec) {
+  Geom g;
+  g.nx = h->nx;
+  g.ny = h->ny;
+  g.nz = h->nz;
+  g.bx = h->tile.bx;
+  g.by = h->tile.by;
+  const int runs = (h->nx + vec - 1) / vec;
+  if (g.bx > runs) g.bx = runs;
+  g.tiles_x = (runs + g.bx - 1) / g.bx;
+  g.tiles_y = (h->ny + g.by - 1) / g.by;
+  g.zchunk = h->tile.zchunk;
+  g.nchunks = (h->nz + g.zchunk - 1) / g.zchunk;
+  g.plane = (long long)h->nx * h->ny;
+  return g;
+}
+
+inline bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+template <class CT, class A, int VEC, class Src, class Epi>
+int launch_sweep(const Geom& g, const CoefView<CT, A>& cf, const Src& src, const Epi& epi,
+                 Scalars* sc, bool vl, cudaStream_t st) {
+  const int threads = ((g.bx * g.by + 31) / 32) * 32;
+  const size_t smem = (size_t)3 * (g.by + 2) * (g.bx * VEC + 2 * VEC) * sizeof(A);
+  void (*kern)(Geom, CoefView<CT, A>, Src, Epi, Scalars*) =
+      vl ? k_sweep<CT, A, VEC, true, Src, Epi> : k_sweep<CT, A, VEC, false, Src, Epi>;
+  if (smem > 48 * 1024) {
+    if (cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+      return S7_ECUDA;
+  }
+  kern<<<s7_nblocks(g), threads, smem, st>>>(g, cf, src, epi, sc);
+  return cudaGetLastError() == cudaSuccess ? S7_OK : S7_ECUDA;
+}
+
+template <class T_, class X_, class DT_, class A_>
+struct EngineImpl {
+  typedef T_ T;
+  typedef X_ X;
+  typedef DT_ DT;
+  typedef A_ A;
+  static constexpr int VEC = 16 / (int)sizeof(T);
+
+  template <class AA>
+  static CoefView<T, AA> stored(const Handle* h) {
+    CoefView<T, AA> cf;
+    for (int d = 0; d < 6; ++d) {
+      cf.c[d] = (const T*)h->c[d];
+      cf.cc[d] = (AA)h->cconst[d];
+    }
+    cf.constant = h->constant;
+    cf.diag = h->jacobi ? nullptr : (const T*)h->diag;
+    cf.cdiag = h->jacobi ? AA(1) : (AA)h->cconst[6];
+    return cf;
+  }
+
+  static int scale(Handle* h, const void* const raw[7], s7_dtype raw_dt, cudaStream_t st, int* bad) {
+    const long long n = h->n;
+    const int grid = pointwise_grid(n, 4);
+    unsigned int* d_bad = (unsigned int*)h->small;
+    cudaMemsetAsync(d_bad, 0, sizeof(unsigned int), st);
+#define S7_SCALE(RT)                                                                              \
+  {                                                                                               \
+    const RT* dg = (const RT*)raw[6];                                                             \
+    k_keep_diag<RT, DT><<<grid, 256, 0, st>>>(n, dg, (DT*)h->d, d_bad);                           \
+    for (int d = 0; d < 6; ++d)                                                                   \
+      k_scale<RT, T><<<grid, 256, 0, st>>>(n, (const RT*)raw[d], dg, (T*)h->c[d], h->jacobi);      \
+    if (!h->jacobi) k_scale<RT, T><<<grid, 256, 0, st>>>(n, dg, dg, (T*)h->diag, 0);              \
+    for (int d = 0; d < 7 && h->keep_true; ++d)                                                   \
+      k_cast<RT, float><<<grid, 256, 0, st>>>(n, (const RT*)raw[d], h->tc[d]);                     \
+  }
+    if (raw_dt == S7_F64) S7_SCALE(double) else S7_SCALE(float)
+#undef S7_SCALE
+    unsigned int hb = 0;
+    cudaMemcpyAsync(&hb, d_bad, sizeof hb, cudaMemcpyDeviceToHost, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess) return S7_ECUDA;
+    *bad = (int)hb;
+    return cudaGetLastError() == cudaSuccess ? S7_OK : S7_ECUDA;
+  }
+
+  static int apply(Handle* h, const void* x, void* y, cudaStream_t st) {
+    const Geom g = make_geom(h, VEC);
+    SrcPlain<T, A> src{(const T*)x};
+    EpiStore<T, A> epi{(T*)y};
+    const bool vl = (h->nx % VEC == 0) && aligned16(x) && aligned16(y);
+    return launch_sweep<T, A, VEC>(g, stored<A>(h), src, epi, nullptr, vl, st);
+  }
+
+  static int init(Handle* h, const void* b, cudaStream_t st) {
+    const Geom g = make_geom(h, VEC);
+    Workspace& w = h->ws;
+    SrcPlain<X, A> src{(const X*)w.x};
+    EpiResid<X, T, DT, A> epi;
+    epi.b = (const X*)b;
+    epi.dinv = (h->jacobi && !h->constant) ? (const DT*)h->d : nullptr;
+    epi.dc = (h->jacobi && h->constant) ? (A)h->cconst[6] : A(1);
+    epi.dmul = nullptr;
+    epi.dmc = A(1);
+    epi.r_out = (T*)w.r;
+    epi.rh_out = (T*)w.rh;
+    epi.parts = w.parts;
+    epi.counter = CNT_INIT;
+    epi.mode = 0;
+    const bool vl = (h->nx % VEC == 0) && aligned16(b);
+    return launch_sweep<T, A, VEC>(g, stored<A>(h), src, epi, w.sc, vl, st);
+  }
+
+  static int step_kernel(Handle* h, int which, cudaStream_t st) {
+    const Geom g = make_geom(h, VEC);
+    Workspace& w = h->ws;
+    const CoefView<T, A> cf = stored<A>(h);
+    const bool vl = (h->nx % VEC == 0);
+    if (which == 0) {
+      SrcPUpdate<T, A> sa;
+      sa.r = (const T*)w.r;
+      sa.pbuf[0] = (T*)w.p[0];
+      sa.pbuf[1] = (T*)w.p[1];
+      sa.sbuf[0] = (T*)w.s[0];
+      sa.sbuf[1] = (T*)w.s[1];
+      EpiS<T, A> ea;
+      ea.sbuf[0] = (T*)w.s[0];
+      ea.sbuf[1] = (T*)w.s[1];
+      ea.rh = (const T*)w.rh;
+      ea.parts = w.parts;
+      return launch_sweep<T, A, VEC>(g, cf, sa, ea, w.sc, vl, st);
+    }
+    if (which == 1) {
+      SrcQ<T, A> sb;
+      sb.r = (const T*)w.r;
+      sb.sbuf[0] = (T*)w.s[0];
+      sb.sbuf[1] = (T*)w.s[1];
+      EpiY<T, A> eb;
+      eb.y_out = (T*)w.y;
+      eb.parts = w.parts;
+      return launch_sweep<T, A, VEC>(g, cf, sb, eb, w.sc, vl, st);
+    }
+    k_update<T, X, A, VEC><<<pointwise_grid(h->n / VEC + 1, 1), 256, 0, st>>>(
+        h->n, (const T*)w.p[0], (const T*)w.p[1], (const T*)w.s[0], (const T*)w.s[1],
+        (const T*)w.y, (const T*)w.rh, (T*)w.r, (X*)w.x, w.sc, w.parts, w.hist);
+    return cudaGetLastError() == cudaSuccess ? S7_OK : S7_ECUDA;
+  }
+
+  // ||b~ - A~ x|| and ||b~|| with float64 accumulation -> sc->res[0], res[1].
+  static int true_resid(Handle* h, const void* b, cudaStream_t st) {
+    const Geom g = make_geom(h, VEC);
+    Workspace& w = h->ws;
+    SrcPlain<X, double> src{(const X*)w.x};
+    EpiResid<X, T, DT, double> epi;
+    epi.b = (const X*)b;
+    epi.dinv = (h->jacobi && !h->constant) ? (const DT*)h->d : nullptr;
+    epi.dc = (h->jacobi && h->constant) ? h->cconst[6] : 1.0;
+    epi.dmul = nullptr;
+    epi.dmc = 1.0;
+    epi.r_out = nullptr;
+    epi.rh_out = nullptr;
+    epi.parts = w.parts;
+    epi.counter = CNT_RES;
+    epi.mode = 1;
+    const bool vl = (h->nx % VEC == 0) && aligned16(b);
+    return launch_sweep<T, double, VEC>(g, stored<double>(h), src, epi, w.sc, vl, st);
+  }
+
+  template <class XT>
+  static int raw_resid_t(Handle* h, const XT* b, const XT* x, XT* r, cudaStream_t st) {
+    Workspace& w = h->ws;
+    if (h->keep_true) {
+      constexpr int V = 16 / (int)sizeof(XT) < 4 ? 16 / (int)sizeof(XT) : 4;
+      const Geom g = make_geom(h, V);
+      CoefView<float, double> cf;
+      for (int d = 0; d < 6; ++d) {
+        cf.c[d] = h->tc[d];
+        cf.cc[d] = 0.0;
+      }
+      cf.diag = h->tc[6];
+      cf.cdiag = 1.0;
+      cf.constant = 0;
+      SrcPlain<XT, double> src{x};
+      EpiResid<XT, XT, float, double> epi;
+      epi.b = b;
+      epi.dinv = nullptr;
+      epi.dc = 1.0;
+      epi.dmul = nullptr;
+      epi.dmc = 1.0;
+      epi.r_out = r;
+      epi.rh_out = nullptr;
+      epi.parts = w.parts;
+      epi.counter = CNT_RES;
+      epi.mode = 1;
+      const bool vl = (h->nx % V == 0) && aligned16(b) && aligned16(x) && (!r || aligned16(r));
+      return launch_sweep<float, double, V>(g, cf, src, epi, w.sc, vl, st);
+    }
+    const Geom g = make_geom(h, VEC);
+    SrcPlain<XT, double> src{x};
+    EpiResid<XT, XT, DT, double> epi;
+    epi.b = b;
+    epi.dinv = nullptr;
+    epi.dc = 1.0;
+    epi.dmul = (h->jacobi && !h->constant) ? (const DT*)h->d : nullptr;
+    epi.dmc = (h->jacobi && h->constant) ? h->cconst[6] : 1.0;
+    epi.r_out = r;
+    epi.rh_out = nullptr;
+    epi.parts = w.parts;
+    epi.counter = CNT_RES;
+    epi.mode = 1;
+    const bool vl = (h->nx % VEC == 0) && aligned16(b) && aligned16(x) && (!r || aligned16(r));
+    return launch_sweep<T, double, VEC>(g, stored<double>(h), src, epi, w.sc, vl, st);
+  }
+
+  static int raw_resid(Handle* h, const void* b, const void* x, void* r, s7_dtype dt, cudaStream_t st) {
+    if (dt == S7_F64) return raw_resid_t<double>(h, (const double*)b, (const double*)x, (double*)r, st);
+    return raw_resid_t<float>(h, (const float*)b, (const float*)x, (float*)r, st);
+  }
+
+  static int cast(const void* src, s7_dtype sdt, void* dst, s7_dtype ddt, long long n, cudaStream_t st) {
+    const int grid = pointwise_grid(n, 4);
+    if (sdt == S7_F64 && ddt == S7_F32)
+      k_cast<double, float><<<grid, 256, 0, st>>>(n, (const double*)src, (float*)dst);
+    else if (sdt == S7_F32 && ddt == S7_F64)
+      k_cast<float, double><<<grid, 256, 0, st>>>(n, (const float*)src, (double*)dst);
+    else
+      return S7_EINVAL;
+    return cudaGetLastError() == cudaSuccess ? S7_OK : S7_ECUDA;
+  }
+
+  static size_t parts_needed(const Handle* h) {
+    size_t m = 0;
+    const int vecs[3] = {VEC, 2, 4};
+    for (int v : vecs) m = std::max(m, (size_t)s7_nblocks(make_geom(h, v)));
+    m = std::max(m, (size_t)pointwise_grid(h->n / VEC + 1, 1));
+    return 4 * m;
+  }
+
+  static int smem_ok(const Handle* h) {
+    const Geom g = make_geom(h, VEC);
+    const size_t smem = (size_t)3 * (g.by + 2) * (g.bx * VEC + 2 * VEC) * sizeof(double);
+    return smem <= 200 * 1024 && g.bx * g.by <= 512;
+  }
+
+  static const Engine* get() {
+    static const Engine e = {sizeof(T), sizeof(X), sizeof(DT), VEC, &scale, &apply, &init, &step_kernel,
+                             &true_resid, &raw_resid, &cast, &parts_needed, &smem_ok};
+    return &e;
+  }
+};
+
+}  // namespace s7

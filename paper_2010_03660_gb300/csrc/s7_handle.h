@@ -1,0 +1,105 @@
+// Host-side handle and workspace layout shared by the C ABI and the
+// per-precision engines.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/stencil7.h"
+
+namespace s7 {
+
+struct Scalars;
+
+// Krylov workspace of one handle (allocated on first solve, reused).
+struct Workspace {
+  void* r = nullptr;
+  void* rh = nullptr;      // shadow residual r0_hat
+  void* p[2] = {nullptr, nullptr};
+  void* s[2] = {nullptr, nullptr};
+  void* y = nullptr;
+  void* x = nullptr;       // iterate (float64 or float32)
+  void* b = nullptr;       // right-hand side in the iterate's type
+  void* stage = nullptr;   // staging for host / other-typed inputs
+  double* parts = nullptr; // grid-combine partials
+  size_t parts_n = 0;
+  double* hist = nullptr;  // device residual history
+  int hist_cap = 0;
+  Scalars* sc = nullptr;   // device scalars
+  Scalars* h_sc = nullptr; // pinned host mirror
+  void* ref_x = nullptr;   // float64 iterate of the refined solver
+  void* ref_b = nullptr;   // float64 right-hand side of the refined solver
+  void* ref_r = nullptr;   // float64 true residual of the refined solver
+  cudaGraphExec_t graph = nullptr;
+  int graph_steps = 0;
+  bool ready = false;
+};
+
+// Launch shape of the sweeps.
+struct Tile {
+  int bx, by, zchunk;
+};
+
+struct Handle {
+  int nx, ny, nz;
+  long long n;
+  s7_dtype storage;
+  int jacobi;       // 1: stored operator is D^-1 A (unit diagonal)
+  int keep_true;
+  int constant;
+  int device;
+  // stored operator (element type = storage)
+  void* c[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  void* diag = nullptr;       // raw diagonal (no_jacobi) in storage type
+  double cconst[7] = {0, 0, 0, 0, 0, 0, 0};  // constant scaled coefficients; [6] = diag
+  void* d = nullptr;          // kept diagonal for b scaling (float64 / float32)
+  float* tc[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // raw float32
+  Tile tile;
+  int check_every;
+  size_t bytes = 0;           // device bytes held
+  void* small = nullptr;      // 256 bytes of device scratch (flags)
+  cudaStream_t stream = nullptr;   // private stream (captures, solves)
+  cudaEvent_t ev = nullptr;
+  Workspace ws;
+  // per-kernel timing (stencil7_profile)
+  int prof = 0;
+  double prof_ms[S7_PROF_NKINDS] = {0, 0, 0, 0, 0, 0};
+  long long prof_n[S7_PROF_NKINDS] = {0, 0, 0, 0, 0, 0};
+  cudaEvent_t* prof_ev = nullptr;   // event pool, pairs
+  int prof_ev_cap = 0, prof_ev_used = 0;
+  int* prof_kind = nullptr;         // kind of each pending pair
+};
+
+// Per-precision engine: launches kernels for one storage type.
+struct Engine {
+  size_t t_size;   // storage element size
+  size_t x_size;   // iterate element size (8 or 4)
+  size_t d_size;   // kept-diagonal element size
+  int vec;         // cells per thread in the sweeps
+  // scale raw coefficients (device, dtype raw_dt) into the handle
+  int (*scale)(Handle* h, const void* const raw[7], s7_dtype raw_dt, cudaStream_t st, int* bad);
+  int (*apply)(Handle* h, const void* x, void* y, cudaStream_t st);
+  int (*init)(Handle* h, const void* b, cudaStream_t st);
+  // one kernel of a BiCGStab step: 0 = p update + s = A p + (r0,s);
+  // 1 = q + y = A q + (q,y),(y,y); 2 = x, r updates + (r0,r),(r,r)
+  int (*step_kernel)(Handle* h, int which, cudaStream_t st);
+  int (*true_resid)(Handle* h, const void* b, cudaStream_t st);
+  int (*raw_resid)(Handle* h, const void* b, const void* x, void* r, s7_dtype dt, cudaStream_t st);
+  int (*cast)(const void* src, s7_dtype sdt, void* dst, s7_dtype ddt, long long n, cudaStream_t st);
+  size_t (*parts_needed)(const Handle* h);
+  int (*smem_ok)(const Handle* h);
+};
+
+const Engine* engine_f64();
+const Engine* engine_f32();
+const Engine* engine_bf16();
+const Engine* engine_f16();
+
+// Shape of the sweep grid for a handle (same for every sweep of the handle).
+void default_tile(int nx, int ny, int nz, int vec, int nsm, Tile* t);
+
+}  // namespace s7
+
+// The opaque handle type of the C ABI.
+struct stencil7_op : public s7::Handle {};

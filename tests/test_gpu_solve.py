@@ -1,0 +1,186 @@
+"""GPU parity of bicgstab_solve against the FP64 oracle (Algorithm 1).
+
+Both sides run Algorithm 1 on the same stored operator (A~ = D^-1 A rounded
+to the storage type) and the same right-hand side, with the same stopping
+rule.  Bars: FP64 storage agrees with the oracle to rounding (iteration
+counts equal, history and x to ~1e-9); FP32 solves to 1e-6 agree in x within
+1e-4 relative (the float32 recurrence drifts from the float64 one, so
+iteration counts may differ by a few steps).
+"""
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import bicgstab as ob
+from oracle import stencil
+from tests import gpu_util as gu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def s7():
+    import paper_2010_03660_gb300 as m
+    m.lib()
+    return m
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+
+
+def test_config1_fp64_constant_convdiff_32cubed(s7):
+    """32^3 convection-diffusion, FP64, tol 1e-8, maxit 500."""
+    p = synth.convdiff_constant(32, 32, 32, seed=0)
+    orc = ob.bicgstab(32, 32, 32, p.coef, p.b, tol=1e-8, maxit=500, storage="f64")
+    with s7.stencil7_create(32, 32, 32, p.coef, storage="f64") as op:
+        res = s7.bicgstab_solve(op, gu.to_dev(p.b), tol=1e-8, maxit=500)
+        x = res.x.cpu().numpy()
+    assert res.status == 0 and orc.status == 0
+    assert res.iters == orc.iters
+    assert np.max(np.abs(res.hist - orc.hist) / orc.hist) < 1e-7
+    assert rel(x, orc.x) < 1e-9
+    assert res.true_resid <= 1.01e-8 and abs(res.true_resid - orc.true_resid) < 1e-10
+
+
+@pytest.mark.parametrize("shape", [(64, 48, 40), (61, 37, 29), (17, 9, 33), (1, 1, 50)])
+def test_fp32_varcoef_solve(s7, shape):
+    nx, ny, nz = shape
+    p = synth.varcoef(nx, ny, nz, seed=21)
+    orc = ob.bicgstab(nx, ny, nz, p.coef, p.b, tol=1e-6, maxit=1000, storage="f32")
+    with s7.stencil7_create(nx, ny, nz, gu.coef_on_device(p), storage="f32") as op:
+        res = s7.bicgstab_solve(op, gu.to_dev(p.b), tol=1e-6, maxit=1000)
+        x = res.x.cpu().numpy()
+    assert res.status == 0
+    assert res.hist[-1] <= 1e-6 and res.hist[0] == pytest.approx(1.0, rel=1e-6)
+    assert abs(res.iters - orc.iters) <= max(3, orc.iters // 10)
+    assert rel(x, orc.x) <= 1e-4
+    assert res.true_resid <= 2e-6
+    # the residual reported by the oracle for the GPU's x agrees
+    sc = stencil.jacobi_scale(nx, ny, nz, p.coef, "f32")
+    bt = stencil.scale_rhs(nx, ny, nz, p.coef, p.b)
+    tr = np.linalg.norm(bt - stencil.apply(nx, ny, nz, sc, x.astype(np.float64))) / np.linalg.norm(bt)
+    assert abs(tr - res.true_resid) <= 1e-3 * tr + 1e-9
+
+
+def test_fp64_varcoef_matches_oracle_step_by_step(s7):
+    nx, ny, nz = 45, 30, 26
+    p = synth.varcoef(nx, ny, nz, seed=5, dtype=np.float64)
+    orc = ob.bicgstab(nx, ny, nz, p.coef, p.b, tol=1e-10, maxit=400, storage="f64")
+    with s7.stencil7_create(nx, ny, nz, gu.coef_on_device(p), storage="f64") as op:
+        res = s7.bicgstab_solve(op, gu.to_dev(p.b), tol=1e-10, maxit=400)
+    assert res.iters == orc.iters
+    assert np.max(np.abs(res.hist - orc.hist) / orc.hist) < 1e-6
+    assert rel(res.x.cpu().numpy(), orc.x) < 1e-8
+
+
+def test_general_x0_and_degenerate_cases(s7):
+    import torch
+    nx, ny, nz = 20, 10, 12
+    p = synth.varcoef(nx, ny, nz, seed=31, dtype=np.float64)
+    x0 = synth.random_vector(p.n, 4, 4, np.float64)
+    orc = ob.bicgstab(nx, ny, nz, p.coef, p.b, x0=x0, tol=1e-9, maxit=300)
+    with s7.stencil7_create(nx, ny, nz, gu.coef_on_device(p), storage="f64") as op:
+        res = s7.bicgstab_solve(op, gu.to_dev(p.b), gu.to_dev(x0), tol=1e-9, maxit=300)
+        assert res.iters == orc.iters and rel(res.x.cpu().numpy(), orc.x) < 1e-8
+        assert res.hist[0] == pytest.approx(orc.hist[0], rel=1e-10)
+        # b = 0: x = 0 after zero steps, whatever x0
+        z = torch.zeros(p.n, dtype=torch.float64, device="cuda:0")
+        r0 = s7.bicgstab_solve(op, z, gu.to_dev(x0), tol=1e-8, maxit=10)
+        assert r0.iters == 0 and r0.status == 0 and float(r0.x.abs().max()) == 0.0
+        # exact start: no step
+        xe = gu.to_dev(orc.x)
+        r1 = s7.bicgstab_solve(op, gu.to_dev(p.b), xe, tol=1e-8, maxit=10)
+        assert r1.iters == 0 and r1.status == 0
+        # maxit reached: NOTCONV with a full history
+        r2 = s7.bicgstab_solve(op, gu.to_dev(p.b), tol=1e-30, maxit=7)
+        assert r2.status == s7.ENOTCONV and r2.iters == 7 and len(r2.hist) == 8
+        o2 = ob.bicgstab(nx, ny, nz, p.coef, p.b, tol=1e-30, maxit=7)
+        assert np.max(np.abs(r2.hist - o2.hist) / o2.hist) < 1e-9
+        # maxit = 0
+        r3 = s7.bicgstab_solve(op, gu.to_dev(p.b), tol=1e-8, maxit=0)
+        assert r3.iters == 0 and r3.status == s7.ENOTCONV
+
+
+def test_single_cell_and_single_row(s7):
+    c1 = {"diag": 2.5, **{d: 0.0 for d in synth.DIRS}}
+    with s7.stencil7_create(1, 1, 1, c1, storage="f64") as op:
+        res = s7.bicgstab_solve(op, gu.to_dev(np.array([5.0])), tol=1e-12, maxit=5)
+        assert res.status == 0 and res.x.item() == pytest.approx(2.0)
+    p = synth.varcoef(1, 1, 40, seed=2, dtype=np.float64)
+    orc = ob.bicgstab(1, 1, 40, p.coef, p.b, tol=1e-12, maxit=200)
+    with s7.stencil7_create(1, 1, 40, gu.coef_on_device(p), storage="f64") as op:
+        res = s7.bicgstab_solve(op, gu.to_dev(p.b), tol=1e-12, maxit=200)
+    assert res.iters == orc.iters and rel(res.x.cpu().numpy(), orc.x) < 1e-10
+
+
+def test_host_buffers_and_mixed_types(s7):
+    nx, ny, nz = 30, 21, 17
+    p = synth.varcoef(nx, ny, nz, seed=41)
+    with s7.stencil7_create(nx, ny, nz, p.coef, storage="f32") as op:
+        rh = s7.bicgstab_solve(op, p.b.copy(), tol=1e-6, maxit=500)            # numpy f32
+        rd = s7.bicgstab_solve(op, gu.to_dev(p.b), tol=1e-6, maxit=500)       # torch f32
+        r64 = s7.bicgstab_solve(op, p.b.astype(np.float64), tol=1e-6, maxit=500)  # numpy f64
+    assert rh.iters == rd.iters == r64.iters
+    assert np.array_equal(rh.x, rd.x.cpu().numpy())
+    assert np.array_equal(rh.x.astype(np.float64), r64.x)
+
+
+def test_solves_are_deterministic(s7):
+    nx, ny, nz = 50, 41, 37
+    p = synth.varcoef(nx, ny, nz, seed=42)
+    with s7.stencil7_create(nx, ny, nz, gu.coef_on_device(p), storage="f32") as op:
+        a = s7.bicgstab_solve(op, gu.to_dev(p.b), tol=1e-7, maxit=500)
+        b = s7.bicgstab_solve(op, gu.to_dev(p.b), tol=1e-7, maxit=500)
+    assert a.iters == b.iters
+    assert np.array_equal(a.hist, b.hist)
+    assert np.array_equal(a.x.cpu().numpy(), b.x.cpu().numpy())
+
+
+def test_graph_step_count_does_not_change_results(s7):
+    nx, ny, nz = 40, 33, 21
+    p = synth.varcoef(nx, ny, nz, seed=43)
+    outs = []
+    for ce in (1, 3, 16):
+        with s7.stencil7_create(nx, ny, nz, gu.coef_on_device(p), storage="f32",
+                                check_every=ce) as op:
+            outs.append(s7.bicgstab_solve(op, gu.to_dev(p.b), tol=1e-6, maxit=500))
+    for o in outs[1:]:
+        assert o.iters == outs[0].iters
+        assert np.array_equal(o.x.cpu().numpy(), outs[0].x.cpu().numpy())
+
+
+def test_residual_entry_point(s7):
+    nx, ny, nz = 26, 19, 15
+    p = synth.varcoef(nx, ny, nz, seed=44)
+    x = synth.random_vector(p.n, 9, 1, np.float32)
+    ref = p.b.astype(np.float64) - stencil.apply(nx, ny, nz, p.coef, x.astype(np.float64))
+    for keep in (True, False):
+        with s7.stencil7_create(nx, ny, nz, gu.coef_on_device(p), storage="f32",
+                                keep_true=keep) as op:
+            r = gu.to_dev(np.zeros(p.n, np.float32))
+            rn, bn = s7.stencil7_residual(op, gu.to_dev(p.b), gu.to_dev(x), r)
+            rr = r.cpu().numpy().astype(np.float64)
+        den = stencil.abs_apply(nx, ny, nz, p.coef, x) + np.abs(p.b)
+        tol = 1e-6 if keep else 1e-5     # without keep_true A is rebuilt from rounded A~ and d
+        assert np.max(np.abs(rr - ref) / den) < tol
+        assert rn == pytest.approx(np.linalg.norm(ref), rel=tol * 10)
+        assert bn == pytest.approx(np.linalg.norm(p.b.astype(np.float64)), rel=1e-12)
+
+
+@pytest.mark.parametrize("storage", ["bf16", "f16", "f32"])
+def test_refined_solve_reaches_1e10(s7, storage):
+    nx, ny, nz = 48, 40, 36
+    p = synth.varcoef(nx, ny, nz, seed=2)
+    b64 = p.b.astype(np.float64)
+    # oracle: the same (float32-coefficient) system solved in float64
+    orc = ob.bicgstab(nx, ny, nz, p.coef, b64, tol=1e-13, maxit=2000, storage="f64")
+    with s7.stencil7_create(nx, ny, nz, gu.coef_on_device(p), storage=storage,
+                            keep_true=True) as op:
+        res = s7.bicgstab_solve_refined(op, gu.to_dev(b64), tol=1e-10, max_outer=40,
+                                        inner_maxit=100, inner_tol=1e-2)
+        x = res.x.cpu().numpy()
+    assert res.status == 0 and res.hist[-1] <= 1e-10
+    assert ob.true_residual(nx, ny, nz, p.coef, b64, x) <= 1.5e-10
+    assert rel(x, orc.x) < 1e-8
