@@ -9,6 +9,8 @@
 #include <algorithm>
 #include <new>
 
+#include <cuda.h>
+
 #include "s7_handle.h"
 #include "s7_sweep.cuh"
 
@@ -75,6 +77,37 @@ static bool on_device(const void* p) {
     return false;
   }
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// The library carries its own CUDA runtime.  A caller (for instance PyTorch)
+// selects a device by making that device's primary context current on the
+// thread; bind this runtime to the same device before any work.
+typedef CUresult (*CtxGetDeviceFn)(CUdevice*);
+
+static void bind_caller_device() {
+  static CtxGetDeviceFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetDevice", (void**)&fn, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      fn = nullptr;
+    cudaGetLastError();
+  }
+  CUdevice d;
+  if (fn && fn(&d) == CUDA_SUCCESS) {
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess || cur != (int)d) cudaSetDevice((int)d);
+  }
+  cudaGetLastError();
+}
+
+static void bind_handle_device(const Handle* h) {
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess || cur != h->device) cudaSetDevice(h->device);
+  cudaGetLastError();
 }
 
 static int dmalloc(Handle* h, void** p, size_t bytes) {
@@ -220,6 +253,7 @@ extern "C" int stencil7_create(stencil7_t* out, int nx, int ny, int nz, const s7
   s7_opts opts;
   memset(&opts, 0, sizeof opts);
   if (o) opts = *o;
+  bind_caller_device();
   const Engine* eng = engine_for(opts.storage);
   if (!eng) return fail(S7_EINVAL, "stencil7_create: unknown storage type %d", (int)opts.storage);
 
@@ -366,6 +400,7 @@ fail_out:
 
 extern "C" int stencil7_destroy(stencil7_t h) {
   if (!h) return S7_OK;
+  bind_handle_device(h);
   cudaStreamSynchronize(h->stream);
   release(h);
   delete h;
@@ -481,6 +516,7 @@ extern "C" int stencil7_apply(stencil7_t h, const void* x, void* y, s7_dtype dt,
     return fail(S7_EINVAL, "stencil7_apply: dt (%d) must equal the storage type (%d)", (int)dt,
                 (int)h->storage);
   if (x == y) return fail(S7_EINVAL, "stencil7_apply: x and y must not overlap");
+  bind_handle_device(h);
   const Engine* eng = engine_for(h->storage);
   cudaStream_t st = (cudaStream_t)stream;
   const bool dx = on_device(x), dy = on_device(y);
@@ -526,6 +562,7 @@ extern "C" int stencil7_residual(stencil7_t h, const void* b, const void* x, voi
                                  double* rnorm, double* bnorm, void* stream) {
   if (!h || !b || !x) return fail(S7_EINVAL, "stencil7_residual: NULL argument");
   if (dt != S7_F64 && dt != S7_F32) return fail(S7_EINVAL, "stencil7_residual: dt must be F64 or F32");
+  bind_handle_device(h);
   int rc;
   if ((rc = ensure_ws(h, 0))) return rc;
   cudaStream_t us = (cudaStream_t)stream, st = h->stream;
@@ -609,6 +646,7 @@ static void prof_free(Handle* h) {
 
 extern "C" int stencil7_profile(stencil7_t h, int enable, double* ms, long long* launches) {
   if (!h) return fail(S7_EINVAL, "stencil7_profile: NULL handle");
+  bind_handle_device(h);
   cudaStreamSynchronize(h->stream);
   prof_collect(h);
   for (int k = 0; k < S7_PROF_NKINDS; ++k) {
@@ -715,6 +753,7 @@ extern "C" int bicgstab_solve(stencil7_t h, const void* b, void* x, s7_dtype dt,
   if (!h || !b || !x) return fail(S7_EINVAL, "bicgstab_solve: NULL argument");
   if (dt != S7_F64 && dt != S7_F32) return fail(S7_EINVAL, "bicgstab_solve: dt must be F64 or F32");
   if (maxit < 0 || !(tol >= 0.0)) return fail(S7_EINVAL, "bicgstab_solve: bad tol or maxit");
+  bind_handle_device(h);
   int rc;
   if ((rc = ensure_ws(h, maxit))) return rc;
   Workspace& w = h->ws;
@@ -763,6 +802,7 @@ extern "C" int bicgstab_solve_refined(stencil7_t h, const double* b, double* x, 
     return fail(S7_EINVAL, "bicgstab_solve_refined: bad tolerances or limits");
   if ((h->storage == S7_BF16 || h->storage == S7_F16) && !h->keep_true)
     return fail(S7_EINVAL, "bicgstab_solve_refined: 16-bit storage needs keep_true");
+  bind_handle_device(h);
   int rc;
   if ((rc = ensure_ws(h, inner_maxit))) return rc;
   Workspace& w = h->ws;

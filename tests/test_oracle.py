@@ -220,6 +220,24 @@ def test_recurrence_and_true_residual_agree():
     assert res.hist[0] == pytest.approx(1.0, abs=1e-15)
 
 
+def test_history_sensitivity_to_dot_rounding(monkeypatch):
+    """BiCGStab amplifies rounding differences.  Rerunning the oracle with
+    exactly rounded inner products (math.fsum) instead of NumPy's pairwise
+    sums leaves the first steps of the residual history equal to ~1e-12 but
+    moves it by more than 1e-3 relative near convergence, while x still
+    agrees within the tolerance's bound.  GPU parity bars for solves are
+    built on this (early history tight, final x within tol-derived bounds)."""
+    p = synth.convdiff_constant(32, 32, 32, seed=0)
+    a = ob.bicgstab(32, 32, 32, p.coef, p.b, tol=1e-8, maxit=500)
+    monkeypatch.setattr(ob, "_dot", lambda u, v: math.fsum(u * v))
+    b = ob.bicgstab(32, 32, 32, p.coef, p.b, tol=1e-8, maxit=500)
+    k = min(len(a.hist), len(b.hist))
+    d = np.abs(a.hist[:k] - b.hist[:k]) / a.hist[:k]
+    assert np.max(d[:15]) < 1e-11
+    assert np.max(d) > 1e-3
+    assert np.linalg.norm(a.x - b.x) / np.linalg.norm(a.x) < 1e-7
+
+
 def test_bicgstab_general_x0():
     coef, b = rand_coef(6, 6, 6, seed=42)
     x0 = synth.random_vector(216, 9, 9, np.float64)
