@@ -139,6 +139,33 @@ int stencil7_apply(stencil7_t h, const void* x, void* y, s7_dtype dt, void* stre
 int stencil7_residual(stencil7_t h, const void* b, const void* x, void* r,
                       s7_dtype dt, double* rnorm, double* bnorm, void* stream);
 
+/* The same residual as stencil7_residual (same float64 sweep, same results),
+ * for callers that must not allocate device memory when they call: services
+ * that reserve their whole device-memory budget at start-up (a pool that owns
+ * the memory, where a cudaMalloc would fail or fragment it), latency-bound
+ * loops that cannot afford cudaMalloc's implicit synchronisation, and
+ * callers whose memory manager forbids direct cudaMalloc.  stencil7_residual
+ * sets up the handle's solver workspace (several mesh-sized vectors) on
+ * first use; this call allocates nothing.  Its scratch -- the per-block
+ * partial sums and a small block of scalars, for at most
+ * S7_NOALLOC_MAX_BLOCKS thread blocks (about 1 MiB) -- is one fixed array in
+ * device memory, held by every GPU that loads the library until the process
+ * exits.  The paper has no counterpart.
+ *   b, x, r   device memory only (r may be NULL), nx*ny*nz elements of dt
+ *             (S7_F64 or S7_F32); host buffers are rejected with S7_EINVAL.
+ *   Sizes whose sweep needs more than S7_NOALLOC_MAX_BLOCKS blocks are
+ *   rejected with S7_EINVAL (a larger opts.zchunk lowers the count).
+ * Set-up: the first call on each device looks up the device address of the
+ * scratch array (once per device, under a lock); make that first call
+ * before any stream capture.  All calls share the one array, which keeps
+ * the last call's contents; each call clears the part that must start at
+ * zero.  Calls whose work overlaps on the GPU (unordered streams or host
+ * threads) race on the array: order them.  Runs on `stream`; returns after
+ * the norms are on the host. */
+#define S7_NOALLOC_MAX_BLOCKS 65536
+int stencil7_residual_noalloc(stencil7_t h, const void* b, const void* x, void* r,
+                              s7_dtype dt, double* rnorm, double* bnorm, void* stream);
+
 /* BiCGStab (Algorithm 1) on A~ x = D^-1 b.
  *   b      nx*ny*nz elements of dt (S7_F64 or S7_F32); unchanged.
  *   x      in: start vector x0; out: the last iterate.  Same size and type.

@@ -27,8 +27,8 @@ from . import _build
 __all__ = [
     "S7_F64", "S7_F32", "S7_BF16", "S7_F16", "S7Error", "Operator", "lib", "EXPORTS",
     "stencil7_create", "stencil7_destroy", "stencil7_info", "stencil7_apply",
-    "stencil7_residual", "bicgstab_solve", "bicgstab_solve_refined", "stencil7_profile",
-    "s7_last_error", "s7_version",
+    "stencil7_residual", "stencil7_residual_noalloc", "bicgstab_solve",
+    "bicgstab_solve_refined", "stencil7_profile", "s7_last_error", "s7_version",
 ]
 
 S7_F64, S7_F32, S7_BF16, S7_F16 = 0, 1, 2, 3
@@ -41,8 +41,8 @@ _STORAGE = {"f64": S7_F64, "f32": S7_F32, "bf16": S7_BF16, "f16": S7_F16}
 # Entry points declared in include/stencil7.h (checked by the tests).
 EXPORTS = (
     "stencil7_create", "stencil7_destroy", "stencil7_info", "stencil7_apply",
-    "stencil7_residual", "bicgstab_solve", "bicgstab_solve_refined", "stencil7_profile",
-    "s7_last_error", "s7_version",
+    "stencil7_residual", "stencil7_residual_noalloc", "bicgstab_solve",
+    "bicgstab_solve_refined", "stencil7_profile", "s7_last_error", "s7_version",
 )
 PROF_KINDS = ("spmv_p_dot", "spmv_q_dots", "update_dots", "start_residual", "true_residual",
               "other")
@@ -91,6 +91,7 @@ def lib():
         "stencil7_info": (i, [vp, P(i), P(i), P(i), P(i), P(C.c_size_t)]),
         "stencil7_apply": (i, [vp, vp, vp, i, vp]),
         "stencil7_residual": (i, [vp, vp, vp, vp, i, P(d), P(d), vp]),
+        "stencil7_residual_noalloc": (i, [vp, vp, vp, vp, i, P(d), P(d), vp]),
         "bicgstab_solve": (i, [vp, vp, vp, i, d, i, P(i), P(d), P(d), vp]),
         "bicgstab_solve_refined": (i, [vp, vp, vp, d, i, i, d, P(i), P(i), P(d), vp]),
         "stencil7_profile": (i, [vp, i, P(d), P(C.c_longlong)]),
@@ -290,6 +291,15 @@ def stencil7_profile(op, enable):
     n = (C.c_longlong * 6)()
     _check(lib().stencil7_profile(op.handle, 1 if enable else 0, ms, n))
     return {k: (ms[j], n[j]) for j, k in enumerate(PROF_KINDS)}
+
+
+def stencil7_residual_noalloc(op, b, x, r=None):
+    """:func:`stencil7_residual` without any allocation (device buffers only);
+    for callers that may not allocate device memory at call time."""
+    rn, bn = C.c_double(), C.c_double()
+    _check(lib().stencil7_residual_noalloc(op.handle, _ptr(b), _ptr(x), _ptr(r), _dtype_code(b),
+                                           C.byref(rn), C.byref(bn), _stream(b, x, r)))
+    return rn.value, bn.value
 
 
 @dataclass

@@ -41,6 +41,10 @@ static int cuda_fail(cudaError_t e, const char* what) {
   } while (0)
 
 extern "C" const char* s7_last_error(void) { return g_err; }
+
+namespace s7 {
+int set_error(int code, const char* msg) { return fail(code, "%s", msg); }
+}  // namespace s7
 extern "C" const char* s7_version(void) { return "stencil7-gb300 0.1 (sm_103a)"; }
 
 // ---------------------------------------------------------------------------

@@ -366,6 +366,65 @@ struct EngineImpl {
     return raw_resid_t<float>(h, (const float*)b, (const float*)x, (float*)r, st);
   }
 
+  // The raw-system residual sweep with caller-supplied combine scratch.
+  template <class XT>
+  static int raw_resid_into_t(Handle* h, const XT* b, const XT* x, XT* r, double* parts,
+                              Scalars* sc, cudaStream_t st) {
+    const bool al = aligned16(b) && aligned16(x) && (!r || aligned16(r));
+    EpiResid<XT, XT, DT, double> epi;
+    epi.b = b;
+    epi.dinv = nullptr;
+    epi.dc = 1.0;
+    epi.r_out = r;
+    epi.rh_out = nullptr;
+    epi.parts = parts;
+    epi.counter = CNT_RES;
+    epi.mode = 1;
+    SrcPlain<XT, double> src{x};
+    if (h->keep_true) {
+      constexpr int V = 16 / (int)sizeof(XT) < 4 ? 16 / (int)sizeof(XT) : 4;
+      const Geom g = make_geom(h, V);
+      CoefView<float, double> cf;
+      for (int d = 0; d < 6; ++d) {
+        cf.c[d] = h->tc[d];
+        cf.cc[d] = 0.0;
+      }
+      cf.diag = h->tc[6];
+      cf.cdiag = 1.0;
+      cf.constant = 0;
+      EpiResid<XT, XT, float, double> e2;
+      e2.b = b;
+      e2.dinv = nullptr;
+      e2.dc = 1.0;
+      e2.dmul = nullptr;
+      e2.dmc = 1.0;
+      e2.r_out = r;
+      e2.rh_out = nullptr;
+      e2.parts = parts;
+      e2.counter = CNT_RES;
+      e2.mode = 1;
+      return launch_sweep<float, double, V>(g, cf, src, e2, sc, (h->nx % V == 0) && al, st);
+    }
+    const Geom g = make_geom(h, VEC);
+    epi.dmul = (h->jacobi && !h->constant) ? (const DT*)h->d : nullptr;
+    epi.dmc = (h->jacobi && h->constant) ? h->cconst[6] : 1.0;
+    return launch_sweep<T, double, VEC>(g, stored<double>(h), src, epi, sc,
+                                        (h->nx % VEC == 0) && al, st);
+  }
+
+  static int raw_resid_into(Handle* h, const void* b, const void* x, void* r, s7_dtype dt,
+                            double* parts, Scalars* sc, cudaStream_t st) {
+    if (dt == S7_F64)
+      return raw_resid_into_t<double>(h, (const double*)b, (const double*)x, (double*)r, parts,
+                                      sc, st);
+    return raw_resid_into_t<float>(h, (const float*)b, (const float*)x, (float*)r, parts, sc, st);
+  }
+
+  static long long raw_resid_blocks(const Handle* h, s7_dtype dt) {
+    const int v = h->keep_true ? (dt == S7_F64 ? 2 : 4) : VEC;
+    return s7_nblocks(make_geom(h, v));
+  }
+
   static int cast(const void* src, s7_dtype sdt, void* dst, s7_dtype ddt, long long n, cudaStream_t st) {
     const int grid = pointwise_grid(n, 4);
     if (sdt == S7_F64 && ddt == S7_F32)
@@ -393,7 +452,8 @@ struct EngineImpl {
 
   static const Engine* get() {
     static const Engine e = {sizeof(T), sizeof(X), sizeof(DT), VEC, &scale, &apply, &init, &step_kernel,
-                             &true_resid, &raw_resid, &cast, &parts_needed, &smem_ok};
+                             &true_resid, &raw_resid, &cast, &parts_needed, &smem_ok,
+                             &raw_resid_into, &raw_resid_blocks};
     return &e;
   }
 };

@@ -89,12 +89,20 @@ struct Engine {
   int (*cast)(const void* src, s7_dtype sdt, void* dst, s7_dtype ddt, long long n, cudaStream_t st);
   size_t (*parts_needed)(const Handle* h);
   int (*smem_ok)(const Handle* h);
+  // raw_resid with the grid-combine partials and scalars in memory the
+  // caller supplies, and the number of blocks (partials per value) it uses
+  int (*raw_resid_into)(Handle* h, const void* b, const void* x, void* r, s7_dtype dt,
+                        double* parts, Scalars* sc, cudaStream_t st);
+  long long (*raw_resid_blocks)(const Handle* h, s7_dtype dt);
 };
 
 const Engine* engine_f64();
 const Engine* engine_f32();
 const Engine* engine_bf16();
 const Engine* engine_f16();
+
+// Record `msg` as the calling thread's error text; returns `code`.
+int set_error(int code, const char* msg);
 
 // Shape of the sweep grid for a handle (same for every sweep of the handle).
 void default_tile(int nx, int ny, int nz, int vec, int nsm, Tile* t);
