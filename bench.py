@@ -66,6 +66,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-nz", type=int, default=24)
     ap.add_argument("--cpu-sample-iters", type=int, default=10)
+    ap.add_argument("--bx", type=int, default=0, help="sweep tile width in threads (0 = tuned)")
+    ap.add_argument("--by", type=int, default=0, help="sweep tile rows (0 = tuned)")
+    ap.add_argument("--zchunk", type=int, default=0, help="z planes per block (0 = tuned)")
     ap.add_argument("--ref-sample-nz", type=int, default=8)
     ap.add_argument("--ref-sample-iters", type=int, default=5)
     return ap.parse_args()
@@ -248,7 +251,8 @@ def run_ours(args):
     prob = synth.varcoef(nx, ny, nz, seed=rank, dtype=raw)
     gen_s = time.time() - t0
     coef_d = {k: torch.from_numpy(v).to(dev) for k, v in prob.coef.items()}
-    op = s7.stencil7_create(nx, ny, nz, coef_d, storage=args.storage)
+    op = s7.stencil7_create(nx, ny, nz, coef_d, storage=args.storage, bx=args.bx, by=args.by,
+                            zchunk=args.zchunk)
     del coef_d
     torch.cuda.empty_cache()
     b = torch.from_numpy(prob.b).to(dev)

@@ -106,6 +106,12 @@ typedef struct {
   int zchunk;        /* z planes per thread block in the sweeps; 0 = default  */
   int check_every;   /* iterations per CUDA-graph launch between host checks
                         of the device convergence flag; 0 = default            */
+  int stages;        /* depth of the asynchronous-copy pipeline of the two SpMV
+                        sweeps of a step: 2 or 3 shared-memory stages; 1 = no
+                        pipeline (direct loads); 0 = default                   */
+  int pipe_kinds;    /* which sweeps use that pipeline: bit 0 = the p-update +
+                        s = A p sweep, bit 1 = the q + y = A q sweep;
+                        0 = default (tuned)                                    */
 } s7_opts;
 
 /* Create an operator handle.  Copies the coefficients to library-owned device

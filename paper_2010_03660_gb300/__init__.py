@@ -63,7 +63,7 @@ class s7_coeffs(C.Structure):
 class s7_opts(C.Structure):
     _fields_ = [("storage", C.c_int), ("no_jacobi", C.c_int), ("keep_true", C.c_int),
                 ("bx", C.c_int), ("by", C.c_int), ("zchunk", C.c_int),
-                ("check_every", C.c_int)]
+                ("check_every", C.c_int), ("stages", C.c_int), ("pipe_kinds", C.c_int)]
 
 
 _lib = None
@@ -216,7 +216,8 @@ class Operator:
 
 
 def stencil7_create(nx, ny, nz, coef, storage="f32", jacobi=True, keep_true=False,
-                    bx=0, by=0, zchunk=0, check_every=0, constant=None):
+                    bx=0, by=0, zchunk=0, check_every=0, constant=None, stages=0,
+                    pipe_kinds=0):
     """Create an operator from raw coefficients.
 
     ``coef`` maps ``diag, xm, xp, ym, yp, zm, zp`` to arrays/tensors of
@@ -248,7 +249,8 @@ def stencil7_create(nx, ny, nz, coef, storage="f32", jacobi=True, keep_true=Fals
     cs = s7_coeffs(ptrs["diag"], ptrs["xm"], ptrs["xp"], ptrs["ym"], ptrs["yp"],
                    ptrs["zm"], ptrs["zp"], raw_dt, 1 if constant else 0)
     st = _STORAGE[storage] if isinstance(storage, str) else int(storage)
-    op = s7_opts(st, 0 if jacobi else 1, 1 if keep_true else 0, bx, by, zchunk, check_every)
+    op = s7_opts(st, 0 if jacobi else 1, 1 if keep_true else 0, bx, by, zchunk, check_every,
+                 stages, pipe_kinds)
     h = C.c_void_p()
     _check(lib().stencil7_create(C.byref(h), nx, ny, nz, C.byref(cs), C.byref(op)))
     del keep

@@ -173,7 +173,7 @@ void default_tile(int nx, int ny, int nz, int vec, int nsm, Tile* t) {
   const int runs = (nx + vec - 1) / vec;
   const int ntx = (runs + 31) / 32;
   int bx = (runs + ntx - 1) / ntx;          // <= 32 runs per row, balanced tiles
-  int by = std::max(1, std::min(ny, 256 / std::max(1, bx)));
+  int by = std::max(1, std::min(ny, 128 / std::max(1, bx)));
   if (by > 16) by = 16;
   while (bx * by > 512) --by;
   const long long tiles = (long long)ntx * ((ny + by - 1) / by);
@@ -286,6 +286,11 @@ extern "C" int stencil7_create(stencil7_t* out, int nx, int ny, int nz, const s7
     int ce = (int)std::min(64.0, std::max(2.0, 1000.0 / est_us));
     h->check_every = opts.check_every > 0 ? opts.check_every : ce;
   }
+  h->stages = opts.stages > 0 ? std::min(opts.stages, 3) : 2;
+  // measured on GB300 (600x595 planes, f32): the pipeline helps the p/s
+  // sweep, whose register version is limited by occupancy, and not the
+  // q/y sweep
+  h->pipe_kinds = opts.pipe_kinds > 0 ? (opts.pipe_kinds & 3) : 1;
   if (!eng->smem_ok(h)) {
     delete h;
     return fail(S7_EINVAL, "stencil7_create: tile too large for shared memory");
@@ -682,6 +687,7 @@ static int capture_graph(Handle* h) {
   Workspace& w = h->ws;
   const Engine* eng = engine_for(h->storage);
   if (w.graph) return S7_OK;
+  if (eng->prepare_capture(h)) return cuda_fail(cudaGetLastError(), "kernel attributes");
   cudaGraph_t g = nullptr;
   CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
   int rc = S7_OK;

@@ -7,6 +7,7 @@
 #include <algorithm>
 
 #include "s7_handle.h"
+#include "s7_step.cuh"
 #include "s7_sweep.cuh"
 
 namespace s7 {
@@ -172,6 +173,24 @@ inline Geom make_geom(const Handle* h, int vec) {
 
 inline bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
+// Allow `smem` bytes of dynamic shared memory for `kern`.  While `st` is
+// being captured into a graph the attribute cannot be set; the solve driver
+// sets it for the step kernels (prepare_capture) before it captures.
+// Static shared memory of the sweep kernels is about 1 KB (reduction
+// scratch); the opt-in is needed once static + dynamic exceeds 48 KB.
+constexpr size_t kSmemNoOptIn = 48 * 1024 - 4096;
+
+inline int allow_smem(const void* kern, size_t smem, cudaStream_t st) {
+  if (smem <= kSmemNoOptIn) return S7_OK;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) return S7_ECUDA;
+  if (cs != cudaStreamCaptureStatusNone) return S7_OK;
+  return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) ==
+                 cudaSuccess
+             ? S7_OK
+             : S7_ECUDA;
+}
+
 template <class CT, class A, int VEC, class Src, class Epi>
 int launch_sweep(const Geom& g, const CoefView<CT, A>& cf, const Src& src, const Epi& epi,
                  Scalars* sc, bool vl, cudaStream_t st) {
@@ -179,11 +198,7 @@ int launch_sweep(const Geom& g, const CoefView<CT, A>& cf, const Src& src, const
   const size_t smem = (size_t)3 * (g.by + 2) * (g.bx * VEC + 2 * VEC) * sizeof(A);
   void (*kern)(Geom, CoefView<CT, A>, Src, Epi, Scalars*) =
       vl ? k_sweep<CT, A, VEC, true, Src, Epi> : k_sweep<CT, A, VEC, false, Src, Epi>;
-  if (smem > 48 * 1024) {
-    if (cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess)
-      return S7_ECUDA;
-  }
+  if (allow_smem((const void*)kern, smem, st)) return S7_ECUDA;
   kern<<<s7_nblocks(g), threads, smem, st>>>(g, cf, src, epi, sc);
   return cudaGetLastError() == cudaSuccess ? S7_OK : S7_ECUDA;
 }
@@ -260,11 +275,72 @@ struct EngineImpl {
     return launch_sweep<T, A, VEC>(g, stored<A>(h), src, epi, w.sc, vl, st);
   }
 
+  // The pipelined sweeps serve the common case: Jacobi-scaled per-cell
+  // coefficients, rows of whole 16-byte vectors, at most 256 threads.
+  static bool pipelined(const Handle* h, const Geom& g, int kind) {
+    return h->stages >= 2 && ((h->pipe_kinds >> kind) & 1) && h->jacobi && !h->constant &&
+           h->nx % VEC == 0 &&
+           g.bx * g.by <= 256 &&
+           step_smem_bytes<T, A, VEC>(g.bx, g.by, h->stages, kind) <= 200 * 1024;
+  }
+
+  template <int KIND, int STAGES>
+  static int launch_step(const Handle* h, const Geom& g, cudaStream_t st) {
+    const Workspace& w = h->ws;
+    StepArgs<T> a;
+    for (int d = 0; d < 6; ++d) a.c[d] = (const T*)h->c[d];
+    a.r = (const T*)w.r;
+    a.rh = (const T*)w.rh;
+    a.pbuf[0] = (T*)w.p[0];
+    a.pbuf[1] = (T*)w.p[1];
+    a.sbuf[0] = (T*)w.s[0];
+    a.sbuf[1] = (T*)w.s[1];
+    a.y = (T*)w.y;
+    a.parts = w.parts;
+    const size_t smem = step_smem_bytes<T, A, VEC>(g.bx, g.by, STAGES, KIND);
+    void (*kern)(Geom, StepArgs<T>, Scalars*) = k_step<T, A, VEC, KIND, STAGES>;
+    if (allow_smem((const void*)kern, smem, st)) return S7_ECUDA;
+    const int threads = ((g.bx * g.by + 31) / 32) * 32;
+    kern<<<s7_nblocks(g), threads, smem, st>>>(g, a, w.sc);
+    return cudaGetLastError() == cudaSuccess ? S7_OK : S7_ECUDA;
+  }
+
+  // Shared-memory attributes of the step kernels, set outside any capture.
+  static int prepare_capture(Handle* h) {
+    const Geom g = make_geom(h, VEC);
+    int rc = S7_OK;
+    auto set = [&](const void* k, size_t bytes) {
+      if (bytes > kSmemNoOptIn &&
+          cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
+              cudaSuccess)
+        rc = S7_ECUDA;
+    };
+    for (int kind = 0; kind < 2; ++kind) {
+      if (!pipelined(h, g, kind)) continue;
+      const size_t b = step_smem_bytes<T, A, VEC>(g.bx, g.by, h->stages, kind);
+      if (h->stages == 3)
+        set(kind == 0 ? (const void*)k_step<T, A, VEC, 0, 3> : (const void*)k_step<T, A, VEC, 1, 3>, b);
+      else
+        set(kind == 0 ? (const void*)k_step<T, A, VEC, 0, 2> : (const void*)k_step<T, A, VEC, 1, 2>, b);
+    }
+    const size_t gb = (size_t)3 * (g.by + 2) * (g.bx * VEC + 2 * VEC) * sizeof(A);
+    set((const void*)k_sweep<T, A, VEC, true, SrcPUpdate<T, A>, EpiS<T, A>>, gb);
+    set((const void*)k_sweep<T, A, VEC, false, SrcPUpdate<T, A>, EpiS<T, A>>, gb);
+    set((const void*)k_sweep<T, A, VEC, true, SrcQ<T, A>, EpiY<T, A>>, gb);
+    set((const void*)k_sweep<T, A, VEC, false, SrcQ<T, A>, EpiY<T, A>>, gb);
+    return rc;
+  }
+
   static int step_kernel(Handle* h, int which, cudaStream_t st) {
     const Geom g = make_geom(h, VEC);
     Workspace& w = h->ws;
     const CoefView<T, A> cf = stored<A>(h);
     const bool vl = (h->nx % VEC == 0);
+    if (which < 2 && pipelined(h, g, which)) {
+      if (which == 0)
+        return h->stages == 3 ? launch_step<0, 3>(h, g, st) : launch_step<0, 2>(h, g, st);
+      return h->stages == 3 ? launch_step<1, 3>(h, g, st) : launch_step<1, 2>(h, g, st);
+    }
     if (which == 0) {
       SrcPUpdate<T, A> sa;
       sa.r = (const T*)w.r;
@@ -453,7 +529,7 @@ struct EngineImpl {
   static const Engine* get() {
     static const Engine e = {sizeof(T), sizeof(X), sizeof(DT), VEC, &scale, &apply, &init, &step_kernel,
                              &true_resid, &raw_resid, &cast, &parts_needed, &smem_ok,
-                             &raw_resid_into, &raw_resid_blocks};
+                             &raw_resid_into, &raw_resid_blocks, &prepare_capture};
     return &e;
   }
 };

@@ -57,6 +57,8 @@ struct Handle {
   float* tc[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // raw float32
   Tile tile;
   int check_every;
+  int stages;                 // step-sweep pipeline depth (1 = direct loads)
+  int pipe_kinds;             // bit k: sweep k of a step uses the pipeline
   size_t bytes = 0;           // device bytes held
   void* small = nullptr;      // 256 bytes of device scratch (flags)
   cudaStream_t stream = nullptr;   // private stream (captures, solves)
@@ -94,6 +96,8 @@ struct Engine {
   int (*raw_resid_into)(Handle* h, const void* b, const void* x, void* r, s7_dtype dt,
                         double* parts, Scalars* sc, cudaStream_t st);
   long long (*raw_resid_blocks)(const Handle* h, s7_dtype dt);
+  // set kernel attributes the step kernels need, before graph capture
+  int (*prepare_capture)(Handle* h);
 };
 
 const Engine* engine_f64();

@@ -1,0 +1,349 @@
+// Pipelined step sweeps: the two SpMV kernels of a BiCGStab step with their
+// inputs staged through shared memory by asynchronous copies.
+//
+// Same arithmetic and the same z march as k_sweep (s7_sweep.cuh), but every
+// global read of plane z+1 (the six coefficient tiles, r0_hat, and the
+// inputs of the on-the-fly vector with a one-cell halo ring) is issued with
+// cp.async into a STAGES-deep ring of shared-memory stages while plane z is
+// computed.  No register holds an in-flight load, so a block keeps whole
+// planes of loads in flight at modest register use.
+//
+// Stage k (for output plane z = z0 + k) holds: coef(z), r0_hat(z) and the
+// inputs at plane z+1 (rows y0-1 .. y0+by, each the aligned span
+// [x0-VEC, x0+bx*VEC+VEC), so the x halo cells come from the neighbouring
+// 16-byte vectors).  Cells outside the mesh are zero-filled by the copy.
+//
+// Barriers: one per plane.  At step k a thread waits for its own copies of
+// stage k, then __syncthreads() makes all of stage k and the vector plane z
+// (produced at step k-1) visible; it then refills the stage buffer that
+// held stage k-1 (fully consumed before the barrier), forms plane z+1 into
+// the 3-buffer vector ring, and computes plane z from the ring buffer
+// written at step k-1.
+#pragma once
+
+#include "s7_sweep.cuh"
+
+namespace s7 {
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+
+// 16-byte asynchronous global->shared copy; `bytes` = 16 copies, 0 zero-fills.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, int bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_u32(dst)), "l"(src),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+
+// Pointers of one pipelined sweep.  KIND 0: p_i = r + beta (p_{i-1} - omega
+// s_{i-1}) formed on the fly, s_i = A p_i, (r0,s_i).  KIND 1: q = r - alpha s
+// formed on the fly, y = A q, (q,y), (y,y).
+template <class T>
+struct StepArgs {
+  const T* c[6];
+  const T* r;
+  const T* rh;
+  T* pbuf[2];
+  T* sbuf[2];
+  T* y;
+  double* parts;
+};
+
+template <class T, int VEC>
+struct StepLayout {
+  int TW, W, rows;     // tile width (elements), padded row pitch, rows incl. halo
+  int coef_sz, rh_sz, in_sz, stage_sz;  // in elements of T
+};
+
+template <class T, int VEC>
+__host__ __device__ inline StepLayout<T, VEC> step_layout(int bx, int by, int nin, bool rh) {
+  StepLayout<T, VEC> L;
+  L.TW = bx * VEC;
+  L.W = L.TW + 2 * VEC;
+  L.rows = by + 2;
+  L.coef_sz = 6 * by * L.TW;
+  L.rh_sz = rh ? by * L.TW : 0;
+  L.in_sz = nin * L.rows * L.W;
+  L.stage_sz = L.coef_sz + L.rh_sz + L.in_sz;
+  return L;
+}
+
+template <class T, class A, int VEC>
+__host__ __device__ inline size_t step_smem_bytes(int bx, int by, int stages, int kind) {
+  const StepLayout<T, VEC> L = step_layout<T, VEC>(bx, by, kind == 0 ? 3 : 2, kind == 0);
+  const size_t st = (size_t)L.stage_sz * sizeof(T);
+  const size_t ring = (size_t)3 * L.rows * L.W * sizeof(A);
+  return (size_t)stages * st + ring;
+}
+
+template <class T, class A, int VEC, int KIND, int STAGES>
+__global__ void __launch_bounds__(256) k_step(Geom g, StepArgs<T> a, Scalars* sc) {
+  extern __shared__ __align__(16) unsigned char s7_smem[];
+  __shared__ double red[32 * 4];
+  if (*((volatile int*)&sc->done)) return;
+
+  const int it = sc->iter;
+  const bool odd = (it & 1) != 0;
+  const bool first = (KIND == 0) && it == 0;
+  const A beta = (A)sc->beta, omega = (A)sc->omega, alpha = (A)sc->alpha;
+  // inputs of the on-the-fly vector
+  const T* in0 = a.r;
+  const T* in1 = (KIND == 0) ? (odd ? a.pbuf[0] : a.pbuf[1]) : (odd ? a.sbuf[1] : a.sbuf[0]);
+  const T* in2 = (KIND == 0) ? (odd ? a.sbuf[0] : a.sbuf[1]) : nullptr;
+  const int nin = (KIND == 0) ? (first ? 1 : 3) : 2;
+  T* p_out = odd ? a.pbuf[1] : a.pbuf[0];
+  T* out = (KIND == 0) ? (odd ? a.sbuf[1] : a.sbuf[0]) : a.y;
+
+  const StepLayout<T, VEC> L = step_layout<T, VEC>(g.bx, g.by, KIND == 0 ? 3 : 2, KIND == 0);
+  T* stage0 = reinterpret_cast<T*>(s7_smem);
+  A* ring = reinterpret_cast<A*>(s7_smem + (size_t)STAGES * L.stage_sz * sizeof(T));
+  const int PL = L.rows * L.W;
+
+  const int t = threadIdx.x;
+  const bool has_cell = t < g.bx * g.by;
+  const int tx = has_cell ? t % g.bx : 0;
+  const int ty = has_cell ? t / g.bx : 0;
+  const int bid = blockIdx.x;
+  const int tile_x = bid % g.tiles_x;
+  const int rest = bid / g.tiles_x;
+  const int tile_y = rest % g.tiles_y;
+  const int chunk = rest / g.tiles_y;
+  const int x0 = tile_x * L.TW;
+  const int y0 = tile_y * g.by;
+  const int z0 = chunk * g.zchunk;
+  const int z1 = min(z0 + g.zchunk, g.nz);
+  const int x = x0 + tx * VEC;
+  const int y = y0 + ty;
+  const bool own = has_cell && y < g.ny && x < g.nx;   // full vector (nx % VEC == 0)
+  const long long row = (long long)y * g.nx + x;
+  const int so = (ty + 1) * L.W + VEC + tx * VEC;     // own element 0 in an input/ring plane
+  const int sc_own = ty * L.TW + tx * VEC;            // own element 0 in a coef/rh tile
+
+  // ---- asynchronous copy of stage `k` (output plane z0+k) into buffer `buf`.
+  // Each thread copies its own 16-byte vectors; threads on the tile edge also
+  // copy the halo vector beside them.  Every staged value a thread later
+  // reads is one it copied itself (the barrier orders buffer reuse).
+  const bool v_top = has_cell && ty == 0 && y0 > 0 && x < g.nx;
+  const bool v_bot = has_cell && ty == g.by - 1 && y + 1 < g.ny && x < g.nx;
+  const bool v_lft = has_cell && tx == 0 && x0 > 0 && y < g.ny;
+  const bool v_rgt = has_cell && tx == g.bx - 1 && x + VEC < g.nx && y < g.ny;
+  auto issue_stage = [&](int k, T* buf) {
+    if (!has_cell) return;
+    const int z = z0 + k;
+    const long long gi = own ? (long long)z * g.plane + row : 0;
+#pragma unroll
+    for (int d = 0; d < 6; ++d) cp_async16(buf + d * g.by * L.TW + sc_own, a.c[d] + gi, own ? 16 : 0);
+    if (KIND == 0) cp_async16(buf + L.coef_sz + sc_own, a.rh + gi, own ? 16 : 0);
+    const int zi = z + 1;
+    if (zi >= g.nz) return;
+    const long long gb = (long long)zi * g.plane + row;
+    T* ib = buf + L.coef_sz + L.rh_sz + so;
+    for (int sidx = 0; sidx < nin; ++sidx) {
+      const T* base = sidx == 0 ? in0 : (sidx == 1 ? in1 : in2);
+      T* d = ib + sidx * PL;
+      cp_async16(d, base + (own ? gb : 0), own ? 16 : 0);
+      if (ty == 0) cp_async16(d - L.W, base + (v_top ? gb - g.nx : 0), v_top ? 16 : 0);
+      if (ty == g.by - 1) cp_async16(d + L.W, base + (v_bot ? gb + g.nx : 0), v_bot ? 16 : 0);
+      if (tx == 0) cp_async16(d - VEC, base + (v_lft ? gb - VEC : 0), v_lft ? 16 : 0);
+      if (tx == g.bx - 1) cp_async16(d + VEC, base + (v_rgt ? gb + VEC : 0), v_rgt ? 16 : 0);
+    }
+  };
+
+  // value of the on-the-fly vector from staged inputs (index e in a plane)
+  auto form = [&](const T* inb, int e) -> A {
+    const A rv = to_acc<A>(inb[e]);
+    if (KIND == 1) return q_of(rv, to_acc<A>(inb[PL + e]), alpha);
+    if (first) return rv;
+    return as_stored<T>(fma(beta, fma(-omega, to_acc<A>(inb[2 * PL + e]), to_acc<A>(inb[PL + e])), rv));
+  };
+
+  // prologue: the vector at z0-1 (own) and z0 (own + ring) from global memory,
+  // then the first STAGES-1 stages in flight
+  A vm[VEC], vc[VEC], vp[VEC];
+  {
+    SrcPUpdate<T, A> sa;
+    SrcQ<T, A> sb;
+    if (KIND == 0) {
+      sa.r = a.r;
+      sa.pbuf[0] = a.pbuf[0];
+      sa.pbuf[1] = a.pbuf[1];
+      sa.sbuf[0] = a.sbuf[0];
+      sa.sbuf[1] = a.sbuf[1];
+      sa.setup(sc);
+    } else {
+      sb.r = a.r;
+      sb.sbuf[0] = a.sbuf[0];
+      sb.sbuf[1] = a.sbuf[1];
+      sb.setup(sc);
+    }
+    auto prod = [&](long long i, int nv, A (&v)[VEC], bool write) {
+      if (KIND == 0) sa.template produce<VEC, true>(i, nv, v, write);
+      else sb.template produce<VEC, true>(i, nv, v, write);
+    };
+    auto prod1 = [&](long long i) -> A { return KIND == 0 ? sa.produce1(i) : sb.produce1(i); };
+    if (z0 > 0 && own) prod((long long)(z0 - 1) * g.plane + row, VEC, vm, false);
+    else zero(vm);
+    A* rb = ring;
+    if (has_cell) {
+      const long long base = (long long)z0 * g.plane + row;
+      if (own) prod(base, VEC, vc, true);
+      else zero(vc);
+      sm_store<A, VEC>(rb + so, vc);
+      if (ty == 0) {
+        A h[VEC];
+        if (y0 > 0 && x < g.nx) prod(base - g.nx, VEC, h, false);
+        else zero(h);
+        sm_store<A, VEC>(rb + so - L.W, h);
+      }
+      if (ty == g.by - 1) {
+        A h[VEC];
+        if (y + 1 < g.ny && x < g.nx) prod(base + g.nx, VEC, h, false);
+        else zero(h);
+        sm_store<A, VEC>(rb + so + L.W, h);
+      }
+      if (tx == 0) rb[so - 1] = (x0 > 0 && y < g.ny) ? prod1(base - 1) : A(0);
+      if (tx == g.bx - 1) rb[so + VEC] = (x + VEC < g.nx && y < g.ny) ? prod1(base + VEC) : A(0);
+    } else {
+      zero(vc);
+    }
+  }
+  const int nsteps = z1 - z0;
+#pragma unroll
+  for (int k = 0; k < STAGES - 1; ++k) {
+    if (k < nsteps) issue_stage(k, stage0 + k * L.stage_sz);
+    cp_async_commit();
+  }
+
+  DotAcc<A, 2> acc;
+  acc.init();
+  for (int k = 0; k < nsteps; ++k) {
+    const int z = z0 + k;
+    cp_async_wait<STAGES - 2>();
+    __syncthreads();
+    // refill the buffer of stage k-1 with stage k+STAGES-1
+    {
+      const int kn = k + STAGES - 1;
+      if (kn < nsteps) issue_stage(kn, stage0 + (kn % STAGES) * L.stage_sz);
+      cp_async_commit();
+    }
+    const T* st = stage0 + (k % STAGES) * L.stage_sz;
+    const T* inb = st + L.coef_sz + L.rh_sz;
+    // form plane z+1: own cells (+ ring if the next step needs it)
+    A* nb = ring + ((k + 1) % 3) * PL;
+    if (z + 1 < g.nz) {
+      const bool ring_needed = z + 1 < z1;
+      if (has_cell) {
+#pragma unroll
+        for (int j = 0; j < VEC; ++j) vp[j] = own ? form(inb, so + j) : A(0);
+        if (ring_needed) {
+          sm_store<A, VEC>(nb + so, vp);
+          if (KIND == 0 && own) store_run<T, VEC, true, true>(p_out + (long long)(z + 1) * g.plane + row, VEC, vp);
+          if (ty == 0) {
+            A h[VEC];
+#pragma unroll
+            for (int j = 0; j < VEC; ++j) h[j] = form(inb, so - L.W + j);
+            sm_store<A, VEC>(nb + so - L.W, h);
+          }
+          if (ty == g.by - 1) {
+            A h[VEC];
+#pragma unroll
+            for (int j = 0; j < VEC; ++j) h[j] = form(inb, so + L.W + j);
+            sm_store<A, VEC>(nb + so + L.W, h);
+          }
+          if (tx == 0) nb[so - 1] = form(inb, so - 1);
+          if (tx == g.bx - 1) nb[so + VEC] = form(inb, so + VEC);
+        }
+      }
+    } else {
+      zero(vp);
+    }
+    // stencil on plane z
+    if (own) {
+      const A* cb = ring + (k % 3) * PL;
+      A up[VEC], dn[VEC], c[6][VEC];
+      sm_load<A, VEC>(cb + so - L.W, up);
+      sm_load<A, VEC>(cb + so + L.W, dn);
+      const A lf = cb[so - 1];
+      const A rt = cb[so + VEC];
+#pragma unroll
+      for (int d = 0; d < 6; ++d) ldv<T, VEC>(st + d * g.by * L.TW + sc_own, c[d]);
+      A o[VEC];
+#pragma unroll
+      for (int j = 0; j < VEC; ++j) {
+        const A l = (j == 0) ? lf : vc[j - 1];
+        const A r = (j == VEC - 1) ? rt : vc[j + 1];
+        A s = vc[j];
+        s = fma(c[0][j], l, s);
+        s = fma(c[1][j], r, s);
+        s = fma(c[2][j], up[j], s);
+        s = fma(c[3][j], dn[j], s);
+        s = fma(c[4][j], vm[j], s);
+        s = fma(c[5][j], vp[j], s);
+        o[j] = as_stored<T>(s);
+      }
+      store_run<T, VEC, true, true>(out + (long long)z * g.plane + row, VEC, o);
+      if (KIND == 0) {
+        A hv[VEC];
+        ldv<T, VEC>(st + L.coef_sz + sc_own, hv);
+#pragma unroll
+        for (int j = 0; j < VEC; ++j) acc.part[0] = fma(hv[j], o[j], acc.part[0]);
+      } else {
+#pragma unroll
+        for (int j = 0; j < VEC; ++j) {
+          acc.part[0] = fma(vc[j], o[j], acc.part[0]);
+          acc.part[1] = fma(o[j], o[j], acc.part[1]);
+        }
+      }
+    }
+    if ((k & 7) == 7) acc.fold();
+#pragma unroll
+    for (int j = 0; j < VEC; ++j) {
+      vm[j] = vc[j];
+      vc[j] = vp[j];
+    }
+  }
+  cp_async_wait<0>();
+  acc.fold();
+  const int nb_total = s7_nblocks(g);
+  if (KIND == 0) {
+    double v[1] = {acc.tot[0]}, tot[1];
+    block_sum<1>(v, red);
+    if (grid_combine<1>(a.parts, &sc->counter[CNT_A], nb_total, bid, v, tot, red) && t == 0) {
+      const double sigma = tot[0];
+      if (sigma == 0.0 || !isfinite(sigma) || !isfinite(sc->rho)) {
+        sc->status = 3;
+        sc->done = 1;
+      } else {
+        sc->alpha = sc->rho / sigma;
+      }
+    }
+  } else {
+    double v[2] = {acc.tot[0], acc.tot[1]}, tot[2];
+    block_sum<2>(v, red);
+    if (grid_combine<2>(a.parts, &sc->counter[CNT_B], nb_total, bid, v, tot, red) && t == 0) {
+      const double qy = tot[0], yy = tot[1];
+      if (yy == 0.0) {
+        sc->special = 1;
+        sc->omega = 0.0;
+      } else {
+        const double om = qy / yy;
+        if (om == 0.0 || !isfinite(om)) {
+          sc->status = 3;
+          sc->done = 1;
+        } else {
+          sc->omega = om;
+        }
+      }
+    }
+  }
+}
+
+}  // namespace s7

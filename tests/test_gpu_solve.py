@@ -163,6 +163,38 @@ def test_graph_step_count_does_not_change_results(s7):
         assert np.array_equal(o.x.cpu().numpy(), outs[0].x.cpu().numpy())
 
 
+@pytest.mark.parametrize("shape", [(64, 48, 40), (40, 31, 70), (8, 3, 5)])
+def test_pipeline_depth_does_not_change_results(s7, shape):
+    # the shared-memory pipelined sweeps (2 or 3 stages) and the direct-load
+    # sweeps (stages = 1) do the same arithmetic in the same order
+    nx, ny, nz = shape
+    p = synth.varcoef(nx, ny, nz, seed=44)
+    outs = []
+    for stages, by, kinds in ((1, 0, 0), (2, 0, 0), (3, 0, 3), (2, 3, 3), (3, 1, 2), (2, 8, 1)):
+        with s7.stencil7_create(nx, ny, nz, gu.coef_on_device(p), storage="f32",
+                                stages=stages, by=by, pipe_kinds=kinds) as op:
+            outs.append(s7.bicgstab_solve(op, gu.to_dev(p.b), tol=1e-6, maxit=300))
+    for o in outs[1:]:
+        assert o.iters == outs[0].iters
+        assert np.array_equal(o.hist, outs[0].hist)
+        assert np.array_equal(o.x.cpu().numpy(), outs[0].x.cpu().numpy())
+
+
+@pytest.mark.parametrize("storage", ["f64", "bf16", "f16"])
+def test_pipeline_depth_other_storage(s7, storage):
+    nx, ny, nz = 48, 20, 30
+    raw = np.float64 if storage == "f64" else np.float32
+    p = synth.varcoef(nx, ny, nz, seed=45, dtype=raw)
+    outs = []
+    for stages, kinds in ((1, 0), (2, 3), (3, 3), (2, 1)):
+        with s7.stencil7_create(nx, ny, nz, gu.coef_on_device(p), storage=storage,
+                                stages=stages, pipe_kinds=kinds) as op:
+            outs.append(s7.bicgstab_solve(op, gu.to_dev(p.b), tol=1e-3, maxit=60))
+    for o in outs[1:]:
+        assert o.iters == outs[0].iters
+        assert np.array_equal(o.x.cpu().numpy(), outs[0].x.cpu().numpy())
+
+
 def test_residual_entry_point(s7):
     nx, ny, nz = 26, 19, 15
     p = synth.varcoef(nx, ny, nz, seed=44)
