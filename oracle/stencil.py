@@ -72,6 +72,37 @@ def apply(nx, ny, nz, coef, v):
     return out.reshape(n)
 
 
+def apply_at(nx, ny, nz, coef_rows, x_at, idx):
+    """Rows ``idx`` of ``A v`` in float64, one row at a time.
+
+    ``coef_rows`` maps ``diag`` (optional: unit) and the six directions to
+    the coefficients *of those rows* (arrays aligned with ``idx``); ``x_at``
+    returns v at an array of linear indices.  Used on meshes too large to
+    hold in float64 on the host: each sampled row needs only its own
+    coefficients and seven values of v.  Returns ``(A v)[idx]`` and
+    ``(|A||v|)[idx]``.
+    """
+    idx = np.asarray(idx, dtype=np.int64)
+    x = idx % nx
+    y = (idx // nx) % ny
+    z = idx // (nx * ny)
+    d = coef_rows.get("diag", None)
+    vi = np.asarray(x_at(idx), dtype=np.float64)
+    dv = np.ones(idx.shape) if d is None else np.asarray(d, dtype=np.float64)
+    out = dv * vi
+    mag = np.abs(dv * vi)
+    steps = {"xm": (x > 0, -1), "xp": (x < nx - 1, 1), "ym": (y > 0, -nx),
+             "yp": (y < ny - 1, nx), "zm": (z > 0, -nx * ny), "zp": (z < nz - 1, nx * ny)}
+    for name in DIRS:
+        inside, off = steps[name]
+        j = np.where(inside, idx + off, idx)            # any valid index where off-mesh
+        vj = np.where(inside, np.asarray(x_at(j), dtype=np.float64), 0.0)
+        c = np.asarray(coef_rows[name], dtype=np.float64)
+        out = out + c * vj
+        mag = mag + np.abs(c * vj)
+    return out, mag
+
+
 def abs_apply(nx, ny, nz, coef, v):
     """``|A| |v|`` (elementwise magnitudes): the scale of each row's sum.
 

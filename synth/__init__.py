@@ -279,6 +279,13 @@ def random_vector(n, seed, stream, dtype=np.float32, kind="normal"):
     return _fill(out, lambda s, c: (2.0 * uniform(seed, stream, s, c) - 1.0).astype(dtype))
 
 
+def random_vector_at(idx, seed, stream, dtype=np.float32):
+    """Values of ``random_vector(n, seed, stream, dtype, kind="uniform")`` at
+    indices ``idx`` (bit for bit)."""
+    u = uniform_at(seed, stream, np.asarray(idx, dtype=np.int64))
+    return (2.0 * u - 1.0).astype(dtype)
+
+
 # ---------------------------------------------------------------------------
 # batched and served workloads
 # ---------------------------------------------------------------------------

@@ -1,0 +1,129 @@
+"""Parity at the workloads' full sizes, on sampled rows and by properties.
+
+600 x 595 x 1536 (548M cells, FP32; the mesh of the paper's Sec. V run) and
+512^3 (134M cells, BF16 and FP16 storage with FP64 refinement).  The FP64
+oracle cannot solve these on the host, so:
+
+* SpMV: sampled rows (random, mesh faces and edges, tile and chunk seams) are
+  recomputed by the oracle one by one (``stencil.apply_at``) from the
+  generator's values at those cells, bit-identical to the GPU's inputs.
+* Solves: the GPU's float64 residual vector r = b - A x is checked row by
+  row against the oracle's recomputation from the GPU's x (so the residual
+  norm that certifies convergence is itself verified), and the certified
+  norms must meet the tolerance.
+"""
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import stencil
+from tests import gpu_util as gu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def s7():
+    import paper_2010_03660_gb300 as m
+    m.lib()
+    return m
+
+
+def sample_rows(nx, ny, nz, count, seed):
+    rng = np.random.default_rng(seed)
+    n = nx * ny * nz
+    idx = list(rng.integers(0, n, count))
+    # faces, edges, corners, tile seams (multiples of 120 in x, 4 in y) and
+    # z-chunk seams (multiples of 64)
+    for x in (0, 1, 119, 120, 121, nx - 2, nx - 1):
+        for y in (0, 3, 4, ny - 1):
+            for z in (0, 63, 64, nz // 2, nz - 1):
+                idx.append(x + nx * (y + ny * z))
+    return np.unique(np.asarray(idx, dtype=np.int64))
+
+
+def gpu_at(t):
+    import torch
+
+    def f(j):
+        j = np.asarray(j, dtype=np.int64)
+        return t[torch.from_numpy(j).to(t.device)].double().cpu().numpy()
+    return f
+
+
+def residual_rows_check(nx, ny, nz, seed, idx, x_gpu, b_at, r_gpu):
+    """Oracle r = b - A x on rows idx (raw float32 coefficients, float64
+    arithmetic, the GPU's x) against the GPU's residual vector."""
+    coef, _ = synth.varcoef_at(nx, ny, nz, idx, seed=seed)
+    ax, mag = stencil.apply_at(nx, ny, nz, coef, gpu_at(x_gpu), idx)
+    r_ref = b_at - ax
+    r_dev = gpu_at(r_gpu)(idx)
+    return float(np.max(np.abs(r_dev - r_ref) / (mag + np.abs(b_at))))
+
+
+@pytest.fixture(scope="module")
+def config2(s7):
+    nx, ny, nz = 600, 595, 1536
+    p = synth.varcoef(nx, ny, nz, seed=0)
+    op = s7.stencil7_create(nx, ny, nz, p.coef, storage="f32", keep_true=True)
+    yield nx, ny, nz, p, op
+    op.close()
+
+
+def test_config2_fullsize_spmv_sampled_rows(s7, config2):
+    import torch
+    nx, ny, nz, p, op = config2
+    x = gu.to_dev(synth.random_vector(p.n, 11, 5, np.float32, kind="uniform"))
+    y = s7.stencil7_apply(op, x)
+    torch.cuda.synchronize()
+    idx = sample_rows(nx, ny, nz, 4000, 1)
+    coef, _ = synth.varcoef_at(nx, ny, nz, idx, seed=0)
+    d = coef["diag"].astype(np.float64)
+    scaled = {k: stencil.round_to(coef[k].astype(np.float64) / d, "f32") for k in synth.DIRS}
+    ref, mag = stencil.apply_at(nx, ny, nz, scaled,
+                                lambda j: synth.random_vector_at(j, 11, 5), idx)
+    got = gpu_at(y)(idx)
+    err = float(np.max(np.abs(got - ref) / mag))
+    assert err <= 2e-6, err
+
+
+def test_config2_fullsize_solve_to_1e6(s7, config2):
+    import torch
+    nx, ny, nz, p, op = config2
+    b = gu.to_dev(p.b)
+    res = s7.bicgstab_solve(op, b, tol=1e-6, maxit=500)
+    assert res.status == 0, res.status
+    assert res.hist[-1] <= 1e-6 and res.hist[0] == pytest.approx(1.0, rel=1e-6)
+    assert res.true_resid <= 2e-6
+    # the float64 residual of the raw system, verified row by row
+    r = torch.empty_like(b)
+    rn, bn = s7.stencil7_residual(op, b, res.x, r)
+    assert rn / bn <= 1e-5
+    idx = sample_rows(nx, ny, nz, 3000, 2)
+    err = residual_rows_check(nx, ny, nz, 0, idx, res.x, p.b[idx].astype(np.float64), r)
+    assert err <= 1e-7, err
+    # the reported norm agrees with the sampled rows' mean square (loose,
+    # statistical: 3000 of 548M rows)
+    ms = float(np.mean(gpu_at(r)(idx) ** 2))
+    assert 0.2 < ms * p.n / rn ** 2 < 5.0
+
+
+@pytest.mark.parametrize("storage", ["bf16", "f16"])
+def test_config3_512cubed_refined_to_1e10(s7, storage):
+    import torch
+    nx = ny = nz = 512
+    p = synth.varcoef(nx, ny, nz, seed=2)
+    b64 = p.b.astype(np.float64)
+    with s7.stencil7_create(nx, ny, nz, p.coef, storage=storage, keep_true=True) as op:
+        b = gu.to_dev(b64)
+        res = s7.bicgstab_solve_refined(op, b, tol=1e-10, max_outer=60, inner_maxit=200,
+                                        inner_tol=1e-2)
+        assert res.status == 0, (res.status, res.hist)
+        assert res.hist[-1] <= 1e-10
+        r = torch.empty_like(b)
+        rn, bn = s7.stencil7_residual(op, b, res.x, r)
+        assert rn / bn <= 1.01e-10
+        idx = sample_rows(nx, ny, nz, 3000, 3)
+        err = residual_rows_check(nx, ny, nz, 2, idx, res.x, b64[idx], r)
+        assert err <= 1e-12, err

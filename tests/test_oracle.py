@@ -92,6 +92,25 @@ def test_apply_matches_dense_assembly(shape):
     assert np.max(np.abs(a @ v - stencil.apply(nx, ny, nz, coef, v))) < 1e-13
 
 
+def test_apply_at_rows_equals_full_apply():
+    nx, ny, nz = 9, 7, 6
+    coef, _ = rand_coef(nx, ny, nz, seed=15)
+    v = synth.random_vector(nx * ny * nz, 3, 3, np.float64)
+    full = stencil.apply(nx, ny, nz, coef, v)
+    mag = stencil.abs_apply(nx, ny, nz, coef, v)
+    idx = np.array([0, 1, 8, 9, 62, 63, 200, nx * ny * nz - 1, 17, 100])
+    rows = {k: np.asarray(c)[idx] for k, c in coef.items()}
+    out, m = stencil.apply_at(nx, ny, nz, rows, lambda j: v[j], idx)
+    assert np.max(np.abs(out - full[idx])) < 1e-14
+    assert np.max(np.abs(m - mag[idx])) < 1e-14
+
+
+def test_sampled_generators_match_full():
+    v = synth.random_vector(5000, 7, 4, np.float32, kind="uniform")
+    idx = np.array([0, 3, 4999, 1234])
+    assert np.array_equal(synth.random_vector_at(idx, 7, 4), v[idx])
+
+
 def test_adjoint_identity_with_independent_transpose():
     nx, ny, nz = 5, 4, 6
     coef, _ = rand_coef(nx, ny, nz, seed=12)
