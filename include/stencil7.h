@@ -210,6 +210,37 @@ int bicgstab_solve_refined(stencil7_t h, const double* b, double* x, double tol,
                            int max_outer, int inner_maxit, double inner_tol,
                            int* outer, int* inner_total, double* hist, void* stream);
 
+/* Options of a batched solve.  Zero-initialise; NULL = all defaults. */
+typedef struct {
+  int threads;      /* threads per block of the batched sweeps (64..256);
+                       0 = chosen by the autotuner                           */
+  int zchunk;       /* z planes per block; 0 = chosen by the autotuner       */
+  int check_every;  /* steps per graph launch between host checks; 0 = 16    */
+  int no_autotune;  /* 1: skip the autotuner (use threads/zchunk or 128/16)  */
+} s7_batch_opts;
+
+/* Solve nsys independent systems together (BiCGStab, Algorithm 1, on each).
+ * One launch per kernel of a step covers every system: each system owns a
+ * range of the launch's blocks and its own grid combine, scalars and stop
+ * flag, so systems of different sizes and tolerances share the launches and
+ * stop independently.  The steps are replayed from a captured CUDA graph.
+ *   hs[j]     operator handles; all of the same storage type and device.  A
+ *             handle may appear once only.
+ *   b[j],x[j] right-hand side and start vector / result of system j
+ *             (nx_j*ny_j*nz_j elements of dt, S7_F64 or S7_F32; host or device).
+ *   tol[j], maxit[j]  per-system stopping rule (as in bicgstab_solve).
+ *   iters[j], status[j], resid[j]  out (each array may be NULL): steps taken,
+ *             S7_OK / S7_ENOTCONV / S7_EBREAKDOWN, final recurrence residual.
+ * Block shape and z chunk are picked by a built-in autotuner that times
+ * candidates with a batched SpMV over the batch's own operators (no change
+ * to the solve) and caches the winner per batch signature.  Synchronous.
+ * Returns S7_OK if every system converged, else S7_EBREAKDOWN if any broke
+ * down, else S7_ENOTCONV. */
+int bicgstab_solve_batched(int nsys, const stencil7_t* hs, const void* const* b,
+                           void* const* x, s7_dtype dt, const double* tol,
+                           const int* maxit, int* iters, int* status, double* resid,
+                           const s7_batch_opts* opts, void* stream);
+
 /* Per-kernel timing for benchmarks.  enable = 1 turns timing on for handle
  * h: solves then launch each kernel directly (not from a captured graph)
  * with a CUDA event pair around it on the handle's stream; enable = 0 turns

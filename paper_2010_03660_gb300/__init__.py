@@ -28,7 +28,8 @@ __all__ = [
     "S7_F64", "S7_F32", "S7_BF16", "S7_F16", "S7Error", "Operator", "lib", "EXPORTS",
     "stencil7_create", "stencil7_destroy", "stencil7_info", "stencil7_apply",
     "stencil7_residual", "stencil7_residual_noalloc", "bicgstab_solve",
-    "bicgstab_solve_refined", "stencil7_profile", "s7_last_error", "s7_version",
+    "bicgstab_solve_refined", "bicgstab_solve_batched", "stencil7_profile", "s7_last_error",
+    "s7_version",
 ]
 
 S7_F64, S7_F32, S7_BF16, S7_F16 = 0, 1, 2, 3
@@ -42,7 +43,8 @@ _STORAGE = {"f64": S7_F64, "f32": S7_F32, "bf16": S7_BF16, "f16": S7_F16}
 EXPORTS = (
     "stencil7_create", "stencil7_destroy", "stencil7_info", "stencil7_apply",
     "stencil7_residual", "stencil7_residual_noalloc", "bicgstab_solve",
-    "bicgstab_solve_refined", "stencil7_profile", "s7_last_error", "s7_version",
+    "bicgstab_solve_refined", "bicgstab_solve_batched", "stencil7_profile", "s7_last_error",
+    "s7_version",
 )
 PROF_KINDS = ("spmv_p_dot", "spmv_q_dots", "update_dots", "start_residual", "true_residual",
               "other")
@@ -64,6 +66,11 @@ class s7_opts(C.Structure):
     _fields_ = [("storage", C.c_int), ("no_jacobi", C.c_int), ("keep_true", C.c_int),
                 ("bx", C.c_int), ("by", C.c_int), ("zchunk", C.c_int),
                 ("check_every", C.c_int), ("stages", C.c_int), ("pipe_kinds", C.c_int)]
+
+
+class s7_batch_opts(C.Structure):
+    _fields_ = [("threads", C.c_int), ("zchunk", C.c_int), ("check_every", C.c_int),
+                ("no_autotune", C.c_int)]
 
 
 _lib = None
@@ -95,6 +102,8 @@ def lib():
         "bicgstab_solve": (i, [vp, vp, vp, i, d, i, P(i), P(d), P(d), vp]),
         "bicgstab_solve_refined": (i, [vp, vp, vp, d, i, i, d, P(i), P(i), P(d), vp]),
         "stencil7_profile": (i, [vp, i, P(d), P(C.c_longlong)]),
+        "bicgstab_solve_batched": (i, [i, P(vp), P(vp), P(vp), i, P(d), P(i), P(i), P(i), P(d),
+                                       P(s7_batch_opts), vp]),
         "s7_last_error": (C.c_char_p, []),
         "s7_version": (C.c_char_p, []),
     }
@@ -363,3 +372,47 @@ def bicgstab_solve_refined(op, b, x=None, tol=1e-10, max_outer=30, inner_maxit=2
                                       _stream(b, x))
     _check(rc, allow=(EBREAKDOWN, ENOTCONV))
     return RefinedResult(x, outer.value, inner.value, hist[:outer.value + 1], rc)
+
+
+@dataclass
+class BatchResult:
+    x: list
+    iters: list
+    status: list
+    resid: list
+    rc: int
+
+
+def bicgstab_solve_batched(ops, bs, xs=None, tol=1e-6, maxit=500, threads=0, zchunk=0,
+                           check_every=0, autotune=True):
+    """Solve independent systems together (one launch per kernel covers all).
+
+    ``ops``: operators (same storage type); ``bs``: right-hand sides (all the
+    same dtype); ``xs``: start vectors (default zeros), overwritten with the
+    results.  ``tol`` and ``maxit`` may be scalars or per-system sequences.
+    """
+    n = len(ops)
+    if xs is None:
+        xs = []
+        for b in bs:
+            x = _empty_like(b)
+            if _is_torch(x):
+                x.zero_()
+            else:
+                x[...] = 0
+            xs.append(x)
+    tols = [float(tol)] * n if np.isscalar(tol) else [float(t) for t in tol]
+    mits = [int(maxit)] * n if np.isscalar(maxit) else [int(m) for m in maxit]
+    H = (C.c_void_p * n)(*[op.handle.value for op in ops])
+    B = (C.c_void_p * n)(*[_ptr(b) for b in bs])
+    X = (C.c_void_p * n)(*[_ptr(x) for x in xs])
+    T = (C.c_double * n)(*tols)
+    M = (C.c_int * n)(*mits)
+    it = (C.c_int * n)()
+    stt = (C.c_int * n)()
+    rs = (C.c_double * n)()
+    o = s7_batch_opts(threads, zchunk, check_every, 0 if autotune else 1)
+    rc = lib().bicgstab_solve_batched(n, H, B, X, _dtype_code(bs[0]), T, M, it, stt, rs,
+                                      C.byref(o), _stream(*bs))
+    _check(rc, allow=(EBREAKDOWN, ENOTCONV))
+    return BatchResult(xs, list(it), list(stt), list(rs), rc)

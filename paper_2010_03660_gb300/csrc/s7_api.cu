@@ -7,7 +7,11 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <new>
+#include <tuple>
+#include <vector>
 
 #include <cuda.h>
 
@@ -860,4 +864,309 @@ extern "C" int bicgstab_solve_refined(stencil7_t h, const double* b, double* x, 
   if (status == S7_EBREAKDOWN) return fail(status, "inner solve broke down at outer step %d", k);
   if (status == S7_ENOTCONV) return fail(status, "refinement not converged in %d outer steps", k);
   return S7_OK;
+}
+
+// ---------------------------------------------------------------------------
+// batched solves
+// ---------------------------------------------------------------------------
+namespace {
+
+struct BatchPolicy {
+  int threads;
+  int zchunk;
+};
+
+// Autotuned policies by batch signature (storage, systems, log2 cells).
+std::map<std::tuple<int, int, int, int>, BatchPolicy> g_policy;
+std::mutex g_policy_mu;
+
+Tile batch_tile(const Handle* h, int vec, const BatchPolicy& p) {
+  const int runs = (h->nx + vec - 1) / vec;
+  const int cap = std::min(32, p.threads);
+  const int ntx = (runs + cap - 1) / cap;
+  Tile t;
+  t.bx = (runs + ntx - 1) / ntx;
+  t.by = std::max(1, std::min(h->ny, p.threads / t.bx));
+  t.zchunk = std::max(1, std::min(p.zchunk, h->nz));
+  return t;
+}
+
+struct BatchBuffers {
+  Scalars* sc = nullptr;
+  Scalars* h_sc = nullptr;
+  double* hist = nullptr;
+  double* parts = nullptr;
+  void* desc = nullptr;
+  std::vector<unsigned char> h_desc;
+  ~BatchBuffers() {
+    if (sc) cudaFree(sc);
+    if (h_sc) cudaFreeHost(h_sc);
+    if (hist) cudaFree(hist);
+    if (parts) cudaFree(parts);
+    if (desc) cudaFree(desc);
+  }
+};
+
+}  // namespace
+
+// Lay out the batch for policy p: descriptors (host + device), block offsets.
+static int batch_layout(int nsys, Handle* const* hs, const void* const* bdev, const Engine* eng,
+                        const BatchPolicy& p, BatchBuffers& bb, const std::vector<size_t>& hist_off,
+                        const std::vector<size_t>& parts_off, int* sweep_blocks, int* upd_blocks,
+                        size_t* smem, cudaStream_t st) {
+  int b0 = 0, u0 = 0;
+  size_t sm = 0;
+  for (int j = 0; j < nsys; ++j) {
+    const Tile t = batch_tile(hs[j], eng->vec, p);
+    int nb = 0, ub = 0;
+    eng->fill_desc(hs[j], bb.h_desc.data() + (size_t)j * eng->desc_size, t, bdev[j],
+                   bb.parts + parts_off[j], bb.hist + hist_off[j], bb.sc + j, b0, u0, &nb, &ub);
+    b0 += nb;
+    u0 += ub;
+    sm = std::max(sm, eng->batched_smem(hs[j], t));
+  }
+  *sweep_blocks = b0;
+  *upd_blocks = u0;
+  *smem = sm;
+  CK(cudaMemcpyAsync(bb.desc, bb.h_desc.data(), (size_t)nsys * eng->desc_size,
+                     cudaMemcpyHostToDevice, st));
+  return S7_OK;
+}
+
+extern "C" int bicgstab_solve_batched(int nsys, const stencil7_t* hs_in, const void* const* b,
+                                      void* const* x, s7_dtype dt, const double* tol,
+                                      const int* maxit, int* iters, int* status, double* resid,
+                                      const s7_batch_opts* o, void* stream) {
+  if (nsys < 1 || !hs_in || !b || !x || !tol || !maxit)
+    return fail(S7_EINVAL, "bicgstab_solve_batched: bad arguments");
+  if (dt != S7_F64 && dt != S7_F32)
+    return fail(S7_EINVAL, "bicgstab_solve_batched: dt must be F64 or F32");
+  s7_batch_opts opts;
+  memset(&opts, 0, sizeof opts);
+  if (o) opts = *o;
+  std::vector<Handle*> hs(nsys);
+  for (int j = 0; j < nsys; ++j) {
+    hs[j] = hs_in[j];
+    if (!hs[j] || !b[j] || !x[j]) return fail(S7_EINVAL, "bicgstab_solve_batched: NULL system %d", j);
+    if (hs[j]->storage != hs[0]->storage || hs[j]->device != hs[0]->device)
+      return fail(S7_EINVAL, "bicgstab_solve_batched: mixed storage types or devices");
+    if (maxit[j] < 0 || !(tol[j] >= 0.0))
+      return fail(S7_EINVAL, "bicgstab_solve_batched: bad tol/maxit for system %d", j);
+  }
+  {
+    std::vector<Handle*> sorted(hs);
+    std::sort(sorted.begin(), sorted.end());
+    if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end())
+      return fail(S7_EINVAL, "bicgstab_solve_batched: a handle appears twice");
+  }
+  bind_handle_device(hs[0]);
+  const Engine* eng = engine_for(hs[0]->storage);
+  const s7_dtype xt = xtype(hs[0]);
+  cudaStream_t us = (cudaStream_t)stream;
+  cudaStream_t st = nullptr;
+  cudaEvent_t ev = nullptr;
+  CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+  int rc = S7_OK;
+  cudaGraphExec_t gexec = nullptr;
+  BatchBuffers bb;
+  std::vector<const void*> bdev(nsys);
+  std::vector<size_t> hist_off(nsys), parts_off(nsys);
+  size_t hist_total = 0, parts_total = 0;
+  long long cells = 0;
+  int sweep_blocks = 0, upd_blocks = 0, threads = 128;
+  size_t smem = 0;
+  BatchPolicy pol{128, 16};
+  const int ce = opts.check_every > 0 ? opts.check_every : 16;
+  cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+  if (e != cudaSuccess) { rc = cuda_fail(e, "event"); goto out; }
+  if ((rc = join(us, st, ev))) goto out;
+  // workspaces and inputs
+  for (int j = 0; j < nsys; ++j) {
+    Handle* h = hs[j];
+    if ((rc = ensure_ws(h, 0))) goto out;
+    if ((rc = stage_in(h, b[j], dt, xt, h->ws.b, &bdev[j], st))) goto out;
+    const void* xin = nullptr;
+    if ((rc = stage_in(h, x[j], dt, xt, h->ws.x, &xin, st))) goto out;
+    if (xin != h->ws.x) {
+      e = cudaMemcpyAsync(h->ws.x, xin, (size_t)h->n * eng->x_size, cudaMemcpyDeviceToDevice, st);
+      if (e != cudaSuccess) { rc = cuda_fail(e, "x0 copy"); goto out; }
+    }
+    hist_off[j] = hist_total;
+    hist_total += (size_t)maxit[j] + 1;
+    cells += h->n;
+  }
+  // batch-owned scalars, histories, partial sums, descriptors
+  {
+    // partials: 2 per block, for the largest block count of any policy tried
+    std::vector<BatchPolicy> pols;
+    for (int t : {64, 128, 256})
+      for (int z : {8, 16, 32}) pols.push_back(BatchPolicy{t, z});
+    pols.push_back(BatchPolicy{opts.threads > 0 ? std::max(64, std::min(256, opts.threads)) : 128,
+                               opts.zchunk > 0 ? opts.zchunk : 16});
+    for (int j = 0; j < nsys; ++j) {
+      Handle* h = hs[j];
+      const long long runs = (h->nx + eng->vec - 1) / eng->vec;
+      long long cap = 4096;  // update blocks
+      for (const BatchPolicy& q : pols) {
+        const Tile t = batch_tile(h, eng->vec, q);
+        const long long nb = ((runs + t.bx - 1) / t.bx) * ((h->ny + t.by - 1) / t.by) *
+                             ((h->nz + t.zchunk - 1) / t.zchunk);
+        cap = std::max(cap, nb);
+      }
+      parts_off[j] = parts_total;
+      parts_total += 2 * (size_t)cap;
+    }
+    bb.h_desc.resize((size_t)nsys * eng->desc_size);
+    void* p = nullptr;
+    if ((e = cudaMalloc(&p, (size_t)nsys * sizeof(Scalars))) != cudaSuccess) { rc = cuda_fail(e, "batch scalars"); goto out; }
+    bb.sc = (Scalars*)p;
+    if ((e = cudaMallocHost(&p, (size_t)nsys * sizeof(Scalars))) != cudaSuccess) { rc = cuda_fail(e, "batch scalars (host)"); goto out; }
+    bb.h_sc = (Scalars*)p;
+    if ((e = cudaMalloc(&p, hist_total * 8)) != cudaSuccess) { rc = cuda_fail(e, "batch history"); goto out; }
+    bb.hist = (double*)p;
+    if ((e = cudaMalloc(&p, parts_total * 8)) != cudaSuccess) { rc = cuda_fail(e, "batch partials"); goto out; }
+    bb.parts = (double*)p;
+    if ((e = cudaMalloc(&p, (size_t)nsys * eng->desc_size)) != cudaSuccess) { rc = cuda_fail(e, "batch descriptors"); goto out; }
+    bb.desc = p;
+  }
+  // policy: explicit, cached, or autotuned with a batched SpMV probe
+  {
+    int l2 = 0;
+    while ((1LL << l2) < cells) ++l2;
+    const auto key = std::make_tuple((int)hs[0]->storage, nsys, l2, 0);
+    bool have = false;
+    if (opts.threads > 0 || opts.zchunk > 0 || opts.no_autotune) {
+      pol.threads = opts.threads > 0 ? std::max(64, std::min(256, opts.threads)) : 128;
+      pol.zchunk = opts.zchunk > 0 ? opts.zchunk : 16;
+      have = true;
+    } else {
+      std::lock_guard<std::mutex> lk(g_policy_mu);
+      auto it = g_policy.find(key);
+      if (it != g_policy.end()) {
+        pol = it->second;
+        have = true;
+      }
+    }
+    if (!have) {
+      const int cand_t[3] = {64, 128, 256};
+      const int cand_z[3] = {8, 16, 32};
+      float best = 1e30f;
+      cudaEvent_t e0, e1;
+      cudaEventCreate(&e0);
+      cudaEventCreate(&e1);
+      for (int ti = 0; ti < 3; ++ti)
+        for (int zi = 0; zi < 3; ++zi) {
+          BatchPolicy c{cand_t[ti], cand_z[zi]};
+          if ((rc = batch_layout(nsys, hs.data(), bdev.data(), eng, c, bb, hist_off, parts_off,
+                                 &sweep_blocks, &upd_blocks, &smem, st)))
+            goto tune_out;
+          if (eng->batched_prepare(smem)) { rc = fail(S7_ECUDA, "batched kernel attributes"); goto tune_out; }
+          // warm, then time two probes
+          if ((rc = eng->launch_batched(3, bb.desc, nsys, sweep_blocks, c.threads, smem, st))) goto tune_out;
+          cudaEventRecord(e0, st);
+          for (int r = 0; r < 2 && rc == S7_OK; ++r)
+            rc = eng->launch_batched(3, bb.desc, nsys, sweep_blocks, c.threads, smem, st);
+          cudaEventRecord(e1, st);
+          if (rc) goto tune_out;
+          if ((e = cudaEventSynchronize(e1)) != cudaSuccess) { rc = cuda_fail(e, "autotune"); goto tune_out; }
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, e0, e1);
+          if (ms < best) {
+            best = ms;
+            pol = c;
+          }
+        }
+    tune_out:
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      if (rc) goto out;
+      std::lock_guard<std::mutex> lk(g_policy_mu);
+      g_policy[key] = pol;
+    }
+  }
+  threads = pol.threads;
+  if ((rc = batch_layout(nsys, hs.data(), bdev.data(), eng, pol, bb, hist_off, parts_off,
+                         &sweep_blocks, &upd_blocks, &smem, st)))
+    goto out;
+  if (eng->batched_prepare(smem)) { rc = fail(S7_ECUDA, "batched kernel attributes"); goto out; }
+  // scalars: tol, maxit
+  for (int j = 0; j < nsys; ++j) {
+    Scalars& s = bb.h_sc[j];
+    memset(&s, 0, sizeof s);
+    s.tol = tol[j];
+    s.maxit = maxit[j];
+    s.status = S7_ENOTCONV;
+  }
+  if ((e = cudaMemcpyAsync(bb.sc, bb.h_sc, (size_t)nsys * sizeof(Scalars), cudaMemcpyHostToDevice, st)) != cudaSuccess) { rc = cuda_fail(e, "scalars"); goto out; }
+  if ((rc = eng->launch_batched(2, bb.desc, nsys, sweep_blocks, threads, smem, st)) ||
+      (rc = eng->launch_batched(5, bb.desc, nsys, 0, 0, 0, st))) {
+    rc = fail(rc, "batched start launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+    goto out;
+  }
+  // capture ce steps
+  {
+    cudaGraph_t g = nullptr;
+    if ((e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) { rc = cuda_fail(e, "capture"); goto out; }
+    for (int k = 0; k < ce && rc == S7_OK; ++k) {
+      rc = eng->launch_batched(0, bb.desc, nsys, sweep_blocks, threads, smem, st);
+      if (!rc) rc = eng->launch_batched(1, bb.desc, nsys, sweep_blocks, threads, smem, st);
+      if (!rc) rc = eng->launch_batched(4, bb.desc, nsys, upd_blocks, 256, 0, st);
+    }
+    e = cudaStreamEndCapture(st, &g);
+    if (rc || e != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      rc = rc ? fail(rc, "batched capture: launch failed") : cuda_fail(e, "cudaStreamEndCapture");
+      goto out;
+    }
+    e = cudaGraphInstantiate(&gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) { gexec = nullptr; rc = cuda_fail(e, "cudaGraphInstantiate"); goto out; }
+  }
+  {
+    int mx = 0;
+    for (int j = 0; j < nsys; ++j) mx = std::max(mx, maxit[j]);
+    const int max_launch = mx / ce + 3;
+    for (int launches = 0;; ++launches) {
+      if ((e = cudaMemcpyAsync(bb.h_sc, bb.sc, (size_t)nsys * sizeof(Scalars), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+          (e = cudaStreamSynchronize(st)) != cudaSuccess) { rc = cuda_fail(e, "batched poll"); goto out; }
+      bool all = true;
+      for (int j = 0; j < nsys && all; ++j) all = bb.h_sc[j].done != 0;
+      if (all) break;
+      if (launches >= max_launch) { rc = fail(S7_ECUDA, "batched solve did not terminate"); goto out; }
+      if ((e = cudaGraphLaunch(gexec, st)) != cudaSuccess) { rc = cuda_fail(e, "graph launch"); goto out; }
+    }
+  }
+  // results
+  {
+    bool any_break = false, any_nc = false;
+    for (int j = 0; j < nsys; ++j) {
+      const Scalars& s = bb.h_sc[j];
+      Handle* h = hs[j];
+      if (s.bnorm == 0.0) {
+        if ((e = cudaMemsetAsync(h->ws.x, 0, (size_t)h->n * eng->x_size, st)) != cudaSuccess) { rc = cuda_fail(e, "zero x"); goto out; }
+      }
+      if ((rc = stage_out(h, h->ws.x, xt, x[j], dt, st))) goto out;
+      if (iters) iters[j] = s.iter;
+      if (status) status[j] = s.status;
+      if (resid) resid[j] = s.bnorm == 0.0 ? 0.0 : s.res[2];
+      any_break |= s.status == S7_EBREAKDOWN;
+      any_nc |= s.status == S7_ENOTCONV;
+    }
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) { rc = cuda_fail(e, "batched results"); goto out; }
+    if (any_break) rc = fail(S7_EBREAKDOWN, "breakdown in at least one system");
+    else if (any_nc) rc = fail(S7_ENOTCONV, "at least one system did not converge");
+  }
+out:
+  if (gexec) cudaGraphExecDestroy(gexec);
+  if (st) {
+    cudaStreamSynchronize(st);
+    if (ev && us != st) {
+      cudaEventRecord(ev, st);
+      cudaStreamWaitEvent(us, ev, 0);
+    }
+  }
+  if (ev) cudaEventDestroy(ev);
+  if (st) cudaStreamDestroy(st);
+  return rc;
 }

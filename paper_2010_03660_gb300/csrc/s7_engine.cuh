@@ -6,6 +6,8 @@
 
 #include <algorithm>
 
+#include <string.h>
+
 #include "s7_handle.h"
 #include "s7_step.cuh"
 #include "s7_sweep.cuh"
@@ -42,14 +44,13 @@ __device__ inline void finish_step(Scalars* sc, double rho_new, double rr, doubl
   }
 }
 
+// Block `bid` of `nblk` blocks of the update over one system of n cells.
 template <class T, class X, class A, int VEC>
-__global__ void __launch_bounds__(256) k_update(long long n, const T* p0, const T* p1,
-                                                const T* s0, const T* s1,
-                                                const T* __restrict__ y, const T* __restrict__ rh,
-                                                T* __restrict__ r, X* __restrict__ x, Scalars* sc,
-                                                double* parts, double* hist) {
-  __shared__ double red[32 * 4];
-  if (*((volatile int*)&sc->done)) return;
+__device__ __forceinline__ void update_body(long long n, const T* p0, const T* p1, const T* s0,
+                                            const T* s1, const T* __restrict__ y,
+                                            const T* __restrict__ rh, T* __restrict__ r,
+                                            X* __restrict__ x, Scalars* sc, double* parts,
+                                            double* hist, int bid, int nblk, double* red) {
   const int it = sc->iter;
   const T* __restrict__ p = (it & 1) ? p1 : p0;
   const T* __restrict__ s = (it & 1) ? s1 : s0;
@@ -57,9 +58,9 @@ __global__ void __launch_bounds__(256) k_update(long long n, const T* p0, const 
   DotAcc<A, 2> acc;
   acc.init();
   const long long nvec = n / VEC;
-  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long stride = (long long)nblk * blockDim.x;
   int cnt = 0;
-  for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < nvec; v += stride) {
+  for (long long v = (long long)bid * blockDim.x + threadIdx.x; v < nvec; v += stride) {
     const long long i = v * VEC;
     A pv[VEC], sv[VEC], yv[VEC], rv[VEC], hv[VEC], xv[VEC];
     ldv<T, VEC, LD_STREAM>(r + i, rv);
@@ -84,7 +85,7 @@ __global__ void __launch_bounds__(256) k_update(long long n, const T* p0, const 
       cnt = 0;
     }
   }
-  if (blockIdx.x == 0) {
+  if (bid == 0) {
     for (long long i = nvec * VEC + threadIdx.x; i < n; i += blockDim.x) {
       const A rv = to_acc<A>(r[i]), sv = to_acc<A>(s[i]);
       const A q = q_of(rv, sv, alpha);
@@ -98,9 +99,20 @@ __global__ void __launch_bounds__(256) k_update(long long n, const T* p0, const 
   acc.fold();
   double vv[2] = {acc.tot[0], acc.tot[1]}, tot[2];
   block_sum<2>(vv, red);
-  if (grid_combine<2>(parts, &sc->counter[CNT_C], gridDim.x, blockIdx.x, vv, tot, red) &&
-      threadIdx.x == 0)
+  if (grid_combine<2>(parts, &sc->counter[CNT_C], nblk, bid, vv, tot, red) && threadIdx.x == 0)
     finish_step(sc, tot[0], tot[1], hist);
+}
+
+template <class T, class X, class A, int VEC>
+__global__ void __launch_bounds__(256) k_update(long long n, const T* p0, const T* p1,
+                                                const T* s0, const T* s1,
+                                                const T* __restrict__ y, const T* __restrict__ rh,
+                                                T* __restrict__ r, X* __restrict__ x, Scalars* sc,
+                                                double* parts, double* hist) {
+  __shared__ double red[32 * 4];
+  if (*((volatile int*)&sc->done)) return;
+  update_body<T, X, A, VEC>(n, p0, p1, s0, s1, y, rh, r, x, sc, parts, hist, blockIdx.x,
+                            gridDim.x, red);
 }
 
 // Coefficient scaling to a unit diagonal (Sec. IV): out = c / diag computed
@@ -141,6 +153,13 @@ template <class V> __global__ void k_fill(long long n, V* dst, V v) {
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) dst[i] = v;
 }
+
+}  // namespace s7
+
+// the batched kernels reuse update_body above
+#include "s7_batch.cuh"
+
+namespace s7 {
 
 // ---------------------------------------------------------------------------
 // host side
@@ -526,10 +545,103 @@ struct EngineImpl {
     return smem <= 200 * 1024 && g.bx * g.by <= 512;
   }
 
+  // ---- batched solves ----
+  typedef SysDesc<T, X> Desc;
+
+  static Geom geom_tile(const Handle* h, const Tile& t) {
+    Geom g;
+    g.nx = h->nx;
+    g.ny = h->ny;
+    g.nz = h->nz;
+    const int runs = (h->nx + VEC - 1) / VEC;
+    g.bx = std::min(t.bx, runs);
+    g.by = std::min(t.by, h->ny);
+    g.tiles_x = (runs + g.bx - 1) / g.bx;
+    g.tiles_y = (h->ny + g.by - 1) / g.by;
+    g.zchunk = std::min(t.zchunk, h->nz);
+    g.nchunks = (h->nz + g.zchunk - 1) / g.zchunk;
+    g.plane = (long long)h->nx * h->ny;
+    return g;
+  }
+
+  static void fill_desc(Handle* h, void* out, const Tile& t, const void* b, double* parts,
+                        double* hist, Scalars* sc, int block0, int ublock0, int* nb, int* unb) {
+    Desc d;
+    memset(&d, 0, sizeof d);
+    d.g = geom_tile(h, t);
+    d.vl = (h->nx % VEC == 0) && aligned16(b);
+    d.block0 = block0;
+    d.nblocks = s7_nblocks(d.g);
+    d.ublock0 = ublock0;
+    const long long nvec = h->n / VEC;
+    d.unblocks = (int)std::max(1LL, std::min(4096LL, (nvec + 1023) / 1024));
+    d.constant = h->constant;
+    d.n = h->n;
+    for (int k = 0; k < 6; ++k) {
+      d.c[k] = (const T*)h->c[k];
+      d.cc[k] = h->cconst[k];
+    }
+    d.diag = h->jacobi ? nullptr : (const T*)h->diag;
+    d.cdiag = h->jacobi ? 1.0 : h->cconst[6];
+    d.d = (h->jacobi && !h->constant) ? h->d : nullptr;
+    d.cdiv = (h->jacobi && h->constant) ? h->cconst[6] : 1.0;
+    const Workspace& w = h->ws;
+    d.r = (T*)w.r;
+    d.rh = (T*)w.rh;
+    d.p[0] = (T*)w.p[0];
+    d.p[1] = (T*)w.p[1];
+    d.s[0] = (T*)w.s[0];
+    d.s[1] = (T*)w.s[1];
+    d.y = (T*)w.y;
+    d.x = (X*)w.x;
+    d.b = (const X*)b;
+    d.parts = parts;
+    d.hist = hist;
+    d.sc = sc;
+    memcpy(out, &d, sizeof d);
+    *nb = d.nblocks;
+    *unb = d.unblocks;
+  }
+
+  static size_t batched_smem(const Handle* h, const Tile& t) {
+    const Geom g = geom_tile(h, t);
+    return (size_t)3 * (g.by + 2) * (g.bx * VEC + 2 * VEC) * sizeof(A);
+  }
+
+  static int batched_prepare(size_t smem) {
+    if (smem <= kSmemNoOptIn) return S7_OK;
+    const void* ks[4] = {(const void*)k_sweep_batched<T, X, DT, A, VEC, 0>,
+                         (const void*)k_sweep_batched<T, X, DT, A, VEC, 1>,
+                         (const void*)k_sweep_batched<T, X, DT, A, VEC, 2>,
+                         (const void*)k_sweep_batched<T, X, DT, A, VEC, 3>};
+    for (const void* k : ks)
+      if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+          cudaSuccess)
+        return S7_ECUDA;
+    return S7_OK;
+  }
+
+  static int launch_batched(int kind, const void* descs, int nsys, int blocks, int threads,
+                            size_t smem, cudaStream_t st) {
+    const Desc* d = (const Desc*)descs;
+    switch (kind) {
+      case 0: k_sweep_batched<T, X, DT, A, VEC, 0><<<blocks, threads, smem, st>>>(d, nsys); break;
+      case 1: k_sweep_batched<T, X, DT, A, VEC, 1><<<blocks, threads, smem, st>>>(d, nsys); break;
+      case 2: k_sweep_batched<T, X, DT, A, VEC, 2><<<blocks, threads, smem, st>>>(d, nsys); break;
+      case 3: k_sweep_batched<T, X, DT, A, VEC, 3><<<blocks, threads, smem, st>>>(d, nsys); break;
+      case 4: k_update_batched<T, X, A, VEC><<<blocks, 256, 0, st>>>(d, nsys); break;
+      case 5: k_hist0_batched<T, X><<<(nsys + 127) / 128, 128, 0, st>>>(d, nsys); break;
+      default: return S7_EINVAL;
+    }
+    return cudaGetLastError() == cudaSuccess ? S7_OK : S7_ECUDA;
+  }
+
   static const Engine* get() {
     static const Engine e = {sizeof(T), sizeof(X), sizeof(DT), VEC, &scale, &apply, &init, &step_kernel,
                              &true_resid, &raw_resid, &cast, &parts_needed, &smem_ok,
-                             &raw_resid_into, &raw_resid_blocks, &prepare_capture};
+                             &raw_resid_into, &raw_resid_blocks, &prepare_capture,
+                             sizeof(Desc), &fill_desc, &batched_smem, &launch_batched,
+                             &batched_prepare};
     return &e;
   }
 };

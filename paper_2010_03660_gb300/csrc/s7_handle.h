@@ -98,6 +98,19 @@ struct Engine {
   long long (*raw_resid_blocks)(const Handle* h, s7_dtype dt);
   // set kernel attributes the step kernels need, before graph capture
   int (*prepare_capture)(Handle* h);
+  // ---- batched solves (s7_batch.cuh) ----
+  size_t desc_size;
+  // Fill the batch descriptor of system h (host memory) for tile t with
+  // sweep blocks starting at block0 and update blocks at ublock0; returns
+  // the block counts.
+  void (*fill_desc)(Handle* h, void* desc, const Tile& t, const void* b, double* parts,
+                    double* hist, Scalars* sc, int block0, int ublock0, int* nblocks,
+                    int* unblocks);
+  size_t (*batched_smem)(const Handle* h, const Tile& t);
+  // kind 0..3: batched sweeps (see s7_batch.cuh), 4: update, 5: history start
+  int (*launch_batched)(int kind, const void* descs, int nsys, int blocks, int threads,
+                        size_t smem, cudaStream_t st);
+  int (*batched_prepare)(size_t smem);
 };
 
 const Engine* engine_f64();

@@ -105,24 +105,20 @@ template <class A, int VEC> __device__ __forceinline__ void sm_store(A* p, const
 // thread, VL vector loads (nx % VEC == 0 and aligned buffers), Src / Epi the
 // policies.  blockDim.x = roundup(bx*by, 32); threads past bx*by own no
 // cells but take part in barriers and reductions.
+// The body of one sweep block: block `bid` of the `nblocks` blocks of the
+// sweep over the mesh `g`.  `sm` is the dynamic shared memory (three plane
+// buffers), `red` 128 doubles of reduction scratch.
 template <class CT, class A, int VEC, bool VL, class Src, class Epi>
-__global__ void __launch_bounds__(512) k_sweep(Geom g, CoefView<CT, A> cf, Src src_in, Epi epi_in,
-                                               Scalars* sc) {
-  extern __shared__ __align__(16) unsigned char s7_smem[];
-  __shared__ double red[32 * 4];
-  if (sc != nullptr && Epi::kSkipWhenDone && *((volatile int*)&sc->done)) return;
-
-  Src src = src_in;
-  Epi epi = epi_in;
+__device__ __forceinline__ void sweep_body(const Geom& g, const CoefView<CT, A>& cf, Src& src,
+                                           Epi& epi, Scalars* sc, int bid, int nblocks, A* sm,
+                                           double* red) {
   src.setup(sc);
   epi.setup(sc);
 
-  A* sm = reinterpret_cast<A*>(s7_smem);
   const int t = threadIdx.x;
   const bool has_cell = t < g.bx * g.by;
   const int tx = has_cell ? t % g.bx : 0;
   const int ty = has_cell ? t / g.bx : 0;
-  const int bid = blockIdx.x;
   const int tile_x = bid % g.tiles_x;
   const int rest = bid / g.tiles_x;
   const int tile_y = rest % g.tiles_y;
@@ -244,7 +240,19 @@ __global__ void __launch_bounds__(512) k_sweep(Geom g, CoefView<CT, A> cf, Src s
       vc[j] = vp[j];
     }
   }
-  epi.finish(sc, s7_nblocks(g), bid, red);
+  epi.finish(sc, nblocks, bid, red);
+}
+
+template <class CT, class A, int VEC, bool VL, class Src, class Epi>
+__global__ void __launch_bounds__(512) k_sweep(Geom g, CoefView<CT, A> cf, Src src_in, Epi epi_in,
+                                               Scalars* sc) {
+  extern __shared__ __align__(16) unsigned char s7_smem[];
+  __shared__ double red[32 * 4];
+  if (sc != nullptr && Epi::kSkipWhenDone && *((volatile int*)&sc->done)) return;
+  Src src = src_in;
+  Epi epi = epi_in;
+  sweep_body<CT, A, VEC, VL>(g, cf, src, epi, sc, blockIdx.x, s7_nblocks(g),
+                             reinterpret_cast<A*>(s7_smem), red);
 }
 
 // ---------------------------------------------------------------------------

@@ -1,0 +1,153 @@
+"""GPU parity of bicgstab_solve_batched.
+
+Each system of a batch runs Algorithm 1 with its own grid combine, scalars
+and stop flag, so (i) every system matches the FP64 oracle at its own
+tolerance, (ii) with a fixed launch policy a system's result is bitwise the
+same alone and inside any batch, and (iii) the batch of 512 systems of
+log-uniform cube edges 16..128 converges system by system.
+"""
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import bicgstab as ob
+from tests import gpu_util as gu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def s7():
+    import paper_2010_03660_gb300 as m
+    m.lib()
+    return m
+
+
+SHAPES = [(16, 16, 16), (17, 9, 33), (40, 31, 25), (1, 1, 50), (24, 24, 24), (5, 7, 3),
+          (64, 20, 12), (33, 33, 8), (8, 8, 64), (3, 1, 1), (28, 19, 22), (1, 12, 1)]
+
+
+def make(shapes, seed0):
+    return [synth.varcoef(nx, ny, nz, seed=seed0 + j) for j, (nx, ny, nz) in enumerate(shapes)]
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+
+
+def test_batched_matches_oracle_per_system(s7):
+    probs = make(SHAPES, 100)
+    tols = [1e-6 if j % 3 else 1e-5 for j in range(len(probs))]
+    ops = [s7.stencil7_create(p.nx, p.ny, p.nz, gu.coef_on_device(p), storage="f32")
+           for p in probs]
+    try:
+        bs = [gu.to_dev(p.b) for p in probs]
+        res = s7.bicgstab_solve_batched(ops, bs, tol=tols, maxit=1000)
+        assert all(st == 0 for st in res.status), res.status
+        for j, p in enumerate(probs):
+            orc = ob.bicgstab(p.nx, p.ny, p.nz, p.coef, p.b, tol=tols[j], maxit=1000,
+                              storage="f32")
+            x = res.x[j].cpu().numpy()
+            assert res.resid[j] <= tols[j]
+            # float32 recurrences drift from the float64 one (step counts are
+            # not a parity bar); the solution and its true residual are
+            assert abs(res.iters[j] - orc.iters) <= max(6, orc.iters // 4), j
+            assert rel(x, orc.x) <= 100 * tols[j], (j, rel(x, orc.x))
+            tr = ob.true_residual(p.nx, p.ny, p.nz, p.coef, p.b, x)
+            assert tr <= 10 * tols[j], (j, tr)
+    finally:
+        for op in ops:
+            op.close()
+
+
+def test_alone_and_in_the_mix_are_identical(s7):
+    probs = make(SHAPES, 200)
+    ops = [s7.stencil7_create(p.nx, p.ny, p.nz, gu.coef_on_device(p), storage="f32")
+           for p in probs]
+    try:
+        kw = dict(tol=1e-7, maxit=500, threads=128, zchunk=16)
+        mix = s7.bicgstab_solve_batched(ops, [gu.to_dev(p.b) for p in probs], **kw)
+        for j in (0, 2, 5, 9):
+            alone = s7.bicgstab_solve_batched([ops[j]], [gu.to_dev(probs[j].b)], **kw)
+            assert alone.iters[0] == mix.iters[j]
+            assert alone.status[0] == mix.status[j]
+            assert np.array_equal(alone.x[0].cpu().numpy(), mix.x[j].cpu().numpy())
+        # a different subset and order
+        sub = [7, 1, 4]
+        part = s7.bicgstab_solve_batched([ops[j] for j in sub],
+                                         [gu.to_dev(probs[j].b) for j in sub], **kw)
+        for k, j in enumerate(sub):
+            assert np.array_equal(part.x[k].cpu().numpy(), mix.x[j].cpu().numpy())
+    finally:
+        for op in ops:
+            op.close()
+
+
+def test_batched_deterministic_and_autotuned(s7):
+    probs = make(SHAPES[:6], 300)
+    ops = [s7.stencil7_create(p.nx, p.ny, p.nz, gu.coef_on_device(p), storage="f32")
+           for p in probs]
+    try:
+        a = s7.bicgstab_solve_batched(ops, [gu.to_dev(p.b) for p in probs], tol=1e-6)
+        b = s7.bicgstab_solve_batched(ops, [gu.to_dev(p.b) for p in probs], tol=1e-6)
+        assert a.iters == b.iters
+        for xa, xb in zip(a.x, b.x):
+            assert np.array_equal(xa.cpu().numpy(), xb.cpu().numpy())
+    finally:
+        for op in ops:
+            op.close()
+
+
+def test_batched_mixed_limits_and_host_buffers(s7):
+    probs = make(SHAPES[:5], 400)
+    ops = [s7.stencil7_create(p.nx, p.ny, p.nz, p.coef, storage="f32") for p in probs]
+    try:
+        # maxit 0, 3 (not converged), and converged systems in one batch
+        res = s7.bicgstab_solve_batched(ops, [p.b.copy() for p in probs], tol=1e-6,
+                                        maxit=[0, 3, 500, 500, 2])
+        assert res.rc == s7.ENOTCONV
+        assert res.iters[0] == 0 and res.status[0] == s7.ENOTCONV
+        assert res.iters[1] == 3 and res.status[1] == s7.ENOTCONV
+        assert res.status[2] == 0 and res.status[3] == 0
+        assert res.iters[4] == 2
+        single = s7.bicgstab_solve(ops[2], probs[2].b.copy(), tol=1e-6, maxit=500)
+        assert abs(single.iters - res.iters[2]) <= 3
+        assert rel(res.x[2], single.x.astype(np.float64)) <= 1e-4
+        # duplicate handle rejected
+        with pytest.raises(s7.S7Error):
+            s7.bicgstab_solve_batched([ops[0], ops[0]], [probs[0].b, probs[0].b])
+    finally:
+        for op in ops:
+            op.close()
+
+
+def test_config4_512_systems(s7):
+    """512 systems, cube edges log-uniform in [16,128] (seed 1), FP32, tol 1e-6."""
+    import torch
+    edges = synth.batched_edges(512, seed=1)
+    ops, bs, probs = [], [], []
+    try:
+        for j, e in enumerate(edges):
+            p = synth.varcoef(e, e, e, seed=synth.system_seed(1, j))
+            ops.append(s7.stencil7_create(e, e, e, gu.coef_on_device(p), storage="f32"))
+            bs.append(gu.to_dev(p.b))
+            if j % 97 == 0:
+                probs.append((j, p))
+        res = s7.bicgstab_solve_batched(ops, bs, tol=1e-6, maxit=2000)
+        assert res.rc == 0 and all(s == 0 for s in res.status)
+        assert max(res.resid) <= 1e-6
+        # spot-check systems against the oracle
+        for j, p in probs:
+            orc = ob.bicgstab(p.nx, p.ny, p.nz, p.coef, p.b, tol=1e-6, maxit=2000, storage="f32")
+            assert rel(res.x[j].cpu().numpy(), orc.x) <= 1e-4
+        # every system's true residual, computed on the GPU in float64
+        worst = 0.0
+        for j, op in enumerate(ops):
+            rn, bn = s7.stencil7_residual(op, bs[j], res.x[j])
+            worst = max(worst, rn / bn)
+        assert worst <= 2e-5      # raw system; scaled system at 1e-6 (diagonals within 3x)
+    finally:
+        for op in ops:
+            op.close()
+        torch.cuda.empty_cache()
