@@ -241,6 +241,76 @@ int bicgstab_solve_batched(int nsys, const stencil7_t* hs, const void* const* b,
                            const int* maxit, int* iters, int* status, double* resid,
                            const s7_batch_opts* opts, void* stream);
 
+/* ---- serving: continuous batching of solve requests ----
+ *
+ * A server owns a scheduler thread and a CUDA stream.  Submitted requests
+ * are admitted first come, first served while a slot is free and the device
+ * memory the request will hold fits the budget; admitted requests run
+ * mixed-precision BiCGStab (storage type `storage`, float32 arithmetic) under
+ * float64 iterative refinement on the true float32 operator, to their own
+ * tolerance.  Every request in an inner solve shares the batched step
+ * launches (bicgstab_solve_batched's kernels), so requests that arrive while
+ * others run join the batch at the next tick and leave it when they meet
+ * their tolerance; their Krylov state stays on the device in between.  A
+ * request's arithmetic does not depend on the other requests in the batch.
+ * Latencies are measured on the host's monotonic clock. */
+typedef struct s7_server* s7_server_t;
+
+typedef struct {
+  size_t hbm_budget_bytes; /* device memory admitted requests may hold; 0 = 150 GiB */
+  s7_dtype storage;        /* inner storage type; pass explicitly (S7_BF16 typical) */
+  int max_active;          /* at most this many admitted requests; 0 = 256         */
+  int steps_per_tick;      /* batched steps between host checks; 0 = 4             */
+  int threads, zchunk;     /* batched tile policy; 0 = 128 threads, 16 planes      */
+  double inner_tol;        /* inner relative residual; 0 = 1e-2                    */
+  int inner_maxit;         /* steps per inner solve; 0 = 100                       */
+  int max_outer;           /* refinement steps; 0 = 60                             */
+} s7_server_opts;
+
+typedef struct {
+  int nx, ny, nz;
+  s7_coeffs coeffs;        /* raw operator (host or device)                       */
+  const void* b;           /* right-hand side, nx*ny*nz elements of dt            */
+  void* x;                 /* out: solution (x0 = 0), nx*ny*nz elements of dt     */
+  s7_dtype dt;             /* S7_F64 or S7_F32                                    */
+  double tol;              /* ||b - A x|| / ||b|| to reach (float64, true operator) */
+} s7_request;
+
+typedef struct {
+  int status;              /* S7_OK, S7_ENOTCONV, S7_EBREAKDOWN, S7_ECANCELED, ... */
+  int outer;               /* refinement steps                                     */
+  int inner_iters;         /* inner BiCGStab steps, summed                         */
+  double resid;            /* final ||b - A x|| / ||b||                            */
+  double t_arrive, t_admit, t_done;  /* host monotonic seconds                     */
+} s7_result;
+
+typedef struct {
+  long long completed, failed, queued, active;
+  size_t mem_used, mem_peak;  /* admitted bytes now / at most (model of request_bytes) */
+  double cell_iters;       /* sum over requests of cells x inner steps             */
+  double busy_s;           /* scheduler time spent with work on the device         */
+} s7_server_stats;
+
+/* Create a server on the current device (opts may be NULL: BF16 storage,
+ * defaults above). */
+int s7_server_create(s7_server_t* out, const s7_server_opts* opts);
+/* Queue a request; *id identifies it.  The buffers behind req (coefficients,
+ * b, x) must stay valid until the request has finished.  S7_ENOMEM if the
+ * request alone exceeds the memory budget. */
+int s7_server_submit(s7_server_t s, const s7_request* req, uint64_t* id);
+/* S7_EAGAIN while the request runs; S7_OK with *out once it has finished
+ * (out->status tells how). */
+int s7_server_poll(s7_server_t s, uint64_t id, s7_result* out);
+/* Block until the request finishes or timeout_s passes (negative: no limit);
+ * S7_ETIMEOUT on timeout. */
+int s7_server_wait(s7_server_t s, uint64_t id, s7_result* out, double timeout_s);
+/* Forget a finished request. */
+int s7_server_release(s7_server_t s, uint64_t id);
+int s7_server_get_stats(s7_server_t s, s7_server_stats* out);
+/* Stop the scheduler (queued and running requests end with S7_ECANCELED)
+ * and free everything. */
+int s7_server_destroy(s7_server_t s);
+
 /* Per-kernel timing for benchmarks.  enable = 1 turns timing on for handle
  * h: solves then launch each kernel directly (not from a captured graph)
  * with a CUDA event pair around it on the handle's stream; enable = 0 turns

@@ -29,7 +29,8 @@ __all__ = [
     "stencil7_create", "stencil7_destroy", "stencil7_info", "stencil7_apply",
     "stencil7_residual", "stencil7_residual_noalloc", "bicgstab_solve",
     "bicgstab_solve_refined", "bicgstab_solve_batched", "stencil7_profile", "s7_last_error",
-    "s7_version",
+    "s7_version", "Server", "s7_server_create", "s7_server_submit", "s7_server_poll",
+    "s7_server_wait", "s7_server_release", "s7_server_get_stats", "s7_server_destroy",
 ]
 
 S7_F64, S7_F32, S7_BF16, S7_F16 = 0, 1, 2, 3
@@ -44,7 +45,8 @@ EXPORTS = (
     "stencil7_create", "stencil7_destroy", "stencil7_info", "stencil7_apply",
     "stencil7_residual", "stencil7_residual_noalloc", "bicgstab_solve",
     "bicgstab_solve_refined", "bicgstab_solve_batched", "stencil7_profile", "s7_last_error",
-    "s7_version",
+    "s7_version", "s7_server_create", "s7_server_submit", "s7_server_poll", "s7_server_wait",
+    "s7_server_release", "s7_server_get_stats", "s7_server_destroy",
 )
 PROF_KINDS = ("spmv_p_dot", "spmv_q_dots", "update_dots", "start_residual", "true_residual",
               "other")
@@ -71,6 +73,29 @@ class s7_opts(C.Structure):
 class s7_batch_opts(C.Structure):
     _fields_ = [("threads", C.c_int), ("zchunk", C.c_int), ("check_every", C.c_int),
                 ("no_autotune", C.c_int)]
+
+
+class s7_server_opts(C.Structure):
+    _fields_ = [("hbm_budget_bytes", C.c_size_t), ("storage", C.c_int), ("max_active", C.c_int),
+                ("steps_per_tick", C.c_int), ("threads", C.c_int), ("zchunk", C.c_int),
+                ("inner_tol", C.c_double), ("inner_maxit", C.c_int), ("max_outer", C.c_int)]
+
+
+class s7_request(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("coeffs", s7_coeffs),
+                ("b", C.c_void_p), ("x", C.c_void_p), ("dt", C.c_int), ("tol", C.c_double)]
+
+
+class s7_result(C.Structure):
+    _fields_ = [("status", C.c_int), ("outer", C.c_int), ("inner_iters", C.c_int),
+                ("resid", C.c_double), ("t_arrive", C.c_double), ("t_admit", C.c_double),
+                ("t_done", C.c_double)]
+
+
+class s7_server_stats(C.Structure):
+    _fields_ = [("completed", C.c_longlong), ("failed", C.c_longlong), ("queued", C.c_longlong),
+                ("active", C.c_longlong), ("mem_used", C.c_size_t), ("mem_peak", C.c_size_t),
+                ("cell_iters", C.c_double), ("busy_s", C.c_double)]
 
 
 _lib = None
@@ -104,6 +129,13 @@ def lib():
         "stencil7_profile": (i, [vp, i, P(d), P(C.c_longlong)]),
         "bicgstab_solve_batched": (i, [i, P(vp), P(vp), P(vp), i, P(d), P(i), P(i), P(i), P(d),
                                        P(s7_batch_opts), vp]),
+        "s7_server_create": (i, [P(vp), P(s7_server_opts)]),
+        "s7_server_submit": (i, [vp, P(s7_request), P(C.c_uint64)]),
+        "s7_server_poll": (i, [vp, C.c_uint64, P(s7_result)]),
+        "s7_server_wait": (i, [vp, C.c_uint64, P(s7_result), d]),
+        "s7_server_release": (i, [vp, C.c_uint64]),
+        "s7_server_get_stats": (i, [vp, P(s7_server_stats)]),
+        "s7_server_destroy": (i, [vp]),
         "s7_last_error": (C.c_char_p, []),
         "s7_version": (C.c_char_p, []),
     }
@@ -416,3 +448,108 @@ def bicgstab_solve_batched(ops, bs, xs=None, tol=1e-6, maxit=500, threads=0, zch
                                       C.byref(o), _stream(*bs))
     _check(rc, allow=(EBREAKDOWN, ENOTCONV))
     return BatchResult(xs, list(it), list(stt), list(rs), rc)
+
+
+def _result_dict(r):
+    return {"status": r.status, "outer": r.outer, "inner_iters": r.inner_iters,
+            "resid": r.resid, "t_arrive": r.t_arrive, "t_admit": r.t_admit,
+            "t_done": r.t_done, "latency": r.t_done - r.t_arrive}
+
+
+def s7_server_create(hbm_budget_bytes=0, storage="bf16", max_active=0, steps_per_tick=0,
+                     threads=0, zchunk=0, inner_tol=0.0, inner_maxit=0, max_outer=0):
+    st = _STORAGE[storage] if isinstance(storage, str) else int(storage)
+    o = s7_server_opts(int(hbm_budget_bytes), st, max_active, steps_per_tick, threads, zchunk,
+                       float(inner_tol), inner_maxit, max_outer)
+    h = C.c_void_p()
+    _check(lib().s7_server_create(C.byref(h), C.byref(o)))
+    return h
+
+
+def s7_server_submit(srv, nx, ny, nz, coef, b, x, tol):
+    names = ("diag",) + DIRS
+    raw_dt = _dtype_code(coef["diag"])
+    cs = s7_coeffs(*[_ptr(coef[k]) for k in names], raw_dt, 0)
+    req = s7_request(nx, ny, nz, cs, _ptr(b), _ptr(x), _dtype_code(b), float(tol))
+    rid = C.c_uint64()
+    _check(lib().s7_server_submit(srv, C.byref(req), C.byref(rid)))
+    return rid.value
+
+
+def s7_server_poll(srv, rid):
+    r = s7_result()
+    rc = lib().s7_server_poll(srv, rid, C.byref(r))
+    if rc == EAGAIN:
+        return None
+    _check(rc)
+    return _result_dict(r)
+
+
+def s7_server_wait(srv, rid, timeout=-1.0):
+    r = s7_result()
+    _check(lib().s7_server_wait(srv, rid, C.byref(r), float(timeout)))
+    return _result_dict(r)
+
+
+def s7_server_release(srv, rid):
+    _check(lib().s7_server_release(srv, rid))
+
+
+def s7_server_get_stats(srv):
+    s = s7_server_stats()
+    _check(lib().s7_server_get_stats(srv, C.byref(s)))
+    return {k: getattr(s, k) for k, _ in s7_server_stats._fields_}
+
+
+def s7_server_destroy(srv):
+    return lib().s7_server_destroy(srv)
+
+
+class Server:
+    """A solve server (continuous batching).  Keeps each request's buffers
+    alive until the request has finished."""
+
+    def __init__(self, **kw):
+        self._h = s7_server_create(**kw)
+        self._keep = {}
+
+    def submit(self, nx, ny, nz, coef, b, x=None, tol=1e-6):
+        if x is None:
+            x = _empty_like(b)
+        rid = s7_server_submit(self._h, nx, ny, nz, coef, b, x, tol)
+        self._keep[rid] = (coef, b, x)
+        return rid
+
+    def result(self, rid):
+        return self._keep[rid][2]
+
+    def poll(self, rid):
+        return s7_server_poll(self._h, rid)
+
+    def wait(self, rid, timeout=-1.0):
+        return s7_server_wait(self._h, rid, timeout)
+
+    def release(self, rid):
+        s7_server_release(self._h, rid)
+        return self._keep.pop(rid)[2]
+
+    def stats(self):
+        return s7_server_get_stats(self._h)
+
+    def close(self):
+        if self._h:
+            s7_server_destroy(self._h)
+            self._h = None
+            self._keep.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -64,7 +64,10 @@ static size_t dsize(s7_dtype t) {
   return 0;
 }
 
-static const Engine* engine_for(s7_dtype t) {
+namespace s7 {
+const Engine* engine_for(s7_dtype t);
+}
+const Engine* s7::engine_for(s7_dtype t) {
   switch (t) {
     case S7_F64: return engine_f64();
     case S7_F32: return engine_f32();
@@ -434,7 +437,10 @@ extern "C" int stencil7_info(stencil7_t h, int* nx, int* ny, int* nz, s7_dtype* 
 // ---------------------------------------------------------------------------
 // workspace
 // ---------------------------------------------------------------------------
-static int ensure_ws(Handle* h, int maxit) {
+namespace s7 {
+int ensure_ws(Handle* h, int maxit);
+}
+int s7::ensure_ws(Handle* h, int maxit) {
   Workspace& w = h->ws;
   const Engine* eng = engine_for(h->storage);
   const size_t n = (size_t)h->n, ts = eng->t_size, xs = eng->x_size;

@@ -120,6 +120,11 @@ const Engine* engine_f16();
 
 // Record `msg` as the calling thread's error text; returns `code`.
 int set_error(int code, const char* msg);
+// The engine of a storage type.
+const Engine* engine_for(s7_dtype t);
+// Allocate (once) the solver workspace of a handle, with a history of
+// maxit+1 entries.
+int ensure_ws(Handle* h, int maxit);
 
 // Shape of the sweep grid for a handle (same for every sweep of the handle).
 void default_tile(int nx, int ny, int nz, int vec, int nsm, Tile* t);

@@ -1,0 +1,589 @@
+// The solve server: continuous batching of independent solve requests.
+//
+// Requests (mesh, raw coefficients, right-hand side, tolerance) are queued
+// by s7_server_submit and admitted by a scheduler thread while the device
+// memory they will need fits the server's budget.  Each admitted request
+// runs mixed-precision BiCGStab with float64 iterative refinement as a small
+// state machine:
+//
+//   RESIDUAL  r = b - A x in float64 on the true float32 operator; stop if
+//             ||r||/||b|| <= tol; else start an inner solve of
+//             A~ d = D^-1 r / s (s = ||r||/sqrt(N)) in the storage precision
+//   INNER     BiCGStab steps; every request in this state shares the same
+//             batched kernel launches (one launch per step kernel covers
+//             them all, each with its own grid combine and stop flag)
+//   back to RESIDUAL after x += s d (float64)
+//
+// so requests that arrive while others are on the GPU join the running
+// batch at the next tick, retire as soon as they meet their own tolerance,
+// and give their memory back for the next admissions.  Every request's
+// arithmetic is independent of the others in the batch (own blocks, own
+// reductions, a fixed tile policy), so its result does not depend on what
+// else was running.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "s7_handle.h"
+#include "s7_sweep.cuh"
+
+using namespace s7;
+
+namespace {
+
+double now_s() {
+  using namespace std::chrono;
+  return duration<double>(steady_clock::now().time_since_epoch()).count();
+}
+
+__global__ void k_rhs_scaled(long long n, const double* r, double inv_s, float* f, double* dd) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    if (f) f[i] = (float)(r[i] * inv_s);
+    if (dd) dd[i] = r[i] * inv_s;
+  }
+}
+
+template <class X>
+__global__ void k_axpy_x(long long n, double s, const X* d, double* x) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    x[i] = fma(s, (double)d[i], x[i]);
+}
+
+template <class S, class D>
+__global__ void k_conv(long long n, const S* a, D* b) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    b[i] = (D)a[i];
+}
+
+int grid_of(long long n) {
+  return (int)std::max(1LL, std::min((n + 255) / 256, 152LL * 16));
+}
+
+enum RState { QUEUED = 0, RESIDUAL = 1, INNER_START = 2, INNER = 3, FINISHED = 4 };
+
+struct Req {
+  uint64_t id = 0;
+  s7_request in;
+  double t_arrive = 0, t_admit = 0, t_done = 0;
+  int state = QUEUED;
+  int status = S7_EAGAIN;
+  int outer = 0, inner_total = 0;
+  double resid = 0, s = 0, rel0 = 0;
+  long long n = 0;
+  size_t bytes = 0;
+  int slot = -1;
+  stencil7_t h = nullptr;
+  double *xr = nullptr, *br = nullptr, *rr = nullptr, *parts = nullptr;
+  size_t parts_n = 0;
+};
+
+}  // namespace
+
+struct s7_server {
+  s7_server_opts o;
+  int device = 0;
+  std::thread th;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<Req*> queue;
+  std::vector<Req*> active;
+  std::map<uint64_t, Req*> reqs;
+  uint64_t next_id = 1;
+  size_t mem_used = 0, mem_peak = 0;
+  bool stop = false;
+  // device state shared by all requests
+  cudaStream_t st = nullptr;
+  Scalars* d_sc = nullptr;
+  Scalars* h_sc = nullptr;
+  double* d_hist = nullptr;
+  void* d_desc = nullptr;
+  void* d_desc_start = nullptr;
+  std::vector<int> free_slots;
+  // statistics
+  long long completed = 0, failed = 0;
+  double cell_iters = 0;
+  double busy_s = 0;
+  const Engine* eng = nullptr;
+};
+
+namespace {
+
+size_t request_bytes(const s7_server* S, long long n) {
+  // stored operator, kept diagonal, true float32 operator, seven Krylov
+  // vectors, x and b in float32, three float64 refinement vectors, and the
+  // float32 staging of the raw coefficients while the operator is created
+  const size_t ts = S->eng->t_size;
+  return (size_t)n * (6 * ts + 4 + 28 + 7 * ts + 8 + 24 + 28) + (1 << 20);
+}
+
+Tile serve_tile(const s7_server* S, int nx, int ny, int nz) {
+  const int vec = S->eng->vec;
+  const int T = S->o.threads;
+  const int runs = (nx + vec - 1) / vec;
+  const int cap = std::min(32, T);
+  const int ntx = (runs + cap - 1) / cap;
+  Tile t;
+  t.bx = (runs + ntx - 1) / ntx;
+  t.by = std::max(1, std::min(ny, T / t.bx));
+  t.zchunk = std::max(1, std::min(S->o.zchunk, nz));
+  return t;
+}
+
+void release_req(s7_server* S, Req* r) {
+  if (r->xr) cudaFree(r->xr);
+  if (r->br) cudaFree(r->br);
+  if (r->rr) cudaFree(r->rr);
+  if (r->parts) cudaFree(r->parts);
+  r->xr = r->br = r->rr = r->parts = nullptr;
+  if (r->h) stencil7_destroy(r->h);
+  r->h = nullptr;
+  if (r->slot >= 0) S->free_slots.push_back(r->slot);
+  r->slot = -1;
+}
+
+// Admit one request: operator, workspace, float64 vectors, slot.
+int admit(s7_server* S, Req* r) {
+  s7_opts oo;
+  memset(&oo, 0, sizeof oo);
+  oo.storage = S->o.storage;
+  oo.keep_true = 1;
+  int rc = stencil7_create(&r->h, r->in.nx, r->in.ny, r->in.nz, &r->in.coeffs, &oo);
+  if (rc) return rc;
+  if ((rc = ensure_ws(r->h, S->o.inner_maxit))) return rc;
+  const size_t n = (size_t)r->n;
+  cudaError_t e = cudaSuccess;
+  if ((e = cudaMalloc(&r->xr, n * 8)) != cudaSuccess ||
+      (e = cudaMalloc(&r->br, n * 8)) != cudaSuccess ||
+      (e = cudaMalloc(&r->rr, n * 8)) != cudaSuccess) {
+    cudaGetLastError();
+    return S7_ENOMEM;
+  }
+  const Tile t = serve_tile(S, r->in.nx, r->in.ny, r->in.nz);
+  const long long runs = (r->in.nx + S->eng->vec - 1) / S->eng->vec;
+  const long long nb = ((runs + t.bx - 1) / t.bx) * ((r->in.ny + t.by - 1) / t.by) *
+                       ((r->in.nz + t.zchunk - 1) / t.zchunk);
+  const long long rb = S->eng->raw_resid_blocks(r->h, S7_F64);
+  r->parts_n = 2 * (size_t)std::max(std::max(nb, rb), 4096LL);
+  if ((e = cudaMalloc(&r->parts, r->parts_n * 8)) != cudaSuccess) {
+    cudaGetLastError();
+    return S7_ENOMEM;
+  }
+  // b (host or device, f32/f64) -> float64; x0 = 0
+  if (r->in.dt == S7_F64) {
+    e = cudaMemcpyAsync(r->br, r->in.b, n * 8, cudaMemcpyDefault, S->st);
+  } else {
+    e = cudaMemcpyAsync(r->h->ws.b, r->in.b, n * 4, cudaMemcpyDefault, S->st);
+    if (e == cudaSuccess) {
+      k_conv<float, double><<<grid_of(n), 256, 0, S->st>>>((long long)n, (const float*)r->h->ws.b, r->br);
+      e = cudaGetLastError();
+    }
+  }
+  if (e == cudaSuccess) e = cudaMemsetAsync(r->xr, 0, n * 8, S->st);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return S7_ECUDA;
+  }
+  r->slot = S->free_slots.back();
+  S->free_slots.pop_back();
+  Scalars z;
+  memset(&z, 0, sizeof z);
+  e = cudaMemcpyAsync(S->d_sc + r->slot, &z, sizeof z, cudaMemcpyHostToDevice, S->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(S->st);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return S7_ECUDA;
+  }
+  r->state = RESIDUAL;
+  return S7_OK;
+}
+
+// Copy the float64 iterate to the caller's buffer and retire the request.
+void finish(s7_server* S, Req* r, int status) {
+  const size_t n = (size_t)r->n;
+  if (status == S7_OK || status == S7_ENOTCONV) {
+    cudaError_t e;
+    if (r->in.dt == S7_F64) {
+      e = cudaMemcpyAsync(r->in.x, r->xr, n * 8, cudaMemcpyDefault, S->st);
+    } else {
+      k_conv<double, float><<<grid_of(n), 256, 0, S->st>>>((long long)n, r->xr, (float*)r->h->ws.x);
+      e = cudaMemcpyAsync(r->in.x, r->h->ws.x, n * 4, cudaMemcpyDefault, S->st);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(S->st);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      status = S7_ECUDA;
+    }
+  }
+  release_req(S, r);
+  std::lock_guard<std::mutex> lk(S->mu);
+  r->t_done = now_s();
+  r->status = status;
+  r->state = FINISHED;
+  S->mem_used -= r->bytes;
+  if (status == S7_OK) S->completed++;
+  else S->failed++;
+  S->cv_done.notify_all();
+}
+
+void fail_all(s7_server* S, int status) {
+  for (Req* r : S->active) finish(S, r, status);
+  S->active.clear();
+}
+
+void scheduler(s7_server* S) {
+  cudaSetDevice(S->device);
+  const Engine* eng = S->eng;
+  const int K = S->o.steps_per_tick;
+  std::vector<unsigned char> hd, hds;
+  int sweep_blocks = 0, upd_blocks = 0;
+  size_t smem_max = 0;
+  for (;;) {
+    // ---- admission
+    std::vector<Req*> admit_now;
+    {
+      std::unique_lock<std::mutex> lk(S->mu);
+      if (S->active.empty() && S->queue.empty())
+        S->cv_work.wait(lk, [&] { return S->stop || !S->queue.empty(); });
+      if (S->stop) break;
+      // first come, first served: admit while a slot is free and the
+      // request at the head of the queue fits the memory budget
+      while (!S->queue.empty() && admit_now.size() < S->free_slots.size() &&
+             S->mem_used + S->queue.front()->bytes <= S->o.hbm_budget_bytes) {
+        Req* r = S->queue.front();
+        S->queue.pop_front();
+        S->mem_used += r->bytes;
+        S->mem_peak = std::max(S->mem_peak, S->mem_used);
+        admit_now.push_back(r);
+      }
+    }
+    for (Req* r : admit_now) {
+      r->t_admit = now_s();
+      const int rc = admit(S, r);
+      if (rc) finish(S, r, rc);
+      else S->active.push_back(r);
+    }
+    if (S->active.empty()) continue;
+    const double t0 = now_s();
+
+    // ---- outer residuals
+    bool any_res = false;
+    for (Req* r : S->active)
+      if (r->state == RESIDUAL) {
+        if (eng->raw_resid_into(r->h, r->br, r->xr, r->rr, S7_F64, r->parts, S->d_sc + r->slot,
+                                S->st)) {
+          fail_all(S, S7_ECUDA);
+          break;
+        }
+        any_res = true;
+      }
+    if (S->active.empty()) continue;
+    if (any_res) {
+      if (cudaMemcpyAsync(S->h_sc, S->d_sc, (size_t)S->o.max_active * sizeof(Scalars),
+                          cudaMemcpyDeviceToHost, S->st) != cudaSuccess ||
+          cudaStreamSynchronize(S->st) != cudaSuccess) {
+        cudaGetLastError();
+        fail_all(S, S7_ECUDA);
+        continue;
+      }
+      std::vector<Req*> keep;
+      for (Req* r : S->active) {
+        if (r->state != RESIDUAL) {
+          keep.push_back(r);
+          continue;
+        }
+        const Scalars& sc = S->h_sc[r->slot];
+        const double rn = sqrt(sc.res[0]), bn = sqrt(sc.res[1]);
+        const double rel = bn > 0 ? rn / bn : rn;
+        r->resid = rel;
+        if (r->outer == 0) r->rel0 = rel;
+        if (rel <= r->in.tol || rn == 0.0) {
+          finish(S, r, S7_OK);
+          continue;
+        }
+        if (r->outer >= S->o.max_outer) {
+          finish(S, r, S7_ENOTCONV);
+          continue;
+        }
+        // inner right-hand side r / s with unit RMS, x_inner = 0
+        r->s = rn / sqrt((double)r->n);
+        const bool f64 = S->o.storage == S7_F64;
+        k_rhs_scaled<<<grid_of(r->n), 256, 0, S->st>>>(
+            r->n, r->rr, 1.0 / r->s, f64 ? nullptr : (float*)r->h->ws.b,
+            f64 ? (double*)r->h->ws.b : nullptr);
+        cudaMemsetAsync(r->h->ws.x, 0, (size_t)r->n * eng->x_size, S->st);
+        Scalars z;
+        memset(&z, 0, sizeof z);
+        z.tol = S->o.inner_tol;
+        z.maxit = S->o.inner_maxit;
+        z.status = S7_ENOTCONV;
+        cudaMemcpyAsync(S->d_sc + r->slot, &z, sizeof z, cudaMemcpyHostToDevice, S->st);
+        r->outer++;
+        r->state = INNER_START;
+        keep.push_back(r);
+      }
+      S->active.swap(keep);
+    }
+    if (S->active.empty()) continue;
+
+    // ---- batched inner solves: start the new ones, then K shared steps
+    std::vector<Req*> inner, starting;
+    for (Req* r : S->active)
+      if (r->state == INNER_START || r->state == INNER) inner.push_back(r);
+    for (Req* r : inner)
+      if (r->state == INNER_START) starting.push_back(r);
+    auto layout = [&](const std::vector<Req*>& set, std::vector<unsigned char>& host, void* dev,
+                      int* nb_total, int* ub_total, size_t* smem) {
+      host.resize(set.size() * eng->desc_size);
+      int b0 = 0, u0 = 0;
+      size_t sm = 0;
+      for (size_t j = 0; j < set.size(); ++j) {
+        Req* r = set[j];
+        const Tile t = serve_tile(S, r->in.nx, r->in.ny, r->in.nz);
+        int nb = 0, ub = 0;
+        eng->fill_desc(r->h, host.data() + j * eng->desc_size, t, r->h->ws.b, r->parts,
+                       S->d_hist + (size_t)r->slot * (S->o.inner_maxit + 1), S->d_sc + r->slot,
+                       b0, u0, &nb, &ub);
+        b0 += nb;
+        u0 += ub;
+        sm = std::max(sm, eng->batched_smem(r->h, t));
+      }
+      *nb_total = b0;
+      *ub_total = u0;
+      *smem = sm;
+      return cudaMemcpyAsync(dev, host.data(), host.size(), cudaMemcpyHostToDevice, S->st);
+    };
+    int rc = S7_OK;
+    if (!starting.empty()) {
+      int nbs = 0, ubs = 0;
+      size_t sms = 0;
+      if (layout(starting, hds, S->d_desc_start, &nbs, &ubs, &sms) != cudaSuccess) rc = S7_ECUDA;
+      if (!rc && sms > smem_max) {
+        smem_max = sms;
+        rc = eng->batched_prepare(smem_max);
+      }
+      if (!rc) rc = eng->launch_batched(2, S->d_desc_start, (int)starting.size(), nbs,
+                                        S->o.threads, sms, S->st);
+      if (!rc) rc = eng->launch_batched(5, S->d_desc_start, (int)starting.size(), 0, 0, 0, S->st);
+      for (Req* r : starting) r->state = INNER;
+    }
+    if (!rc) {
+      // the membership changes as requests start and finish inner solves:
+      // lay the batch out again every tick (a few hundred bytes per request)
+      size_t sm = 0;
+      if (layout(inner, hd, S->d_desc, &sweep_blocks, &upd_blocks, &sm) != cudaSuccess) rc = S7_ECUDA;
+      if (!rc && sm > smem_max) {
+        smem_max = sm;
+        rc = eng->batched_prepare(smem_max);
+      }
+    }
+    for (int k = 0; k < K && !rc; ++k) {
+      rc = eng->launch_batched(0, S->d_desc, (int)inner.size(), sweep_blocks, S->o.threads,
+                               smem_max, S->st);
+      if (!rc) rc = eng->launch_batched(1, S->d_desc, (int)inner.size(), sweep_blocks,
+                                        S->o.threads, smem_max, S->st);
+      if (!rc) rc = eng->launch_batched(4, S->d_desc, (int)inner.size(), upd_blocks, 256, 0, S->st);
+    }
+    if (!rc && (cudaMemcpyAsync(S->h_sc, S->d_sc, (size_t)S->o.max_active * sizeof(Scalars),
+                                cudaMemcpyDeviceToHost, S->st) != cudaSuccess ||
+                cudaStreamSynchronize(S->st) != cudaSuccess))
+      rc = S7_ECUDA;
+    if (rc) {
+      cudaGetLastError();
+      fail_all(S, rc);
+      continue;
+    }
+    std::vector<Req*> keep;
+    for (Req* r : S->active) {
+      if (r->state == INNER && S->h_sc[r->slot].done) {
+        const Scalars& sc = S->h_sc[r->slot];
+        r->inner_total += sc.iter;
+        S->cell_iters += (double)r->n * sc.iter;
+        if (sc.status == S7_EBREAKDOWN && sc.iter == 0) {
+          finish(S, r, S7_EBREAKDOWN);
+          continue;
+        }
+        if (S->o.storage == S7_F64)
+          k_axpy_x<double><<<grid_of(r->n), 256, 0, S->st>>>(r->n, r->s, (const double*)r->h->ws.x, r->xr);
+        else
+          k_axpy_x<float><<<grid_of(r->n), 256, 0, S->st>>>(r->n, r->s, (const float*)r->h->ws.x, r->xr);
+        r->state = RESIDUAL;
+      }
+      keep.push_back(r);
+    }
+    S->active.swap(keep);
+    S->busy_s += now_s() - t0;
+  }
+  // shut down: fail what is left
+  fail_all(S, S7_ECANCELED);
+  std::lock_guard<std::mutex> lk(S->mu);
+  for (Req* r : S->queue) {
+    r->status = S7_ECANCELED;
+    r->state = FINISHED;
+  }
+  S->queue.clear();
+  S->cv_done.notify_all();
+}
+
+void fill_result(const Req* r, s7_result* out) {
+  out->status = r->status;
+  out->outer = r->outer;
+  out->inner_iters = r->inner_total;
+  out->resid = r->resid;
+  out->t_arrive = r->t_arrive;
+  out->t_admit = r->t_admit;
+  out->t_done = r->t_done;
+}
+
+}  // namespace
+
+extern "C" int s7_server_create(s7_server_t* out, const s7_server_opts* o) {
+  if (!out) return set_error(S7_EINVAL, "s7_server_create: out is NULL");
+  *out = nullptr;
+  s7_server_opts opts;
+  memset(&opts, 0, sizeof opts);
+  if (o) opts = *o;
+  if (opts.storage == S7_F64 && !o) opts.storage = S7_BF16;
+  if (opts.hbm_budget_bytes == 0) opts.hbm_budget_bytes = (size_t)150 << 30;
+  if (opts.max_active <= 0) opts.max_active = 256;
+  if (opts.steps_per_tick <= 0) opts.steps_per_tick = 4;
+  if (opts.threads <= 0) opts.threads = 128;
+  opts.threads = std::max(64, std::min(256, opts.threads));
+  if (opts.zchunk <= 0) opts.zchunk = 16;
+  if (!(opts.inner_tol > 0)) opts.inner_tol = 1e-2;
+  if (opts.inner_maxit <= 0) opts.inner_maxit = 100;
+  if (opts.max_outer <= 0) opts.max_outer = 60;
+  s7_server* S = new (std::nothrow) s7_server();
+  if (!S) return set_error(S7_ENOMEM, "s7_server_create: host allocation failed");
+  S->o = opts;
+  S->eng = engine_for(opts.storage);
+  if (!S->eng) {
+    delete S;
+    return set_error(S7_EINVAL, "s7_server_create: bad storage type");
+  }
+  cudaGetDevice(&S->device);
+  cudaError_t e = cudaStreamCreateWithFlags(&S->st, cudaStreamNonBlocking);
+  const size_t ns = (size_t)opts.max_active;
+  if (e == cudaSuccess) e = cudaMalloc(&S->d_sc, ns * sizeof(Scalars));
+  if (e == cudaSuccess) e = cudaMemset(S->d_sc, 0, ns * sizeof(Scalars));
+  if (e == cudaSuccess) e = cudaMallocHost(&S->h_sc, ns * sizeof(Scalars));
+  if (e == cudaSuccess) e = cudaMalloc(&S->d_hist, ns * (opts.inner_maxit + 1) * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&S->d_desc, ns * S->eng->desc_size);
+  if (e == cudaSuccess) e = cudaMalloc(&S->d_desc_start, ns * S->eng->desc_size);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    s7_server_destroy(S);
+    return set_error(S7_ENOMEM, "s7_server_create: device allocation failed");
+  }
+  for (int i = (int)ns - 1; i >= 0; --i) S->free_slots.push_back(i);
+  S->th = std::thread(scheduler, S);
+  *out = S;
+  return S7_OK;
+}
+
+extern "C" int s7_server_submit(s7_server_t S, const s7_request* r, uint64_t* id) {
+  if (!S || !r || !r->b || !r->x) return set_error(S7_EINVAL, "s7_server_submit: bad arguments");
+  if (r->nx < 1 || r->ny < 1 || r->nz < 1 || (r->dt != S7_F64 && r->dt != S7_F32) || !(r->tol > 0))
+    return set_error(S7_EINVAL, "s7_server_submit: bad sizes, dtype or tol");
+  Req* q = new (std::nothrow) Req();
+  if (!q) return set_error(S7_ENOMEM, "s7_server_submit: host allocation failed");
+  q->in = *r;
+  q->n = (long long)r->nx * r->ny * r->nz;
+  q->bytes = request_bytes(S, q->n);
+  if (q->bytes > S->o.hbm_budget_bytes) {
+    delete q;
+    return set_error(S7_ENOMEM, "s7_server_submit: request larger than the memory budget");
+  }
+  std::lock_guard<std::mutex> lk(S->mu);
+  if (S->stop) {
+    delete q;
+    return set_error(S7_ECANCELED, "s7_server_submit: server is stopping");
+  }
+  q->id = S->next_id++;
+  q->t_arrive = now_s();
+  S->reqs[q->id] = q;
+  S->queue.push_back(q);
+  if (id) *id = q->id;
+  S->cv_work.notify_one();
+  return S7_OK;
+}
+
+extern "C" int s7_server_poll(s7_server_t S, uint64_t id, s7_result* out) {
+  if (!S || !out) return set_error(S7_EINVAL, "s7_server_poll: bad arguments");
+  std::lock_guard<std::mutex> lk(S->mu);
+  auto it = S->reqs.find(id);
+  if (it == S->reqs.end()) return set_error(S7_EINVAL, "s7_server_poll: unknown request");
+  if (it->second->state != FINISHED) return S7_EAGAIN;
+  fill_result(it->second, out);
+  return S7_OK;
+}
+
+extern "C" int s7_server_wait(s7_server_t S, uint64_t id, s7_result* out, double timeout_s) {
+  if (!S || !out) return set_error(S7_EINVAL, "s7_server_wait: bad arguments");
+  std::unique_lock<std::mutex> lk(S->mu);
+  auto it = S->reqs.find(id);
+  if (it == S->reqs.end()) return set_error(S7_EINVAL, "s7_server_wait: unknown request");
+  Req* r = it->second;
+  const auto pred = [&] { return r->state == FINISHED; };
+  if (timeout_s < 0) S->cv_done.wait(lk, pred);
+  else if (!S->cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s), pred))
+    return set_error(S7_ETIMEOUT, "s7_server_wait: timed out");
+  fill_result(r, out);
+  return S7_OK;
+}
+
+extern "C" int s7_server_release(s7_server_t S, uint64_t id) {
+  if (!S) return set_error(S7_EINVAL, "s7_server_release: NULL server");
+  std::lock_guard<std::mutex> lk(S->mu);
+  auto it = S->reqs.find(id);
+  if (it == S->reqs.end()) return set_error(S7_EINVAL, "s7_server_release: unknown request");
+  if (it->second->state != FINISHED) return set_error(S7_EAGAIN, "s7_server_release: not finished");
+  delete it->second;
+  S->reqs.erase(it);
+  return S7_OK;
+}
+
+extern "C" int s7_server_get_stats(s7_server_t S, s7_server_stats* out) {
+  if (!S || !out) return set_error(S7_EINVAL, "s7_server_get_stats: bad arguments");
+  std::lock_guard<std::mutex> lk(S->mu);
+  out->completed = S->completed;
+  out->failed = S->failed;
+  out->queued = (long long)S->queue.size();
+  out->active = (long long)S->active.size();
+  out->mem_used = S->mem_used;
+  out->mem_peak = S->mem_peak;
+  out->cell_iters = S->cell_iters;
+  out->busy_s = S->busy_s;
+  return S7_OK;
+}
+
+extern "C" int s7_server_destroy(s7_server_t S) {
+  if (!S) return S7_OK;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->stop = true;
+    S->cv_work.notify_all();
+  }
+  if (S->th.joinable()) S->th.join();
+  for (auto& kv : S->reqs) delete kv.second;
+  S->reqs.clear();
+  if (S->st) cudaStreamSynchronize(S->st);
+  if (S->d_sc) cudaFree(S->d_sc);
+  if (S->h_sc) cudaFreeHost(S->h_sc);
+  if (S->d_hist) cudaFree(S->d_hist);
+  if (S->d_desc) cudaFree(S->d_desc);
+  if (S->d_desc_start) cudaFree(S->d_desc_start);
+  if (S->st) cudaStreamDestroy(S->st);
+  delete S;
+  return S7_OK;
+}
