@@ -40,12 +40,20 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "cell-iters/s & HBM GB/s (BiCGStab 7-pt, 600×595×1536); p99 solve latency"
-# algorithmic HBM bytes per cell per launch of each kernel (float32 storage):
+# Algorithmic HBM bytes per cell per launch of each step kernel:
 # sweep 1: 6 coefficients + r, p_old, s_old, r0 read + p, s written
 # sweep 2: 6 coefficients + r, s read + y written
 # update : x, p, r, s, y, r0 read + x, r written
-BYTES_PER_CELL = {"spmv_p_dot": 48, "spmv_q_dots": 36, "update_dots": 32}
-ITER_BYTES_PER_CELL = 116
+
+
+def bytes_per_cell(storage):
+    """Algorithmic HBM bytes per cell of each step kernel: w_c = w_v = storage
+    size, w_x = 8 for float64 storage else 4 (12 w_c + 15 w_v + 2 w_x per step)."""
+    w = {"f64": 8, "f32": 4, "bf16": 2, "f16": 2}[storage]
+    wx = 8 if storage == "f64" else 4
+    k = {"spmv_p_dot": 6 * w + 6 * w, "spmv_q_dots": 6 * w + 3 * w,
+         "update_dots": 5 * w + wx + w + wx}
+    return k, sum(k.values())
 FLOPS_PER_CELL = 44          # Table I of the paper
 PAPER_CS1_CELL_ITERS = 548352000 / 28.1e-6   # Sec. V, CS-1, mixed 16/32-bit
 
@@ -56,6 +64,14 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="solve", choices=["solve", "refined", "batched", "serve"],
+                    help="solve: FP32 600x595x1536 (default); refined: 512^3 BF16/FP16 vs FP32 "
+                         "storage with FP64 refinement; batched: 512 systems; serve: request stream")
+    ap.add_argument("--edge", type=int, default=512, help="refined: cube edge")
+    ap.add_argument("--systems", type=int, default=512, help="batched: number of systems")
+    ap.add_argument("--requests", type=int, default=300, help="serve: requests")
+    ap.add_argument("--rate", type=float, default=30.0, help="serve: arrivals per second")
+    ap.add_argument("--pool", type=int, default=24, help="serve: distinct problems drawn")
     ap.add_argument("--nx", type=int, default=600)
     ap.add_argument("--ny", type=int, default=595)
     ap.add_argument("--nz", type=int, default=1536)
@@ -299,28 +315,29 @@ def run_ours(args):
     value = n * total_iters / (elapsed_ms / 1e3)
 
     peak, peak_kind = measured_peaks()
+    bpc, iter_bpc = bytes_per_cell(args.storage)
     kern = {}
     for k, (ms, cnt) in prof.items():
         if cnt == 0:
             continue
         avg = ms / cnt
         e = {"launches": int(cnt), "avg_ms": avg, "share": None}
-        if k in BYTES_PER_CELL:
-            gbs = BYTES_PER_CELL[k] * n / (avg / 1e3) / 1e9
-            e.update({"alg_bytes_per_launch": BYTES_PER_CELL[k] * n, "gbs": gbs,
+        if k in bpc:
+            gbs = bpc[k] * n / (avg / 1e3) / 1e9
+            e.update({"alg_bytes_per_launch": bpc[k] * n, "gbs": gbs,
                       "frac": gbs / peak})
         kern[k] = e
     tot_ms = sum(v["avg_ms"] * v["launches"] for v in kern.values())
     for v in kern.values():
         v["share"] = v["avg_ms"] * v["launches"] / tot_ms if tot_ms else None
-    dom = max((k for k in kern if k in BYTES_PER_CELL),
+    dom = max((k for k in kern if k in bpc),
               key=lambda k: kern[k]["avg_ms"] * kern[k]["launches"])
-    traffic = ncu_traffic(dom, n)
+    traffic = ncu_traffic(dom, n) if args.storage == "f32" else None
     roofline = {"bound": "hbm", "kernel": dom, "achieved": kern[dom]["gbs"], "peak": peak,
                 "unit": "GB/s", "frac": kern[dom]["gbs"] / peak, "peak_kind": peak_kind,
                 "traffic": traffic}
     iter_ms = elapsed_ms / (done_iters if done_iters else 1)
-    hbm_gbs = ITER_BYTES_PER_CELL * n * total_iters / (elapsed_ms / 1e3) / 1e9
+    hbm_gbs = iter_bpc * n * total_iters / (elapsed_ms / 1e3) / 1e9
     launches = int(sum(c for _, c in prof.values()))
 
     # end to end through the C ABI with pinned host buffers (rank-local)
@@ -391,10 +408,194 @@ def run_e2e(args, s7, prob, dev):
                         "pinned host b/x (%d iterations) + destroy" % args.iters}
 
 
+# ---------------------------------------------------------------------------
+# other workloads (not the default line)
+# ---------------------------------------------------------------------------
+
+def _timed(fn, steps, warmup):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    outs = []
+    ev0.record()
+    for _ in range(steps):
+        outs.append(fn())
+    ev1.record()
+    torch.cuda.synchronize()
+    return ev0.elapsed_time(ev1) / steps, outs
+
+
+def run_refined(args):
+    """512^3, seed 2: refined solves to 1e-8 and 1e-10 with BF16, FP16 and FP32
+    storage (FP32 arithmetic, FP64 outer residual on the true operator)."""
+    import torch
+    import synth
+    import paper_2010_03660_gb300 as s7
+    from oracle import stencil
+    s7.lib()
+    e = args.edge
+    p = synth.varcoef(e, e, e, seed=2)
+    dev = torch.device("cuda:0")
+    b = torch.from_numpy(p.b.astype(np.float64)).to(dev)
+    coef = {k: torch.from_numpy(v).to(dev) for k, v in p.coef.items()}
+    runs = {}
+    rng = np.random.default_rng(0)
+    idx = rng.integers(0, p.n, 2000)
+    for storage in ("bf16", "f16", "f32"):
+        op = s7.stencil7_create(e, e, e, coef, storage=storage, keep_true=True)
+        inner_tol = 1e-2 if storage != "f32" else 1e-5
+        for tol in (1e-8, 1e-10):
+            def fn():
+                return s7.bicgstab_solve_refined(op, b, tol=tol, max_outer=80, inner_maxit=200,
+                                                 inner_tol=inner_tol)
+            ms, outs = _timed(fn, args.steps, min(args.warmup, 2))
+            r = outs[-1]
+            rr = torch.empty_like(b)
+            rn, bn = s7.stencil7_residual(op, b, r.x, rr)
+            # the certified residual, verified on sampled rows by the oracle
+            cf, _ = synth.varcoef_at(e, e, e, idx, seed=2)
+            xg = r.x
+            def x_at(j):
+                return xg[torch.from_numpy(np.asarray(j)).to(dev)].cpu().numpy()
+            ax, mag = stencil.apply_at(e, e, e, cf, x_at, idx)
+            ref = p.b.astype(np.float64)[idx] - ax
+            got = rr[torch.from_numpy(idx).to(dev)].cpu().numpy()
+            row_err = float(np.max(np.abs(got - ref) / (mag + np.abs(p.b[idx]))))
+            runs["%s_tol%g" % (storage, tol)] = {
+                "ms": ms, "outer": r.outer, "inner_iters": r.inner_total, "status": r.status,
+                "true_resid": rn / bn, "oracle_row_check": row_err, "inner_tol": inner_tol,
+                "inner_cell_iters_per_s": p.n * r.inner_total / (ms / 1e3)}
+        op.close()
+    base = runs["f32_tol1e-08"]["ms"]
+    out = {"metric": "time to relative residual 1e-10, mixed precision (BF16 storage) + FP64 refinement",
+           "value": runs["bf16_tol1e-10"]["ms"] / 1e3, "unit": "s", "higher_is_better": False,
+           "workload": "refined_%d^3" % e, "dtype": "bf16/f16/f32 storage, f32 arithmetic, f64 outer",
+           "data": "synthetic (seed 2)", "runs": runs,
+           "speedup_vs_fp32_storage_to_1e-8": {k: base / runs["%s_tol1e-08" % k]["ms"]
+                                               for k in ("bf16", "f16")},
+           "steps": args.steps}
+    print(json.dumps(out))
+
+
+def run_batched(args):
+    """512 systems, cube edges log-uniform in [16,128] (seed 1), FP32, tol 1e-6."""
+    import torch
+    import synth
+    import paper_2010_03660_gb300 as s7
+    s7.lib()
+    dev = torch.device("cuda:0")
+    edges = synth.batched_edges(args.systems, seed=1)
+    ops, bs = [], []
+    for j, e in enumerate(edges):
+        p = synth.varcoef(e, e, e, seed=synth.system_seed(1, j))
+        ops.append(s7.stencil7_create(e, e, e, {k: torch.from_numpy(v).to(dev)
+                                                for k, v in p.coef.items()}, storage="f32"))
+        bs.append(torch.from_numpy(p.b).to(dev))
+    cells = [e ** 3 for e in edges]
+    xs = [torch.zeros_like(b) for b in bs]
+
+    def fn():
+        for x in xs:
+            x.zero_()
+        return s7.bicgstab_solve_batched(ops, bs, xs, tol=1e-6, maxit=2000)
+    ms, outs = _timed(fn, args.steps, max(1, args.warmup))
+    r = outs[-1]
+    ci = sum(c * it for c, it in zip(cells, r.iters))
+    # the same systems one after another through bicgstab_solve
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    seq_ci = 0
+    for op, b, x, c in zip(ops, bs, xs, cells):
+        x.zero_()
+        rs = s7.bicgstab_solve(op, b, x, tol=1e-6, maxit=2000, history=False, true_resid=False)
+        seq_ci += c * rs.iters
+    torch.cuda.synchronize()
+    seq_s = time.perf_counter() - t0
+    out = {"metric": "batched cell-iters/s (512 systems, edges 16..128, FP32, tol 1e-6)",
+           "value": ci / (ms / 1e3), "unit": "cell-iters/s", "higher_is_better": True,
+           "workload": "batched_%d" % args.systems, "dtype": "f32", "data": "synthetic (seed 1)",
+           "ms_per_batch_solve": ms, "systems": len(ops), "total_cells": int(sum(cells)),
+           "iters_min_max": [min(r.iters), max(r.iters)], "all_converged": r.rc == 0,
+           "hbm_gbs": 116 * ci / (ms / 1e3) / 1e9,
+           "sequential_single_solves": {"s": seq_s, "cell_iters_per_s": seq_ci / seq_s},
+           "speedup_vs_sequential": (seq_s * 1e3) / ms, "steps": args.steps}
+    for op in ops:
+        op.close()
+    print(json.dumps(out))
+
+
+def run_serve(args):
+    """Poisson stream of solve requests (config: edges log-uniform in
+    [32,384], aspect [0.5,2], tol in {1e-4,1e-6,1e-8}, BF16 + FP64
+    refinement, 150 GB budget).  Inputs of `--pool` distinct requests are
+    generated up front and reused by the stream (each request keeps its own
+    arrival time and tolerance)."""
+    import threading
+    import torch
+    import synth
+    import paper_2010_03660_gb300 as s7
+    s7.lib()
+    reqs = synth.request_stream(args.requests, rate=args.rate, seed=3)
+    pool = []
+    for q in reqs[:args.pool]:
+        p = synth.varcoef(q.nx, q.ny, q.nz, seed=q.seed)
+        pin = {k: torch.from_numpy(v).pin_memory() for k, v in p.coef.items()}
+        pool.append((q.nx, q.ny, q.nz, pin, torch.from_numpy(p.b.astype(np.float64)).pin_memory()))
+    srv = s7.Server(storage="bf16", hbm_budget_bytes=150 << 30)
+    ids = [None] * len(reqs)
+    t_start = time.perf_counter()
+    arr0 = reqs[0].arrival
+
+    def producer():
+        for j, q in enumerate(reqs):
+            delay = (q.arrival - arr0) - (time.perf_counter() - t_start)
+            if delay > 0:
+                time.sleep(delay)
+            nx, ny, nz, coef, b = pool[j % len(pool)]
+            x = torch.empty(nx * ny * nz, dtype=torch.float64).pin_memory()
+            ids[j] = srv.submit(nx, ny, nz, coef, b, x, q.tol)
+
+    th = threading.Thread(target=producer)
+    th.start()
+    lat, cells_done, statuses = [], 0, []
+    for j in range(len(reqs)):
+        while ids[j] is None:
+            time.sleep(0.0005)
+        r = srv.wait(ids[j], timeout=600)
+        statuses.append(r["status"])
+        lat.append(r["latency"])
+        srv.release(ids[j])
+    th.join()
+    wall = time.perf_counter() - t_start
+    st = srv.stats()
+    srv.close()
+    warm = min(20, len(lat) // 10)
+    l = np.array(lat[warm:])
+    out = {"metric": "p99 solve latency (serving, BF16 + FP64 refinement)",
+           "value": float(np.percentile(l, 99)), "unit": "s", "higher_is_better": False,
+           "p50_s": float(np.percentile(l, 50)), "p99_s": float(np.percentile(l, 99)),
+           "mean_s": float(l.mean()), "requests": len(reqs), "warmup_requests": warm,
+           "rate_per_s": args.rate, "pool": len(pool), "completed": int(st["completed"]),
+           "failed": int(st["failed"]), "statuses_ok": int(sum(1 for s_ in statuses if s_ == 0)),
+           "wall_s": wall, "cell_iters_per_s": st["cell_iters"] / wall,
+           "mem_peak_gb": st["mem_peak"] / 1e9, "workload": "serve_%d_at_%g" % (len(reqs), args.rate),
+           "data": "synthetic (seed 3)"}
+    print(json.dumps(out))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "refined":
+        run_refined(args)
+    elif args.workload == "batched":
+        run_batched(args)
+    elif args.workload == "serve":
+        run_serve(args)
     else:
         run_ours(args)
 

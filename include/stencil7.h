@@ -107,7 +107,7 @@ typedef struct {
   int check_every;   /* iterations per CUDA-graph launch between host checks
                         of the device convergence flag; 0 = default            */
   int stages;        /* depth of the asynchronous-copy pipeline of the two SpMV
-                        sweeps of a step: 2 or 3 shared-memory stages; 1 = no
+                        sweeps of a step: 2 to 4 shared-memory stages; 1 = no
                         pipeline (direct loads); 0 = default                   */
   int pipe_kinds;    /* which sweeps use that pipeline: bit 0 = the p-update +
                         s = A p sweep, bit 1 = the q + y = A q sweep;

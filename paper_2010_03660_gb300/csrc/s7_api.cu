@@ -293,11 +293,14 @@ extern "C" int stencil7_create(stencil7_t* out, int nx, int ny, int nz, const s7
     int ce = (int)std::min(64.0, std::max(2.0, 1000.0 / est_us));
     h->check_every = opts.check_every > 0 ? opts.check_every : ce;
   }
-  h->stages = opts.stages > 0 ? std::min(opts.stages, 3) : 2;
-  // measured on GB300 (600x595 planes, f32): the pipeline helps the p/s
-  // sweep, whose register version is limited by occupancy, and not the
-  // q/y sweep
-  h->pipe_kinds = opts.pipe_kinds > 0 ? (opts.pipe_kinds & 3) : 1;
+  // Defaults measured on GB300.  float32/float64 (600x595 planes): a
+  // 2-stage pipeline helps the p/s sweep, whose register version is limited
+  // by occupancy, and not the q/y sweep.  16-bit storage (512^2 planes):
+  // both sweeps are bound by the per-plane latency chain at half the bytes
+  // per cell, so both take a 3-stage pipeline.
+  const bool half = opts.storage == S7_BF16 || opts.storage == S7_F16;
+  h->stages = opts.stages > 0 ? std::min(opts.stages, 4) : (half ? 3 : 2);
+  h->pipe_kinds = opts.pipe_kinds > 0 ? (opts.pipe_kinds & 3) : (half ? 3 : 1);
   if (!eng->smem_ok(h)) {
     delete h;
     return fail(S7_EINVAL, "stencil7_create: tile too large for shared memory");

@@ -228,7 +228,10 @@ struct EngineImpl {
   typedef X_ X;
   typedef DT_ DT;
   typedef A_ A;
-  static constexpr int VEC = 16 / (int)sizeof(T);
+  // cells per thread: 16-byte vectors for 32/64-bit storage; 16-bit storage
+  // keeps 4 cells (8-byte vectors) so per-thread state, and with it
+  // occupancy, matches the float32 kernels
+  static constexpr int VEC = sizeof(T) >= 4 ? 16 / (int)sizeof(T) : 4;
 
   template <class AA>
   static CoefView<T, AA> stored(const Handle* h) {
@@ -337,7 +340,9 @@ struct EngineImpl {
     for (int kind = 0; kind < 2; ++kind) {
       if (!pipelined(h, g, kind)) continue;
       const size_t b = step_smem_bytes<T, A, VEC>(g.bx, g.by, h->stages, kind);
-      if (h->stages == 3)
+      if (h->stages == 4)
+        set(kind == 0 ? (const void*)k_step<T, A, VEC, 0, 4> : (const void*)k_step<T, A, VEC, 1, 4>, b);
+      else if (h->stages == 3)
         set(kind == 0 ? (const void*)k_step<T, A, VEC, 0, 3> : (const void*)k_step<T, A, VEC, 1, 3>, b);
       else
         set(kind == 0 ? (const void*)k_step<T, A, VEC, 0, 2> : (const void*)k_step<T, A, VEC, 1, 2>, b);
@@ -357,8 +362,10 @@ struct EngineImpl {
     const bool vl = (h->nx % VEC == 0);
     if (which < 2 && pipelined(h, g, which)) {
       if (which == 0)
-        return h->stages == 3 ? launch_step<0, 3>(h, g, st) : launch_step<0, 2>(h, g, st);
-      return h->stages == 3 ? launch_step<1, 3>(h, g, st) : launch_step<1, 2>(h, g, st);
+        return h->stages == 4 ? launch_step<0, 4>(h, g, st)
+             : h->stages == 3 ? launch_step<0, 3>(h, g, st) : launch_step<0, 2>(h, g, st);
+      return h->stages == 4 ? launch_step<1, 4>(h, g, st)
+           : h->stages == 3 ? launch_step<1, 3>(h, g, st) : launch_step<1, 2>(h, g, st);
     }
     if (which == 0) {
       SrcPUpdate<T, A> sa;

@@ -93,9 +93,13 @@ struct Req {
 struct s7_server {
   s7_server_opts o;
   int device = 0;
-  std::thread th;
+  std::thread th;        // scheduler: ticks of batched work
+  std::thread th_admit;  // admission: operator set-up and uploads
+  std::deque<Req*> ready;  // admitted, set up, not yet picked up by the scheduler
+  cudaStream_t st_admit = nullptr;
   std::mutex mu;
-  std::condition_variable cv_work, cv_done;
+  std::condition_variable cv_work, cv_done, cv_ready;
+  int admitting = 0;
   std::deque<Req*> queue;
   std::vector<Req*> active;
   std::map<uint64_t, Req*> reqs;
@@ -148,7 +152,10 @@ void release_req(s7_server* S, Req* r) {
   r->xr = r->br = r->rr = r->parts = nullptr;
   if (r->h) stencil7_destroy(r->h);
   r->h = nullptr;
-  if (r->slot >= 0) S->free_slots.push_back(r->slot);
+  if (r->slot >= 0) {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->free_slots.push_back(r->slot);
+  }
   r->slot = -1;
 }
 
@@ -180,26 +187,30 @@ int admit(s7_server* S, Req* r) {
     return S7_ENOMEM;
   }
   // b (host or device, f32/f64) -> float64; x0 = 0
+  cudaStream_t as = S->st_admit;
   if (r->in.dt == S7_F64) {
-    e = cudaMemcpyAsync(r->br, r->in.b, n * 8, cudaMemcpyDefault, S->st);
+    e = cudaMemcpyAsync(r->br, r->in.b, n * 8, cudaMemcpyDefault, as);
   } else {
-    e = cudaMemcpyAsync(r->h->ws.b, r->in.b, n * 4, cudaMemcpyDefault, S->st);
+    e = cudaMemcpyAsync(r->h->ws.b, r->in.b, n * 4, cudaMemcpyDefault, as);
     if (e == cudaSuccess) {
-      k_conv<float, double><<<grid_of(n), 256, 0, S->st>>>((long long)n, (const float*)r->h->ws.b, r->br);
+      k_conv<float, double><<<grid_of(n), 256, 0, as>>>((long long)n, (const float*)r->h->ws.b, r->br);
       e = cudaGetLastError();
     }
   }
-  if (e == cudaSuccess) e = cudaMemsetAsync(r->xr, 0, n * 8, S->st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(r->xr, 0, n * 8, as);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return S7_ECUDA;
   }
-  r->slot = S->free_slots.back();
-  S->free_slots.pop_back();
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    r->slot = S->free_slots.back();
+    S->free_slots.pop_back();
+  }
   Scalars z;
   memset(&z, 0, sizeof z);
-  e = cudaMemcpyAsync(S->d_sc + r->slot, &z, sizeof z, cudaMemcpyHostToDevice, S->st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(S->st);
+  e = cudaMemcpyAsync(S->d_sc + r->slot, &z, sizeof z, cudaMemcpyHostToDevice, as);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(as);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return S7_ECUDA;
@@ -234,11 +245,52 @@ void finish(s7_server* S, Req* r, int status) {
   if (status == S7_OK) S->completed++;
   else S->failed++;
   S->cv_done.notify_all();
+  S->cv_work.notify_all();   // memory came back: the admission thread re-checks
 }
 
 void fail_all(s7_server* S, int status) {
-  for (Req* r : S->active) finish(S, r, status);
-  S->active.clear();
+  std::vector<Req*> all;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    all.swap(S->active);
+  }
+  for (Req* r : all) finish(S, r, status);
+}
+
+// Admission: first come, first served, while a slot is free and the request
+// at the head of the queue fits the memory budget.  Set-up (operator
+// creation, uploads) runs on the admission stream, overlapping the
+// scheduler's batched work.
+void admitter(s7_server* S) {
+  cudaSetDevice(S->device);
+  for (;;) {
+    Req* r = nullptr;
+    {
+      std::unique_lock<std::mutex> lk(S->mu);
+      S->cv_work.wait(lk, [&] {
+        return S->stop || (!S->queue.empty() && !S->free_slots.empty() &&
+                           S->mem_used + S->queue.front()->bytes <= S->o.hbm_budget_bytes);
+      });
+      if (S->stop) return;
+      r = S->queue.front();
+      S->queue.pop_front();
+      S->mem_used += r->bytes;
+      S->mem_peak = std::max(S->mem_peak, S->mem_used);
+      S->admitting++;
+    }
+    r->t_admit = now_s();
+    const int rc = admit(S, r);
+    if (rc) {
+      finish(S, r, rc);
+      std::lock_guard<std::mutex> lk(S->mu);
+      S->admitting--;
+      continue;
+    }
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->admitting--;
+    S->ready.push_back(r);
+    S->cv_ready.notify_all();
+  }
 }
 
 void scheduler(s7_server* S) {
@@ -249,29 +301,16 @@ void scheduler(s7_server* S) {
   int sweep_blocks = 0, upd_blocks = 0;
   size_t smem_max = 0;
   for (;;) {
-    // ---- admission
-    std::vector<Req*> admit_now;
+    // ---- pick up requests the admission thread has set up
     {
       std::unique_lock<std::mutex> lk(S->mu);
-      if (S->active.empty() && S->queue.empty())
-        S->cv_work.wait(lk, [&] { return S->stop || !S->queue.empty(); });
+      if (S->active.empty() && S->ready.empty())
+        S->cv_ready.wait(lk, [&] { return S->stop || !S->ready.empty(); });
       if (S->stop) break;
-      // first come, first served: admit while a slot is free and the
-      // request at the head of the queue fits the memory budget
-      while (!S->queue.empty() && admit_now.size() < S->free_slots.size() &&
-             S->mem_used + S->queue.front()->bytes <= S->o.hbm_budget_bytes) {
-        Req* r = S->queue.front();
-        S->queue.pop_front();
-        S->mem_used += r->bytes;
-        S->mem_peak = std::max(S->mem_peak, S->mem_used);
-        admit_now.push_back(r);
+      while (!S->ready.empty()) {
+        S->active.push_back(S->ready.front());
+        S->ready.pop_front();
       }
-    }
-    for (Req* r : admit_now) {
-      r->t_admit = now_s();
-      const int rc = admit(S, r);
-      if (rc) finish(S, r, rc);
-      else S->active.push_back(r);
     }
     if (S->active.empty()) continue;
     const double t0 = now_s();
@@ -332,7 +371,10 @@ void scheduler(s7_server* S) {
         r->state = INNER_START;
         keep.push_back(r);
       }
-      S->active.swap(keep);
+      {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->active.swap(keep);
+      }
     }
     if (S->active.empty()) continue;
 
@@ -421,11 +463,21 @@ void scheduler(s7_server* S) {
       }
       keep.push_back(r);
     }
-    S->active.swap(keep);
-    S->busy_s += now_s() - t0;
+    {
+      std::lock_guard<std::mutex> lk(S->mu);
+      S->active.swap(keep);
+      S->busy_s += now_s() - t0;
+    }
   }
-  // shut down: fail what is left
+  // shut down: fail what is left (the admission thread has stopped)
   fail_all(S, S7_ECANCELED);
+  std::vector<Req*> left;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    left.assign(S->ready.begin(), S->ready.end());
+    S->ready.clear();
+  }
+  for (Req* r : left) finish(S, r, S7_ECANCELED);
   std::lock_guard<std::mutex> lk(S->mu);
   for (Req* r : S->queue) {
     r->status = S7_ECANCELED;
@@ -473,6 +525,7 @@ extern "C" int s7_server_create(s7_server_t* out, const s7_server_opts* o) {
   }
   cudaGetDevice(&S->device);
   cudaError_t e = cudaStreamCreateWithFlags(&S->st, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->st_admit, cudaStreamNonBlocking);
   const size_t ns = (size_t)opts.max_active;
   if (e == cudaSuccess) e = cudaMalloc(&S->d_sc, ns * sizeof(Scalars));
   if (e == cudaSuccess) e = cudaMemset(S->d_sc, 0, ns * sizeof(Scalars));
@@ -487,6 +540,7 @@ extern "C" int s7_server_create(s7_server_t* out, const s7_server_opts* o) {
   }
   for (int i = (int)ns - 1; i >= 0; --i) S->free_slots.push_back(i);
   S->th = std::thread(scheduler, S);
+  S->th_admit = std::thread(admitter, S);
   *out = S;
   return S7_OK;
 }
@@ -558,7 +612,7 @@ extern "C" int s7_server_get_stats(s7_server_t S, s7_server_stats* out) {
   std::lock_guard<std::mutex> lk(S->mu);
   out->completed = S->completed;
   out->failed = S->failed;
-  out->queued = (long long)S->queue.size();
+  out->queued = (long long)(S->queue.size() + S->ready.size() + S->admitting);
   out->active = (long long)S->active.size();
   out->mem_used = S->mem_used;
   out->mem_peak = S->mem_peak;
@@ -573,7 +627,9 @@ extern "C" int s7_server_destroy(s7_server_t S) {
     std::lock_guard<std::mutex> lk(S->mu);
     S->stop = true;
     S->cv_work.notify_all();
+    S->cv_ready.notify_all();
   }
+  if (S->th_admit.joinable()) S->th_admit.join();
   if (S->th.joinable()) S->th.join();
   for (auto& kv : S->reqs) delete kv.second;
   S->reqs.clear();
@@ -584,6 +640,7 @@ extern "C" int s7_server_destroy(s7_server_t S) {
   if (S->d_desc) cudaFree(S->d_desc);
   if (S->d_desc_start) cudaFree(S->d_desc_start);
   if (S->st) cudaStreamDestroy(S->st);
+  if (S->st_admit) cudaStreamDestroy(S->st_admit);
   delete S;
   return S7_OK;
 }

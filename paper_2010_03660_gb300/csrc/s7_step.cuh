@@ -29,11 +29,23 @@ __device__ __forceinline__ unsigned smem_u32(const void* p) {
   return (unsigned)__cvta_generic_to_shared(p);
 }
 
-// 16-byte asynchronous global->shared copy; `bytes` = 16 copies, 0 zero-fills.
-__device__ __forceinline__ void cp_async16(void* dst, const void* src, int bytes) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_u32(dst)), "l"(src),
-               "r"(bytes)
-               : "memory");
+// Asynchronous global->shared copy of B bytes (16, 8 or 4); `bytes` = B
+// copies, 0 zero-fills.  16-byte copies bypass L1 (.cg); smaller ones must
+// use .ca.
+template <int B>
+__device__ __forceinline__ void cp_async(void* dst, const void* src, int bytes) {
+  if (B == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_u32(dst)),
+                 "l"(src), "r"(bytes)
+                 : "memory");
+  else if (B == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(smem_u32(dst)),
+                 "l"(src), "r"(bytes)
+                 : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(smem_u32(dst)),
+                 "l"(src), "r"(bytes)
+                 : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() {
   asm volatile("cp.async.commit_group;\n" ::: "memory");
@@ -76,12 +88,18 @@ __host__ __device__ inline StepLayout<T, VEC> step_layout(int bx, int by, int ni
   return L;
 }
 
+// Bytes of one stage, rounded up so every stage and the ring after the
+// stages start on a 16-byte boundary (vector shared-memory accesses).
+template <class T, int VEC>
+__host__ __device__ inline size_t stage_stride_bytes(const StepLayout<T, VEC>& L) {
+  return ((size_t)L.stage_sz * sizeof(T) + 15) / 16 * 16;
+}
+
 template <class T, class A, int VEC>
 __host__ __device__ inline size_t step_smem_bytes(int bx, int by, int stages, int kind) {
   const StepLayout<T, VEC> L = step_layout<T, VEC>(bx, by, kind == 0 ? 3 : 2, kind == 0);
-  const size_t st = (size_t)L.stage_sz * sizeof(T);
   const size_t ring = (size_t)3 * L.rows * L.W * sizeof(A);
-  return (size_t)stages * st + ring;
+  return (size_t)stages * stage_stride_bytes(L) + ring;
 }
 
 template <class T, class A, int VEC, int KIND, int STAGES>
@@ -103,8 +121,9 @@ __global__ void __launch_bounds__(256) k_step(Geom g, StepArgs<T> a, Scalars* sc
   T* out = (KIND == 0) ? (odd ? a.sbuf[1] : a.sbuf[0]) : a.y;
 
   const StepLayout<T, VEC> L = step_layout<T, VEC>(g.bx, g.by, KIND == 0 ? 3 : 2, KIND == 0);
-  T* stage0 = reinterpret_cast<T*>(s7_smem);
-  A* ring = reinterpret_cast<A*>(s7_smem + (size_t)STAGES * L.stage_sz * sizeof(T));
+  const size_t sstride = stage_stride_bytes(L);
+  auto stage_buf = [&](int k) { return reinterpret_cast<T*>(s7_smem + (size_t)k * sstride); };
+  A* ring = reinterpret_cast<A*>(s7_smem + (size_t)STAGES * sstride);
   const int PL = L.rows * L.W;
 
   const int t = threadIdx.x;
@@ -135,13 +154,14 @@ __global__ void __launch_bounds__(256) k_step(Geom g, StepArgs<T> a, Scalars* sc
   const bool v_bot = has_cell && ty == g.by - 1 && y + 1 < g.ny && x < g.nx;
   const bool v_lft = has_cell && tx == 0 && x0 > 0 && y < g.ny;
   const bool v_rgt = has_cell && tx == g.bx - 1 && x + VEC < g.nx && y < g.ny;
+  constexpr int VB = VEC * (int)sizeof(T);   // bytes per vector copy
   auto issue_stage = [&](int k, T* buf) {
     if (!has_cell) return;
     const int z = z0 + k;
     const long long gi = own ? (long long)z * g.plane + row : 0;
 #pragma unroll
-    for (int d = 0; d < 6; ++d) cp_async16(buf + d * g.by * L.TW + sc_own, a.c[d] + gi, own ? 16 : 0);
-    if (KIND == 0) cp_async16(buf + L.coef_sz + sc_own, a.rh + gi, own ? 16 : 0);
+    for (int d = 0; d < 6; ++d) cp_async<VB>(buf + d * g.by * L.TW + sc_own, a.c[d] + gi, own ? VB : 0);
+    if (KIND == 0) cp_async<VB>(buf + L.coef_sz + sc_own, a.rh + gi, own ? VB : 0);
     const int zi = z + 1;
     if (zi >= g.nz) return;
     const long long gb = (long long)zi * g.plane + row;
@@ -149,11 +169,11 @@ __global__ void __launch_bounds__(256) k_step(Geom g, StepArgs<T> a, Scalars* sc
     for (int sidx = 0; sidx < nin; ++sidx) {
       const T* base = sidx == 0 ? in0 : (sidx == 1 ? in1 : in2);
       T* d = ib + sidx * PL;
-      cp_async16(d, base + (own ? gb : 0), own ? 16 : 0);
-      if (ty == 0) cp_async16(d - L.W, base + (v_top ? gb - g.nx : 0), v_top ? 16 : 0);
-      if (ty == g.by - 1) cp_async16(d + L.W, base + (v_bot ? gb + g.nx : 0), v_bot ? 16 : 0);
-      if (tx == 0) cp_async16(d - VEC, base + (v_lft ? gb - VEC : 0), v_lft ? 16 : 0);
-      if (tx == g.bx - 1) cp_async16(d + VEC, base + (v_rgt ? gb + VEC : 0), v_rgt ? 16 : 0);
+      cp_async<VB>(d, base + (own ? gb : 0), own ? VB : 0);
+      if (ty == 0) cp_async<VB>(d - L.W, base + (v_top ? gb - g.nx : 0), v_top ? VB : 0);
+      if (ty == g.by - 1) cp_async<VB>(d + L.W, base + (v_bot ? gb + g.nx : 0), v_bot ? VB : 0);
+      if (tx == 0) cp_async<VB>(d - VEC, base + (v_lft ? gb - VEC : 0), v_lft ? VB : 0);
+      if (tx == g.bx - 1) cp_async<VB>(d + VEC, base + (v_rgt ? gb + VEC : 0), v_rgt ? VB : 0);
     }
   };
 
@@ -163,6 +183,22 @@ __global__ void __launch_bounds__(256) k_step(Geom g, StepArgs<T> a, Scalars* sc
     if (KIND == 1) return q_of(rv, to_acc<A>(inb[PL + e]), alpha);
     if (first) return rv;
     return as_stored<T>(fma(beta, fma(-omega, to_acc<A>(inb[2 * PL + e]), to_acc<A>(inb[PL + e])), rv));
+  };
+  // the same for a run of VEC cells starting at e (one vector load per input)
+  auto form_run = [&](const T* inb, int e, A (&v)[VEC]) {
+    ldv<T, VEC>(inb + e, v);
+    if (KIND == 1) {
+      A sv[VEC];
+      ldv<T, VEC>(inb + PL + e, sv);
+#pragma unroll
+      for (int j = 0; j < VEC; ++j) v[j] = q_of(v[j], sv[j], alpha);
+    } else if (!first) {
+      A pv[VEC], sv[VEC];
+      ldv<T, VEC>(inb + PL + e, pv);
+      ldv<T, VEC>(inb + 2 * PL + e, sv);
+#pragma unroll
+      for (int j = 0; j < VEC; ++j) v[j] = as_stored<T>(fma(beta, fma(-omega, sv[j], pv[j]), v[j]));
+    }
   };
 
   // prologue: the vector at z0-1 (own) and z0 (own + ring) from global memory,
@@ -218,7 +254,7 @@ __global__ void __launch_bounds__(256) k_step(Geom g, StepArgs<T> a, Scalars* sc
   const int nsteps = z1 - z0;
 #pragma unroll
   for (int k = 0; k < STAGES - 1; ++k) {
-    if (k < nsteps) issue_stage(k, stage0 + k * L.stage_sz);
+    if (k < nsteps) issue_stage(k, stage_buf(k));
     cp_async_commit();
   }
 
@@ -231,31 +267,29 @@ __global__ void __launch_bounds__(256) k_step(Geom g, StepArgs<T> a, Scalars* sc
     // refill the buffer of stage k-1 with stage k+STAGES-1
     {
       const int kn = k + STAGES - 1;
-      if (kn < nsteps) issue_stage(kn, stage0 + (kn % STAGES) * L.stage_sz);
+      if (kn < nsteps) issue_stage(kn, stage_buf(kn % STAGES));
       cp_async_commit();
     }
-    const T* st = stage0 + (k % STAGES) * L.stage_sz;
+    const T* st = stage_buf(k % STAGES);
     const T* inb = st + L.coef_sz + L.rh_sz;
     // form plane z+1: own cells (+ ring if the next step needs it)
     A* nb = ring + ((k + 1) % 3) * PL;
     if (z + 1 < g.nz) {
       const bool ring_needed = z + 1 < z1;
       if (has_cell) {
-#pragma unroll
-        for (int j = 0; j < VEC; ++j) vp[j] = own ? form(inb, so + j) : A(0);
+        if (own) form_run(inb, so, vp);
+        else zero(vp);
         if (ring_needed) {
           sm_store<A, VEC>(nb + so, vp);
           if (KIND == 0 && own) store_run<T, VEC, true, true>(p_out + (long long)(z + 1) * g.plane + row, VEC, vp);
           if (ty == 0) {
             A h[VEC];
-#pragma unroll
-            for (int j = 0; j < VEC; ++j) h[j] = form(inb, so - L.W + j);
+            form_run(inb, so - L.W, h);
             sm_store<A, VEC>(nb + so - L.W, h);
           }
           if (ty == g.by - 1) {
             A h[VEC];
-#pragma unroll
-            for (int j = 0; j < VEC; ++j) h[j] = form(inb, so + L.W + j);
+            form_run(inb, so + L.W, h);
             sm_store<A, VEC>(nb + so + L.W, h);
           }
           if (tx == 0) nb[so - 1] = form(inb, so - 1);

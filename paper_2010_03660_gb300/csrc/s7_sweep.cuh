@@ -88,14 +88,13 @@ template <class A, int VEC> __device__ __forceinline__ void zero(A (&v)[VEC]) {
   for (int k = 0; k < VEC; ++k) v[k] = A(0);
 }
 
-// Shared-memory run of VEC values at `p` (aligned to VEC elements).
+// Shared-memory run of VEC values at `p` (aligned to VEC elements): vector
+// accesses of up to 16 bytes.
 template <class A, int VEC> __device__ __forceinline__ void sm_load(const A* p, A (&o)[VEC]) {
-#pragma unroll
-  for (int k = 0; k < VEC; ++k) o[k] = p[k];
+  ldv<A, VEC>(p, o);
 }
 template <class A, int VEC> __device__ __forceinline__ void sm_store(A* p, const A (&v)[VEC]) {
-#pragma unroll
-  for (int k = 0; k < VEC; ++k) p[k] = v[k];
+  stv<A, VEC>(p, v);
 }
 
 // ---------------------------------------------------------------------------
