@@ -64,7 +64,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="solve", choices=["solve", "refined", "batched", "serve"],
+    ap.add_argument("--workload", default="solve",
+                    choices=["solve", "refined", "batched", "serve", "speedup"],
                     help="solve: FP32 600x595x1536 (default); refined: 512^3 BF16/FP16 vs FP32 "
                          "storage with FP64 refinement; batched: 512 systems; serve: request stream")
     ap.add_argument("--edge", type=int, default=512, help="refined: cube edge")
@@ -444,9 +445,9 @@ def run_refined(args):
     runs = {}
     rng = np.random.default_rng(0)
     idx = rng.integers(0, p.n, 2000)
-    for storage in ("bf16", "f16", "f32"):
+    for storage, inner_tol in (("bf16", 1e-2), ("f16", 1e-2), ("f16", 1e-3), ("f32", 1e-5),
+                               ("f32", 1e-2)):
         op = s7.stencil7_create(e, e, e, coef, storage=storage, keep_true=True)
-        inner_tol = 1e-2 if storage != "f32" else 1e-5
         for tol in (1e-8, 1e-10):
             def fn():
                 return s7.bicgstab_solve_refined(op, b, tol=tol, max_outer=80, inner_maxit=200,
@@ -464,18 +465,19 @@ def run_refined(args):
             ref = p.b.astype(np.float64)[idx] - ax
             got = rr[torch.from_numpy(idx).to(dev)].cpu().numpy()
             row_err = float(np.max(np.abs(got - ref) / (mag + np.abs(p.b[idx]))))
-            runs["%s_tol%g" % (storage, tol)] = {
+            runs["%s_in%g_tol%g" % (storage, inner_tol, tol)] = {
                 "ms": ms, "outer": r.outer, "inner_iters": r.inner_total, "status": r.status,
                 "true_resid": rn / bn, "oracle_row_check": row_err, "inner_tol": inner_tol,
                 "inner_cell_iters_per_s": p.n * r.inner_total / (ms / 1e3)}
         op.close()
-    base = runs["f32_tol1e-08"]["ms"]
+    base = min(runs["f32_in1e-05_tol1e-08"]["ms"], runs["f32_in0.01_tol1e-08"]["ms"])
     out = {"metric": "time to relative residual 1e-10, mixed precision (BF16 storage) + FP64 refinement",
-           "value": runs["bf16_tol1e-10"]["ms"] / 1e3, "unit": "s", "higher_is_better": False,
+           "value": runs["bf16_in0.01_tol1e-10"]["ms"] / 1e3, "unit": "s", "higher_is_better": False,
            "workload": "refined_%d^3" % e, "dtype": "bf16/f16/f32 storage, f32 arithmetic, f64 outer",
            "data": "synthetic (seed 2)", "runs": runs,
-           "speedup_vs_fp32_storage_to_1e-8": {k: base / runs["%s_tol1e-08" % k]["ms"]
-                                               for k in ("bf16", "f16")},
+           "speedup_vs_best_fp32_storage_to_1e-8": {
+               k: base / runs["%s_tol1e-08" % k]["ms"] for k in ("bf16_in0.01", "f16_in0.01",
+                                                                 "f16_in0.001")},
            "steps": args.steps}
     print(json.dumps(out))
 
@@ -586,6 +588,65 @@ def run_serve(args):
     print(json.dumps(out))
 
 
+def run_speedup(args):
+    """The same requests to relative residual 1e-8 two ways: one after another
+    with FP32 storage + FP64 refinement (the plain form), and all at once
+    through the server (BF16 storage + FP64 refinement, continuous batching).
+    Both include operator creation from host memory."""
+    import torch
+    import synth
+    import paper_2010_03660_gb300 as s7
+    s7.lib()
+    reqs = synth.request_stream(args.pool, rate=1.0, seed=3)
+    pool = []
+    for q in reqs:
+        p = synth.varcoef(q.nx, q.ny, q.nz, seed=q.seed)
+        pin = {k: torch.from_numpy(v).pin_memory() for k, v in p.coef.items()}
+        pool.append((q.nx, q.ny, q.nz, pin, torch.from_numpy(p.b.astype(np.float64)).pin_memory()))
+    cells = sum(nx * ny * nz for nx, ny, nz, _, _ in pool)
+
+    def plain():
+        its = 0
+        for nx, ny, nz, coef, b in pool:
+            op = s7.stencil7_create(nx, ny, nz, coef, storage="f32", keep_true=True)
+            x = torch.zeros(nx * ny * nz, dtype=torch.float64).pin_memory()
+            r = s7.bicgstab_solve_refined(op, b, x, tol=1e-8, max_outer=60, inner_maxit=400,
+                                          inner_tol=1e-5)
+            its += r.inner_total
+            op.close()
+        return its
+
+    def served():
+        with s7.Server(storage="bf16", hbm_budget_bytes=150 << 30) as srv:
+            xs = [torch.empty(nx * ny * nz, dtype=torch.float64).pin_memory()
+                  for nx, ny, nz, _, _ in pool]
+            ids = [srv.submit(nx, ny, nz, coef, b, x, 1e-8)
+                   for (nx, ny, nz, coef, b), x in zip(pool, xs)]
+            res = [srv.wait(i, timeout=600) for i in ids]
+            return res
+
+    plain()                       # warm-up (module loading, allocator)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    its = plain()
+    torch.cuda.synchronize()
+    t_plain = time.perf_counter() - t0
+    served()
+    t0 = time.perf_counter()
+    res = served()
+    t_served = time.perf_counter() - t0
+    out = {"metric": "speedup to relative residual 1e-8: served BF16 + FP64 refinement vs "
+                     "sequential FP32 + FP64 refinement",
+           "value": t_plain / t_served, "unit": "x", "higher_is_better": True,
+           "requests": len(pool), "total_cells": cells, "plain_fp32_s": t_plain,
+           "served_bf16_s": t_served, "plain_inner_iters": its,
+           "served_inner_iters": int(sum(r["inner_iters"] for r in res)),
+           "served_all_ok": all(r["status"] == 0 for r in res),
+           "served_max_resid": max(r["resid"] for r in res),
+           "workload": "speedup_%d_requests" % len(pool), "data": "synthetic (seed 3)"}
+    print(json.dumps(out))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -596,6 +657,8 @@ def main():
         run_batched(args)
     elif args.workload == "serve":
         run_serve(args)
+    elif args.workload == "speedup":
+        run_speedup(args)
     else:
         run_ours(args)
 

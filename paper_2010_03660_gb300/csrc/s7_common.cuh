@@ -19,9 +19,25 @@ typedef __half f16;
 // ---------------------------------------------------------------------------
 // conversions (all rounding is round-to-nearest-even)
 // ---------------------------------------------------------------------------
+// binary32 -> binary64 is exact: for normal numbers it only re-biases the
+// exponent (127 -> 1023) and widens the significand, which integer
+// instructions do at full rate; zero, subnormals, infinities and NaN take the
+// hardware conversion.  GB300 runs float64 arithmetic (conversions included)
+// at a small fraction of its float32 rate, and the float64 residual sweeps
+// convert seven coefficients per cell.
+__device__ __forceinline__ double f2d_exact(float v) {
+  const unsigned int u = __float_as_uint(v);
+  const unsigned int e = (u >> 23) & 0xffu;
+  if (e == 0u || e == 0xffu) return (double)v;
+  const unsigned long long bits = ((unsigned long long)(u >> 31) << 63) |
+                                  ((unsigned long long)(e + (1023u - 127u)) << 52) |
+                                  ((unsigned long long)(u & 0x7fffffu) << 29);
+  return __longlong_as_double((long long)bits);
+}
+
 template <class A> __device__ __forceinline__ A to_acc(float v);
 template <> __device__ __forceinline__ float to_acc<float>(float v) { return v; }
-template <> __device__ __forceinline__ double to_acc<double>(float v) { return (double)v; }
+template <> __device__ __forceinline__ double to_acc<double>(float v) { return f2d_exact(v); }
 
 template <class A> __device__ __forceinline__ A to_acc(double v);
 template <> __device__ __forceinline__ double to_acc<double>(double v) { return v; }

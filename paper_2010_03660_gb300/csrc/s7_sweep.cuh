@@ -516,9 +516,13 @@ struct EpiResid {
       else rhs = rhs / dc;
       if (dmul) av = av * dv[k];
       else av = av * dmc;
-      rv[k] = as_stored<T>(rhs - av);
+      const A rk = rhs - av;
+      rv[k] = as_stored<T>(rk);
+      // a solve's start residual enters the recurrence as stored; a reported
+      // residual's norm is that of the unrounded value
+      const A rn = mode == 0 ? rv[k] : rk;
       if (k < nv) {
-        acc.part[0] = fma(rv[k], rv[k], acc.part[0]);
+        acc.part[0] = fma(rn, rn, acc.part[0]);
         acc.part[1] = fma(rhs, rhs, acc.part[1]);
       }
     }

@@ -228,3 +228,29 @@ def test_refined_solve_reaches_1e10(s7, storage):
     assert res.status == 0 and res.hist[-1] <= 1e-10
     assert ob.true_residual(nx, ny, nz, p.coef, b64, x) <= 1.5e-10
     assert rel(x, orc.x) < 1e-8
+
+
+def test_float64_residual_of_float32_data_is_exact(s7):
+    """The float64 residual sweeps widen float32 values with integer
+    instructions on normal numbers (hardware path for zero, subnormal, inf);
+    the widening is exact, so the float64 residual norm of float32 data
+    matches the oracle's to float64 rounding, special values included."""
+    nx, ny, nz = 64, 48, 40
+    p = synth.varcoef(nx, ny, nz, seed=9)
+    x = synth.random_vector(p.n, 3, 3, np.float32)
+    x[:100] = 0.0
+    x[100:200] = np.float32(1e-40)          # binary32 subnormal
+    x[200:300] = np.float32(-2.5e30)        # large
+    x[300:400] = np.float32(-0.0)
+    ref = p.b.astype(np.float64) - stencil.apply(nx, ny, nz, p.coef, x.astype(np.float64))
+    for keep in (True, False):
+        with s7.stencil7_create(nx, ny, nz, gu.coef_on_device(p), storage="f32",
+                                keep_true=keep) as op:
+            r = gu.to_dev(np.zeros(p.n, np.float32))
+            rn, bn = s7.stencil7_residual(op, gu.to_dev(p.b), gu.to_dev(x), r)
+        if keep:
+            assert rn == pytest.approx(np.linalg.norm(ref), rel=1e-13)
+            rr = r.cpu().numpy().astype(np.float64)
+            assert np.max(np.abs(rr - ref) / (np.abs(ref) + 1e-300)) <= 6e-8   # one rounding
+        else:
+            assert rn == pytest.approx(np.linalg.norm(ref), rel=1e-6)
