@@ -131,6 +131,20 @@ def ncu_traffic(kernel, n_cells):
     return k["dram_bytes_per_launch"] * n_cells / k["cells"]
 
 
+def combine_ranks(elapsed_ms, iters, pg, device):
+    """Replicas: the job time is the slowest rank's, the work is every rank's
+    (max of the times, sum of the iterations).  pg is torch.distributed or None."""
+    if pg is None:
+        return float(elapsed_ms), float(iters)
+    import torch
+    t = torch.tensor([float(elapsed_ms), float(iters)], dtype=torch.float64, device=device)
+    tmax = t.clone()
+    pg.all_reduce(tmax, op=pg.ReduceOp.MAX)
+    tsum = t.clone()
+    pg.all_reduce(tsum, op=pg.ReduceOp.SUM)
+    return float(tmax[0]), float(tsum[1])
+
+
 class ClockSampler:
     """nvidia-smi sampling of SM clocks and throttle reasons every 200 ms."""
 
@@ -302,17 +316,7 @@ def run_ours(args):
         pg.barrier()
     clocks = sampler.stop()
     prof = s7.stencil7_profile(op, False)
-    elapsed_ms = ev0.elapsed_time(ev1)
-    t = torch.tensor([elapsed_ms, float(done_iters)], dtype=torch.float64, device=dev)
-    if pg:
-        tmax = t.clone()
-        pg.all_reduce(tmax, op=pg.ReduceOp.MAX)
-        tsum = t.clone()
-        pg.all_reduce(tsum, op=pg.ReduceOp.SUM)
-        elapsed_ms = float(tmax[0])
-        total_iters = float(tsum[1])
-    else:
-        total_iters = float(done_iters)
+    elapsed_ms, total_iters = combine_ranks(ev0.elapsed_time(ev1), done_iters, pg, dev)
     value = n * total_iters / (elapsed_ms / 1e3)
 
     peak, peak_kind = measured_peaks()
