@@ -65,7 +65,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="solve",
-                    choices=["solve", "refined", "batched", "serve", "speedup"],
+                    choices=["solve", "refined", "batched", "serve", "speedup", "accuracy"],
                     help="solve: FP32 600x595x1536 (default); refined: 512^3 BF16/FP16 vs FP32 "
                          "storage with FP64 refinement; batched: 512 systems; serve: request stream")
     ap.add_argument("--edge", type=int, default=512, help="refined: cube edge")
@@ -651,6 +651,43 @@ def run_speedup(args):
     print(json.dumps(out))
 
 
+def run_accuracy(args):
+    """Residual histories of plain BiCGStab (no refinement) with FP32, BF16 and
+    FP16 storage on a 100 x 400 x 100 synthetic system (the mesh of the
+    paper's mixed-precision experiment, Sec. VI-B), and of the refined solve."""
+    import torch
+    import synth
+    import paper_2010_03660_gb300 as s7
+    s7.lib()
+    nx, ny, nz = 100, 400, 100
+    p = synth.varcoef(nx, ny, nz, seed=4)
+    dev = torch.device("cuda:0")
+    coef = {k: torch.from_numpy(v).to(dev) for k, v in p.coef.items()}
+    b = torch.from_numpy(p.b).to(dev)
+    curves = {}
+    for storage in ("f32", "bf16", "f16"):
+        with s7.stencil7_create(nx, ny, nz, coef, storage=storage, keep_true=True) as op:
+            r = s7.bicgstab_solve(op, b, tol=1e-12, maxit=60)
+            rn, bn = s7.stencil7_residual(op, b, r.x)
+            curves[storage] = {"hist": [float(v) for v in r.hist], "status": r.status,
+                               "min_recurrence": float(min(r.hist)),
+                               "true_resid_raw": rn / bn}
+            rr = s7.bicgstab_solve_refined(op, b.double(), tol=1e-10, max_outer=40,
+                                           inner_maxit=100, inner_tol=1e-2)
+            curves[storage]["refined_outer_hist"] = [float(v) for v in rr.hist]
+    ref = np.array(curves["f32"]["hist"])
+    for k in ("bf16", "f16"):
+        h = np.array(curves[k]["hist"])
+        m = min(len(h), len(ref))
+        dev_ = np.abs(h[:m] - ref[:m]) / ref[:m]
+        curves[k]["tracks_fp32_until"] = int(np.argmax(dev_ > 0.1)) if np.any(dev_ > 0.1) else m
+    out = {"metric": "mixed-precision accuracy: residual histories, 100x400x100",
+           "value": curves["bf16"]["true_resid_raw"], "unit": "relative residual (bf16, plain)",
+           "higher_is_better": False, "workload": "accuracy_100x400x100",
+           "data": "synthetic (seed 4)", "curves": curves}
+    print(json.dumps(out))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -663,6 +700,8 @@ def main():
         run_serve(args)
     elif args.workload == "speedup":
         run_speedup(args)
+    elif args.workload == "accuracy":
+        run_accuracy(args)
     else:
         run_ours(args)
 

@@ -254,3 +254,31 @@ def test_float64_residual_of_float32_data_is_exact(s7):
             assert np.max(np.abs(rr - ref) / (np.abs(ref) + 1e-300)) <= 6e-8   # one rounding
         else:
             assert rn == pytest.approx(np.linalg.norm(ref), rel=1e-6)
+
+
+def test_mixed_precision_plateau_and_refinement(s7):
+    """Sec. VI-B analogue: plain BiCGStab with 16-bit storage first tracks the
+    float32 history, then stalls at a plateau set by the storage precision;
+    float64 refinement on the true operator still reaches 1e-10."""
+    nx, ny, nz = 50, 100, 25
+    p = synth.varcoef(nx, ny, nz, seed=4)
+    coef = gu.coef_on_device(p)
+    b = gu.to_dev(p.b)
+    h = {}
+    for storage in ("f32", "bf16", "f16"):
+        with s7.stencil7_create(nx, ny, nz, coef, storage=storage, keep_true=True) as op:
+            r = s7.bicgstab_solve(op, b, tol=1e-12, maxit=80)
+            rn, bn = s7.stencil7_residual(op, b, r.x)
+            h[storage] = (np.asarray(r.hist), rn / bn)
+            if storage != "f32":
+                rr = s7.bicgstab_solve_refined(op, b.double(), tol=1e-10, max_outer=40,
+                                               inner_maxit=100, inner_tol=1e-2)
+                assert rr.status == 0 and rr.hist[-1] <= 1e-10
+    f32 = h["f32"][0]
+    for storage, floor in (("bf16", 1e-4), ("f16", 1e-6)):
+        hist, true_raw = h[storage]
+        # the first steps track float32 closely
+        assert np.max(np.abs(hist[:4] - f32[:4]) / f32[:4]) < 0.05
+        # the true residual stalls far above what float32 reaches
+        assert true_raw > floor
+        assert true_raw > 100 * h["f32"][1]
