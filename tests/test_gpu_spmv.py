@@ -123,3 +123,24 @@ def test_zero_diagonal_is_rejected(s7):
     with pytest.raises(s7.S7Error) as e:
         s7.stencil7_create(8, 8, 8, p.coef, storage="f32")
     assert e.value.code == s7.EINVAL
+
+
+@pytest.mark.parametrize("storage", ["bf16", "f16"])
+def test_16bit_output_rounding_is_nearest_even_bitwise(s7, storage):
+    """y = c x with a raw diagonal c and zero off-diagonals: c and x are 16-bit
+    values, so c*x is exact in float32 and the only rounding is the final one
+    to the storage type, which must equal the oracle's round-to-nearest-even
+    bit for bit (ties included)."""
+    import torch
+    nx, ny, nz = 64, 16, 8
+    n = nx * ny * nz
+    c = float(stencil.round_to(np.float64(1.3), storage))
+    coef = {"diag": c, **{d: 0.0 for d in synth.DIRS}}
+    x64 = stencil.round_to(synth.random_vector(n, 21, 3, np.float64), storage)
+    x64[:64] = stencil.round_to(np.linspace(-3, 3, 64), storage)
+    with s7.stencil7_create(nx, ny, nz, coef, storage=storage, jacobi=False) as op:
+        y = s7.stencil7_apply(op, gu.to_dev(x64, gu.torch_dtype(storage)))
+        torch.cuda.synchronize()
+        got = y.double().cpu().numpy()
+    want = stencil.round_to(c * x64, storage)
+    assert np.array_equal(got, want)
