@@ -299,6 +299,40 @@ def test_storage_rounding_changes_system_but_not_much():
     assert 1e-5 < d < 5e-2
 
 
+def test_merged_variant_tracks_algorithm_1():
+    """Two reduction phases per step (rho from its recurrence) give the
+    iterates of Algorithm 1 in exact arithmetic: in float64 the histories
+    agree closely at first and both reach the direct solution."""
+    nx, ny, nz = 8, 7, 6
+    coef, b = rand_coef(nx, ny, nz, seed=51)
+    a = ob.bicgstab(nx, ny, nz, coef, b, tol=1e-12, maxit=500)
+    m = ob.bicgstab_merged(nx, ny, nz, coef, b, tol=1e-12, maxit=500)
+    k = min(len(a.hist), len(m.hist), 12)
+    assert np.max(np.abs(a.hist[:k] - m.hist[:k]) / a.hist[:k]) < 1e-9
+    xd = direct.dense_solve(nx, ny, nz, coef, b)
+    assert m.status == ob.OK
+    assert np.linalg.norm(m.x - xd) / np.linalg.norm(xd) < 1e-10
+    assert abs(m.iters - a.iters) <= 2
+    # and on the 32^3 constant convection-diffusion case
+    p = synth.convdiff_constant(32, 32, 32, seed=0)
+    a = ob.bicgstab(32, 32, 32, p.coef, p.b, tol=1e-8, maxit=500)
+    m = ob.bicgstab_merged(32, 32, 32, p.coef, p.b, tol=1e-8, maxit=500)
+    assert m.status == ob.OK and m.true_resid < 2e-8
+    assert np.linalg.norm(m.x - a.x) / np.linalg.norm(a.x) < 1e-7
+
+
+def test_planted_wrong_rho_recurrence_is_caught(monkeypatch):
+    # dropping the omega term of the rho recurrence breaks the iterates
+    nx, ny, nz = 8, 7, 6
+    coef, b = rand_coef(nx, ny, nz, seed=51)
+    a = ob.bicgstab(nx, ny, nz, coef, b, tol=1e-12, maxit=500)
+    monkeypatch.setattr(ob, "_rho_next", lambda rho, al, sg, om, ry: rho - al * sg)
+    bad = ob.bicgstab_merged(nx, ny, nz, coef, b, tol=1e-12, maxit=200)
+    # (here rho_new = rho - (rho/sigma) sigma = 0: an immediate breakdown)
+    assert not (bad.status == ob.OK and len(bad.hist) == len(a.hist) and
+                np.allclose(bad.hist, a.hist, rtol=1e-6))
+
+
 # --------------------------------------------------------------------------
 # the paper's printed numbers
 # --------------------------------------------------------------------------
