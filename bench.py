@@ -46,13 +46,19 @@ METRIC = "cell-iters/s & HBM GB/s (BiCGStab 7-pt, 600×595×1536); p99 solve lat
 # update : x, p, r, s, y, r0 read + x, r written
 
 
-def bytes_per_cell(storage):
+def bytes_per_cell(storage, variant=0):
     """Algorithmic HBM bytes per cell of each step kernel: w_c = w_v = storage
-    size, w_x = 8 for float64 storage else 4 (12 w_c + 15 w_v + 2 w_x per step)."""
+    size, w_x = 8 for float64 storage else 4 (12 w_c + 15 w_v + 2 w_x per step).
+    Variant 1 (two passes): the q/y pass reads 6 coefficients + r, s, r0 and
+    writes y; the fused pass reads 6 coefficients + r, s, y, p, r0, x and
+    writes x, r, p, s (12 w_c + 12 w_v + 2 w_x per step)."""
     w = {"f64": 8, "f32": 4, "bf16": 2, "f16": 2}[storage]
     wx = 8 if storage == "f64" else 4
-    k = {"spmv_p_dot": 6 * w + 6 * w, "spmv_q_dots": 6 * w + 3 * w,
-         "update_dots": 5 * w + wx + w + wx}
+    if variant == 1:
+        k = {"spmv_p_dot": 6 * w + 8 * w + 2 * wx, "spmv_q_dots": 6 * w + 4 * w}
+    else:
+        k = {"spmv_p_dot": 6 * w + 6 * w, "spmv_q_dots": 6 * w + 3 * w,
+             "update_dots": 5 * w + wx + w + wx}
     return k, sum(k.values())
 FLOPS_PER_CELL = 44          # Table I of the paper
 PAPER_CS1_CELL_ITERS = 548352000 / 28.1e-6   # Sec. V, CS-1, mixed 16/32-bit
@@ -78,6 +84,8 @@ def parse():
     ap.add_argument("--nz", type=int, default=1536)
     ap.add_argument("--iters", type=int, default=100)
     ap.add_argument("--storage", default="f32", choices=["f32", "f64", "bf16", "f16"])
+    ap.add_argument("--variant", type=int, default=0,
+                    help="0: Algorithm 1, three reductions per step; 1: two (merged passes)")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -245,8 +253,10 @@ def run_reference(args):
 
 
 def config_of(args):
-    return {"workload": "bicgstab_%s_%dx%dx%d_%dit" % (args.storage, args.nx, args.ny, args.nz,
-                                                        args.iters),
+    return {"workload": "bicgstab_%s_%dx%dx%d_%dit%s" % (args.storage, args.nx, args.ny, args.nz,
+                                                          args.iters,
+                                                          "_merged" if args.variant else ""),
+            "variant": "two reductions per step" if args.variant else "Algorithm 1",
             "nx": args.nx, "ny": args.ny, "nz": args.nz, "cells": args.nx * args.ny * args.nz,
             "iters_per_step": args.iters, "storage": args.storage,
             "coefficients": "per-cell off-diagonals -U[0.5,1.5], diag = sum|off| + U[0.01,0.1]",
@@ -283,7 +293,7 @@ def run_ours(args):
     gen_s = time.time() - t0
     coef_d = {k: torch.from_numpy(v).to(dev) for k, v in prob.coef.items()}
     op = s7.stencil7_create(nx, ny, nz, coef_d, storage=args.storage, bx=args.bx, by=args.by,
-                            zchunk=args.zchunk)
+                            zchunk=args.zchunk, variant=args.variant)
     del coef_d
     torch.cuda.empty_cache()
     b = torch.from_numpy(prob.b).to(dev)
@@ -320,7 +330,7 @@ def run_ours(args):
     value = n * total_iters / (elapsed_ms / 1e3)
 
     peak, peak_kind = measured_peaks()
-    bpc, iter_bpc = bytes_per_cell(args.storage)
+    bpc, iter_bpc = bytes_per_cell(args.storage, args.variant)
     kern = {}
     for k, (ms, cnt) in prof.items():
         if cnt == 0:
@@ -337,7 +347,7 @@ def run_ours(args):
         v["share"] = v["avg_ms"] * v["launches"] / tot_ms if tot_ms else None
     dom = max((k for k in kern if k in bpc),
               key=lambda k: kern[k]["avg_ms"] * kern[k]["launches"])
-    traffic = ncu_traffic(dom, n) if args.storage == "f32" else None
+    traffic = ncu_traffic(dom, n) if (args.storage == "f32" and args.variant == 0) else None
     roofline = {"bound": "hbm", "kernel": dom, "achieved": kern[dom]["gbs"], "peak": peak,
                 "unit": "GB/s", "frac": kern[dom]["gbs"] / peak, "peak_kind": peak_kind,
                 "traffic": traffic}

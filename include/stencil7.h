@@ -112,6 +112,14 @@ typedef struct {
   int pipe_kinds;    /* which sweeps use that pipeline: bit 0 = the p-update +
                         s = A p sweep, bit 1 = the q + y = A q sweep;
                         0 = default (tuned)                                    */
+  int variant;       /* 0: Algorithm 1 as printed, three reductions and three
+                        passes per step.  1: two reductions per step: (r0,
+                        r_{i+1}) follows from its recurrence (r0, r_i) -
+                        alpha (r0, s_i) - omega (r0, y_i), so the x and r
+                        updates of one step fuse with the p update and SpMV
+                        of the next (two passes, 104 instead of 116 bytes per
+                        cell in float32; same iterates in exact arithmetic).
+                        Single solves only; batched and served solves use 0. */
 } s7_opts;
 
 /* Create an operator handle.  Copies the coefficients to library-owned device

@@ -183,8 +183,12 @@ def bicgstab_merged(nx, ny, nz, coef, b, x0=None, tol=1e-8, maxit=500, jacobi=Tr
     so beta_i is known as soon as omega_i's reduction, which now also sums
     (r0, y_i), is done.  Then the x and r updates of step i and the p update
     and SpMV s_{i+1} = A p_{i+1} of step i+1 form one pass over the mesh,
-    which also reduces (r0, s_{i+1}) and (r_{i+1}, r_{i+1}) (the latter for
-    the same stopping rule as :func:`bicgstab`; breakdown readings as there).
+    which also reduces (r0, s_{i+1}), (r_{i+1}, r_{i+1}) (the stopping rule
+    of :func:`bicgstab`) and (r0, r_{i+1}) directly.  The recurrence value
+    only predicts beta_i; alpha_{i+1} and the next prediction start from the
+    directly reduced (r0, r_{i+1}), so rounding in the recurrence does not
+    accumulate from step to step (carried alone, it stalls float32 solves).
+    Breakdown readings as in :func:`bicgstab`, on the direct value.
     """
     n = nx * ny * nz
     b = np.asarray(b, dtype=np.float64)
@@ -238,20 +242,21 @@ def bicgstab_merged(nx, ny, nz, coef, b, x0=None, tol=1e-8, maxit=500, jacobi=Tr
             break
         rho_new = _rho_next(rho, alpha, sigma, omega, ry)
         # pass 2: x, r updates of step i; p, s = A p of step i+1
+        beta = (alpha / omega) * (rho_new / rho)
         x = x + alpha * p + omega * q
         r = q - omega * y
+        p = r + beta * (p - omega * s)
+        s = A(p)
+        sigma = _dot(rhat, s)
         rr = _dot(r, r)
+        rho_direct = _dot(rhat, r)
         hist.append(np.sqrt(rr) / bnorm)
         it = i + 1
         if hist[-1] <= tol:
             status = OK
             break
-        if rho_new == 0.0 or not np.isfinite(rho_new):
+        if rho_direct == 0.0 or not np.isfinite(rho_direct):
             status = BREAKDOWN
             break
-        beta = (alpha / omega) * (rho_new / rho)
-        p = r + beta * (p - omega * s)
-        s = A(p)
-        sigma = _dot(rhat, s)
-        rho = rho_new
+        rho = rho_direct
     return _finish(nx, ny, nz, coef, op, b, bt, x, it, hist, status)

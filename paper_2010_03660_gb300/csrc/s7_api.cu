@@ -220,6 +220,7 @@ static void release(Handle* h) {
   dfree(h, (void**)&w.parts, w.parts_n * 8);
   dfree(h, (void**)&w.hist, (size_t)w.hist_cap * 8);
   dfree(h, (void**)&w.sc, sizeof(Scalars));
+  dfree(h, &w.r2, n * ts);
   dfree(h, &w.ref_x, n * 8);
   dfree(h, &w.ref_b, n * 8);
   dfree(h, &w.ref_r, n * 8);
@@ -301,6 +302,11 @@ extern "C" int stencil7_create(stencil7_t* out, int nx, int ny, int nz, const s7
   const bool half = opts.storage == S7_BF16 || opts.storage == S7_F16;
   h->stages = opts.stages > 0 ? std::min(opts.stages, 4) : (half ? 3 : 2);
   h->pipe_kinds = opts.pipe_kinds > 0 ? (opts.pipe_kinds & 3) : (half ? 3 : 1);
+  if (opts.variant < 0 || opts.variant > 1) {
+    delete h;
+    return fail(S7_EINVAL, "stencil7_create: variant must be 0 or 1");
+  }
+  h->variant = opts.variant;
   if (!eng->smem_ok(h)) {
     delete h;
     return fail(S7_EINVAL, "stencil7_create: tile too large for shared memory");
@@ -454,6 +460,7 @@ int s7::ensure_ws(Handle* h, int maxit) {
       if ((rc = dmalloc(h, vs[k], n * ts))) return rc;
     if ((rc = dmalloc(h, &w.x, n * xs))) return rc;
     if ((rc = dmalloc(h, &w.b, n * xs))) return rc;
+    if (h->variant == 1 && (rc = dmalloc(h, &w.r2, n * ts))) return rc;
     w.parts_n = eng->parts_needed(h);
     if ((rc = dmalloc(h, (void**)&w.parts, w.parts_n * 8))) return rc;
     if ((rc = dmalloc(h, (void**)&w.sc, sizeof(Scalars)))) return rc;
@@ -684,6 +691,17 @@ extern "C" int stencil7_profile(stencil7_t h, int enable, double* ms, long long*
 // One BiCGStab step: its three kernels, each timed when profiling.
 static int run_step(Handle* h, cudaStream_t st) {
   const Engine* eng = engine_for(h->storage);
+  if (h->variant == 1) {
+    // the q/y pass, then the fused x, r update + p/s pass of the next step
+    const int kinds[2] = {PK_B, PK_A};
+    for (int k = 0; k < 2; ++k) {
+      const int pi = prof_begin(h, kinds[k], st);
+      int rc = eng->merged_kernel(h, k + 1, st);
+      prof_end(h, pi, st);
+      if (rc) return rc;
+    }
+    return S7_OK;
+  }
   for (int k = 0; k < 3; ++k) {
     const int pi = prof_begin(h, k, st);
     int rc = eng->step_kernel(h, k, st);
@@ -704,8 +722,12 @@ static int capture_graph(Handle* h) {
   cudaGraph_t g = nullptr;
   CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
   int rc = S7_OK;
-  for (int k = 0; k < h->check_every && rc == S7_OK; ++k)
-    for (int j = 0; j < 3 && rc == S7_OK; ++j) rc = eng->step_kernel(h, j, h->stream);
+  for (int k = 0; k < h->check_every && rc == S7_OK; ++k) {
+    if (h->variant == 1)
+      for (int j = 1; j <= 2 && rc == S7_OK; ++j) rc = eng->merged_kernel(h, j, h->stream);
+    else
+      for (int j = 0; j < 3 && rc == S7_OK; ++j) rc = eng->step_kernel(h, j, h->stream);
+  }
   cudaError_t e = cudaStreamEndCapture(h->stream, &g);
   if (rc || e != cudaSuccess) {
     if (g) cudaGraphDestroy(g);
@@ -746,6 +768,13 @@ static int solve_core(Handle* h, const void* bdev, double tol, int maxit, SolveO
   if (rc) return fail(rc, "init launch failed: %s", cudaGetErrorString(cudaGetLastError()));
   // hist[0] = ||r_0|| / ||b~|| is left in res[2] by the start kernel
   CK(cudaMemcpyAsync(w.hist, &w.sc->res[2], sizeof(double), cudaMemcpyDeviceToDevice, st));
+  if (h->variant == 1) {
+    // the two-reduction variant starts with s_0 = A p_0 and (r0, s_0)
+    const int pf = prof_begin(h, PK_OTHER, st);
+    rc = eng->merged_kernel(h, 0, st);
+    prof_end(h, pf, st);
+    if (rc) return fail(rc, "first pass launch failed");
+  }
   if (!h->prof && (rc = capture_graph(h))) return rc;
   const int per = std::max(1, h->check_every);
   const int max_launch = maxit / per + 3;

@@ -222,6 +222,18 @@ int launch_sweep(const Geom& g, const CoefView<CT, A>& cf, const Src& src, const
   return cudaGetLastError() == cudaSuccess ? S7_OK : S7_ECUDA;
 }
 
+template <class CT, class A, int VEC, class P>
+int launch_sweep1(const Geom& g, const CoefView<CT, A>& cf, const P& pol, Scalars* sc, bool vl,
+                  cudaStream_t st) {
+  const int threads = ((g.bx * g.by + 31) / 32) * 32;
+  const size_t smem = (size_t)3 * (g.by + 2) * (g.bx * VEC + 2 * VEC) * sizeof(A);
+  void (*kern)(Geom, CoefView<CT, A>, P, Scalars*) =
+      vl ? k_sweep1<CT, A, VEC, true, P> : k_sweep1<CT, A, VEC, false, P>;
+  if (allow_smem((const void*)kern, smem, st)) return S7_ECUDA;
+  kern<<<s7_nblocks(g), threads, smem, st>>>(g, cf, pol, sc);
+  return cudaGetLastError() == cudaSuccess ? S7_OK : S7_ECUDA;
+}
+
 template <class T_, class X_, class DT_, class A_>
 struct EngineImpl {
   typedef T_ T;
@@ -352,6 +364,10 @@ struct EngineImpl {
     set((const void*)k_sweep<T, A, VEC, false, SrcPUpdate<T, A>, EpiS<T, A>>, gb);
     set((const void*)k_sweep<T, A, VEC, true, SrcQ<T, A>, EpiY<T, A>>, gb);
     set((const void*)k_sweep<T, A, VEC, false, SrcQ<T, A>, EpiY<T, A>>, gb);
+    set((const void*)k_sweep<T, A, VEC, true, SrcQ2<T, A>, EpiYMerged<T, A>>, gb);
+    set((const void*)k_sweep<T, A, VEC, false, SrcQ2<T, A>, EpiYMerged<T, A>>, gb);
+    set((const void*)k_sweep1<T, A, VEC, true, MergedPass<T, X, A>>, gb);
+    set((const void*)k_sweep1<T, A, VEC, false, MergedPass<T, X, A>>, gb);
     return rc;
   }
 
@@ -395,6 +411,39 @@ struct EngineImpl {
         h->n, (const T*)w.p[0], (const T*)w.p[1], (const T*)w.s[0], (const T*)w.s[1],
         (const T*)w.y, (const T*)w.rh, (T*)w.r, (X*)w.x, w.sc, w.parts, w.hist);
     return cudaGetLastError() == cudaSuccess ? S7_OK : S7_ECUDA;
+  }
+
+  static int merged_kernel(Handle* h, int which, cudaStream_t st) {
+    if (which == 0) return step_kernel(h, 0, st);   // s_0 = A p_0 at step 0
+    const Geom g = make_geom(h, VEC);
+    Workspace& w = h->ws;
+    const CoefView<T, A> cf = stored<A>(h);
+    const bool vl = (h->nx % VEC == 0);
+    if (which == 1) {
+      SrcQ2<T, A> sb;
+      sb.rbuf[0] = (T*)w.r;
+      sb.rbuf[1] = (T*)w.r2;
+      sb.sbuf[0] = (T*)w.s[0];
+      sb.sbuf[1] = (T*)w.s[1];
+      EpiYMerged<T, A> eb;
+      eb.y_out = (T*)w.y;
+      eb.rh = (const T*)w.rh;
+      eb.parts = w.parts;
+      return launch_sweep<T, A, VEC>(g, cf, sb, eb, w.sc, vl, st);
+    }
+    MergedPass<T, X, A> m;
+    m.rbuf[0] = (T*)w.r;
+    m.rbuf[1] = (T*)w.r2;
+    m.pbuf[0] = (T*)w.p[0];
+    m.pbuf[1] = (T*)w.p[1];
+    m.sbuf[0] = (T*)w.s[0];
+    m.sbuf[1] = (T*)w.s[1];
+    m.y = (const T*)w.y;
+    m.rh = (const T*)w.rh;
+    m.x = (X*)w.x;
+    m.parts = w.parts;
+    m.hist = w.hist;
+    return launch_sweep1<T, A, VEC>(g, cf, m, w.sc, vl, st);
   }
 
   // ||b~ - A~ x|| and ||b~|| with float64 accumulation -> sc->res[0], res[1].
@@ -647,6 +696,7 @@ struct EngineImpl {
     static const Engine e = {sizeof(T), sizeof(X), sizeof(DT), VEC, &scale, &apply, &init, &step_kernel,
                              &true_resid, &raw_resid, &cast, &parts_needed, &smem_ok,
                              &raw_resid_into, &raw_resid_blocks, &prepare_capture,
+                             &merged_kernel,
                              sizeof(Desc), &fill_desc, &batched_smem, &launch_batched,
                              &batched_prepare};
     return &e;

@@ -28,6 +28,7 @@ struct Workspace {
   int hist_cap = 0;
   Scalars* sc = nullptr;   // device scalars
   Scalars* h_sc = nullptr; // pinned host mirror
+  void* r2 = nullptr;      // second r buffer (two-reduction variant)
   void* ref_x = nullptr;   // float64 iterate of the refined solver
   void* ref_b = nullptr;   // float64 right-hand side of the refined solver
   void* ref_r = nullptr;   // float64 true residual of the refined solver
@@ -59,6 +60,7 @@ struct Handle {
   int check_every;
   int stages;                 // step-sweep pipeline depth (1 = direct loads)
   int pipe_kinds;             // bit k: sweep k of a step uses the pipeline
+  int variant;                // 0: three reductions per step; 1: two (merged passes)
   size_t bytes = 0;           // device bytes held
   void* small = nullptr;      // 256 bytes of device scratch (flags)
   cudaStream_t stream = nullptr;   // private stream (captures, solves)
@@ -98,6 +100,9 @@ struct Engine {
   long long (*raw_resid_blocks)(const Handle* h, s7_dtype dt);
   // set kernel attributes the step kernels need, before graph capture
   int (*prepare_capture)(Handle* h);
+  // the two-reduction variant: 0 = first p/s pass, 1 = q/y pass, 2 = fused
+  // x, r update + p/s pass of the next step
+  int (*merged_kernel)(Handle* h, int which, cudaStream_t st);
   // ---- batched solves (s7_batch.cuh) ----
   size_t desc_size;
   // Fill the batch descriptor of system h (host memory) for tile t with

@@ -357,6 +357,7 @@ __global__ void __launch_bounds__(256) k_step(Geom g, StepArgs<T> a, Scalars* sc
         sc->done = 1;
       } else {
         sc->alpha = sc->rho / sigma;
+        sc->res[3] = sigma;
       }
     }
   } else {

@@ -42,6 +42,7 @@ struct Scalars {
   int status;     // S7_* code once done
   int special;    // 1: (y,y) = 0 in this step (q = 0): take the half step
   int pad_;
+  double rho_next;  // merged variant: (r0, r_{i+1}) from its recurrence
   unsigned int counter[8];  // grid-combine arrival counters, one per kernel kind
 };
 
@@ -242,6 +243,17 @@ __device__ __forceinline__ void sweep_body(const Geom& g, const CoefView<CT, A>&
   epi.finish(sc, nblocks, bid, red);
 }
 
+// One policy object in both roles (its producer and epilogue share state).
+template <class CT, class A, int VEC, bool VL, class P>
+__global__ void __launch_bounds__(512) k_sweep1(Geom g, CoefView<CT, A> cf, P p_in, Scalars* sc) {
+  extern __shared__ __align__(16) unsigned char s7_smem[];
+  __shared__ double red[32 * 4];
+  if (sc != nullptr && P::kSkipWhenDone && *((volatile int*)&sc->done)) return;
+  P pol = p_in;
+  sweep_body<CT, A, VEC, VL>(g, cf, pol, pol, sc, blockIdx.x, s7_nblocks(g),
+                             reinterpret_cast<A*>(s7_smem), red);
+}
+
 template <class CT, class A, int VEC, bool VL, class Src, class Epi>
 __global__ void __launch_bounds__(512) k_sweep(Geom g, CoefView<CT, A> cf, Src src_in, Epi epi_in,
                                                Scalars* sc) {
@@ -424,6 +436,7 @@ struct EpiS {
         sc->done = 1;
       } else {
         sc->alpha = sc->rho / sigma;
+        sc->res[3] = sigma;
       }
     }
   }
@@ -556,6 +569,242 @@ struct EpiResid {
           else if (sc->maxit <= 0) { sc->status = 4; sc->done = 1; }
           else if (!isfinite(h0)) { sc->status = 3; sc->done = 1; }
           else { sc->done = 0; sc->status = 4; }
+        }
+      }
+    }
+  }
+};
+
+}  // namespace s7
+
+namespace s7 {
+
+// ---------------------------------------------------------------------------
+// Two reductions per step (the merged variant).  (r0, r_{i+1}) follows from
+// (r0, r_i) - alpha (r0, s_i) - omega (r0, y_i), so beta_i is known after the
+// y pass, and the x, r updates of step i fuse with the p update and SpMV of
+// step i+1.  r, p and s are double-buffered by step parity.
+// ---------------------------------------------------------------------------
+
+// q_i = r_i - alpha s_i formed on the fly, with r double-buffered.
+template <class T, class A>
+struct SrcQ2 {
+  T* rbuf[2];
+  T* sbuf[2];
+  const T* r;
+  const T* s;
+  A alpha;
+  __device__ void setup(const Scalars* sc) {
+    alpha = (A)sc->alpha;
+    const bool odd = (sc->iter & 1) != 0;
+    r = odd ? rbuf[1] : rbuf[0];
+    s = odd ? sbuf[1] : sbuf[0];
+  }
+  template <int VEC, bool VL>
+  __device__ __forceinline__ void produce(long long i, int nv, A (&v)[VEC], bool) {
+    A sv[VEC];
+    load_run<T, VEC, VL>(r + i, nv, v);
+    load_run<T, VEC, VL>(s + i, nv, sv);
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) v[k] = q_of(v[k], sv[k], alpha);
+  }
+  __device__ __forceinline__ A produce1(long long i) {
+    return q_of(to_acc<A>(r[i]), to_acc<A>(s[i]), alpha);
+  }
+};
+
+// y_i = A q_i stored; (q,y), (y,y), (r0,y) reduced; omega_i, rho_{i+1}, beta_i.
+template <class T, class A>
+struct EpiYMerged {
+  static constexpr bool kSkipWhenDone = true;
+  T* y_out;
+  const T* rh;
+  double* parts;
+  DotAcc<A, 3> acc;
+  A rh_v[8];
+  __device__ void setup(const Scalars*) { acc.init(); }
+  template <int VEC, bool VL> __device__ __forceinline__ void load(long long i, int nv) {
+    if (nv > 0) {
+      A t[VEC];
+      load_run<T, VEC, VL>(rh + i, nv, t);
+#pragma unroll
+      for (int k = 0; k < VEC; ++k) rh_v[k] = t[k];
+    }
+  }
+  template <int VEC, bool VL>
+  __device__ __forceinline__ void consume(long long i, int nv, const A (&out)[VEC], const A (&q)[VEC]) {
+    A yv[VEC];
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) yv[k] = as_stored<T>(out[k]);
+    store_run<T, VEC, VL, true>(y_out + i, nv, yv);
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) {
+      acc.part[0] = fma(q[k], yv[k], acc.part[0]);
+      acc.part[1] = fma(yv[k], yv[k], acc.part[1]);
+      acc.part[2] = fma(rh_v[k], yv[k], acc.part[2]);
+    }
+  }
+  __device__ __forceinline__ void step_end(int k) { if ((k & 7) == 7) acc.fold(); }
+  __device__ void finish(Scalars* sc, int nblocks, int bid, double* red) {
+    acc.fold();
+    double v[3] = {acc.tot[0], acc.tot[1], acc.tot[2]}, tot[3];
+    block_sum<3>(v, red);
+    if (grid_combine<3>(parts, &sc->counter[CNT_B], nblocks, bid, v, tot, red) && threadIdx.x == 0) {
+      const double qy = tot[0], yy = tot[1], ry = tot[2];
+      if (yy == 0.0) {
+        sc->special = 1;
+        sc->omega = 0.0;
+        sc->beta = 0.0;
+        sc->rho_next = 0.0;
+      } else {
+        const double om = qy / yy;
+        if (om == 0.0 || !isfinite(om)) {
+          sc->status = 3;
+          sc->done = 1;
+        } else {
+          sc->omega = om;
+          // (r0, r_{i+1}) = (r0, r_i) - alpha (r0, s_i) - omega (r0, y_i)
+          const double rn = sc->rho - sc->alpha * sc->res[3] - om * ry;
+          sc->rho_next = rn;
+          sc->beta = (sc->alpha / om) * (rn / sc->rho);
+        }
+      }
+    }
+  }
+};
+
+// The fused pass: on every cell of the march (own and halo) it forms
+// r_{i+1} = (r_i - alpha s_i) - omega y_i and p_{i+1} = r_{i+1} + beta (p_i -
+// omega s_i); on the block's own cells it also updates x (x += alpha p_i +
+// omega q_i) and stores r_{i+1}, p_{i+1}.  As the epilogue it stores
+// s_{i+1} = A p_{i+1} and reduces (r0, s_{i+1}), (r_{i+1}, r_{i+1}) and
+// (r0, r_{i+1}): the recurrence value of the latter only predicted beta_i;
+// alpha_{i+1} and the next prediction use the reduced one.  One object serves
+// as both producer and epilogue (k_sweep1): r_{i+1} of the block's own cells
+// waits in a two-plane register ring between the two.
+template <class T, class X, class A>
+struct MergedPass {
+  static constexpr bool kSkipWhenDone = true;
+  T* rbuf[2];
+  T* pbuf[2];
+  T* sbuf[2];
+  const T* y;
+  const T* rh;
+  X* x;
+  double* parts;
+  double* hist;
+  // set up per launch
+  const T *r_in, *p_in, *s_in;
+  T *r_out, *p_out, *s_out;
+  A alpha, omega, beta;
+  DotAcc<A, 3> acc;  // (r0, s_{i+1}), (r_{i+1}, r_{i+1}), (r0, r_{i+1})
+  A rh_v[8];
+  A ring0[8], ring1[8];  // r_{i+1} of own cells, by plane parity
+  int pw, pc;
+  __device__ void setup(const Scalars* sc) {
+    const bool odd = (sc->iter & 1) != 0;
+    r_in = odd ? rbuf[1] : rbuf[0];
+    r_out = odd ? rbuf[0] : rbuf[1];
+    p_in = odd ? pbuf[1] : pbuf[0];
+    p_out = odd ? pbuf[0] : pbuf[1];
+    s_in = odd ? sbuf[1] : sbuf[0];
+    s_out = odd ? sbuf[0] : sbuf[1];
+    alpha = (A)sc->alpha;
+    omega = (A)sc->omega;
+    beta = (A)sc->beta;
+    acc.init();
+    pw = pc = 0;
+  }
+  __device__ __forceinline__ void form(A rv, A sv, A yv, A pv, A& q, A& rn, A& pn) const {
+    q = q_of(rv, sv, alpha);
+    rn = as_stored<T>(fma(-omega, yv, q));
+    pn = as_stored<T>(fma(beta, fma(-omega, sv, pv), rn));
+  }
+  template <int VEC, bool VL>
+  __device__ __forceinline__ void produce(long long i, int nv, A (&v)[VEC], bool write) {
+    static_assert(VEC <= 8, "run too long");
+    A rv[VEC], sv[VEC], yv[VEC], pv[VEC];
+    load_run<T, VEC, VL>(r_in + i, nv, rv);
+    load_run<T, VEC, VL>(s_in + i, nv, sv);
+    load_run<T, VEC, VL>(y + i, nv, yv);
+    load_run<T, VEC, VL>(p_in + i, nv, pv);
+    A rn[VEC], q[VEC];
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) form(rv[k], sv[k], yv[k], pv[k], q[k], rn[k], v[k]);
+    if (write) {
+      A xv[VEC];
+      load_run<X, VEC, VL>(x + i, nv, xv);
+#pragma unroll
+      for (int k = 0; k < VEC; ++k) xv[k] = fma(omega, q[k], fma(alpha, pv[k], xv[k]));
+      store_run<X, VEC, VL, true>(x + i, nv, xv);
+      store_run<T, VEC, VL, true>(r_out + i, nv, rn);
+      store_run<T, VEC, VL, true>(p_out + i, nv, v);
+      if (pw) {
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) ring1[k] = (k < nv) ? rn[k] : A(0);
+      } else {
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) ring0[k] = (k < nv) ? rn[k] : A(0);
+      }
+      pw ^= 1;
+    }
+  }
+  __device__ __forceinline__ A produce1(long long i) {
+    A q, rn, pn;
+    form(to_acc<A>(r_in[i]), to_acc<A>(s_in[i]), to_acc<A>(y[i]), to_acc<A>(p_in[i]), q, rn, pn);
+    return pn;
+  }
+  template <int VEC, bool VL> __device__ __forceinline__ void load(long long i, int nv) {
+    if (nv > 0) {
+      A t[VEC];
+      load_run<T, VEC, VL>(rh + i, nv, t);
+#pragma unroll
+      for (int k = 0; k < VEC; ++k) rh_v[k] = t[k];
+    }
+  }
+  template <int VEC, bool VL>
+  __device__ __forceinline__ void consume(long long i, int nv, const A (&out)[VEC], const A (&)[VEC]) {
+    A sv[VEC];
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) sv[k] = as_stored<T>(out[k]);
+    store_run<T, VEC, VL, true>(s_out + i, nv, sv);
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) {
+      const A rn = pc ? ring1[k] : ring0[k];
+      acc.part[0] = fma(rh_v[k], sv[k], acc.part[0]);
+      acc.part[1] = fma(rn, rn, acc.part[1]);
+      acc.part[2] = fma(rh_v[k], rn, acc.part[2]);
+    }
+    pc ^= 1;
+  }
+  __device__ __forceinline__ void step_end(int k) { if ((k & 7) == 7) acc.fold(); }
+  __device__ void finish(Scalars* sc, int nblocks, int bid, double* red) {
+    acc.fold();
+    double v[3] = {acc.tot[0], acc.tot[1], acc.tot[2]}, tot[3];
+    block_sum<3>(v, red);
+    if (grid_combine<3>(parts, &sc->counter[CNT_C], nblocks, bid, v, tot, red) && threadIdx.x == 0) {
+      const double sigma = tot[0], rr = tot[1], rho_direct = tot[2];
+      const int it = sc->iter + 1;
+      const double h = sqrt(rr) / sc->bnorm;
+      if (hist) hist[it] = h;
+      sc->iter = it;
+      sc->res[2] = h;
+      if (sc->special) {
+        sc->status = (h <= sc->tol) ? 0 : 3;
+        sc->done = 1;
+      } else if (h <= sc->tol) {
+        sc->status = 0;
+        sc->done = 1;
+      } else if (rho_direct == 0.0 || !isfinite(rho_direct) || sigma == 0.0 || !isfinite(sigma)) {
+        sc->status = 3;
+        sc->done = 1;
+      } else {
+        sc->rho = rho_direct;
+        sc->alpha = rho_direct / sigma;
+        sc->res[3] = sigma;
+        if (it >= sc->maxit) {
+          sc->status = 4;
+          sc->done = 1;
         }
       }
     }

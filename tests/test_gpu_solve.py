@@ -282,3 +282,66 @@ def test_mixed_precision_plateau_and_refinement(s7):
         # the true residual stalls far above what float32 reaches
         assert true_raw > floor
         assert true_raw > 100 * h["f32"][1]
+
+
+def test_two_reduction_variant_fp64_matches_its_oracle(s7):
+    """variant 1 (beta from the rho recurrence, fused passes) against the oracle's
+    bicgstab_merged, and both against Algorithm 1's solution."""
+    p = synth.convdiff_constant(32, 32, 32, seed=0)
+    orc = ob.bicgstab_merged(32, 32, 32, p.coef, p.b, tol=1e-8, maxit=500)
+    std = ob.bicgstab(32, 32, 32, p.coef, p.b, tol=1e-8, maxit=500)
+    with s7.stencil7_create(32, 32, 32, p.coef, storage="f64", variant=1) as op:
+        res = s7.bicgstab_solve(op, gu.to_dev(p.b), tol=1e-8, maxit=500)
+    x = res.x.cpu().numpy()
+    assert res.status == 0 and abs(res.iters - orc.iters) <= 3
+    assert np.max(np.abs(res.hist[:15] - orc.hist[:15]) / orc.hist[:15]) < 1e-9
+    assert rel(x, orc.x) < 1e-7 and rel(x, std.x) < 1e-7
+    assert res.true_resid <= 1.01e-8
+    nx, ny, nz = 45, 30, 26
+    q = synth.varcoef(nx, ny, nz, seed=5, dtype=np.float64)
+    orc = ob.bicgstab_merged(nx, ny, nz, q.coef, q.b, tol=1e-10, maxit=400)
+    with s7.stencil7_create(nx, ny, nz, gu.coef_on_device(q), storage="f64", variant=1) as op:
+        res = s7.bicgstab_solve(op, gu.to_dev(q.b), tol=1e-10, maxit=400)
+    # beta comes from a recurrence, not a reduction: near 1e-10 the step count
+    # moves more than for Algorithm 1 (solution and true residual still hold)
+    assert res.status == 0 and abs(res.iters - orc.iters) <= max(6, orc.iters // 6)
+    assert np.max(np.abs(res.hist[:15] - orc.hist[:15]) / orc.hist[:15]) < 1e-9
+    assert rel(res.x.cpu().numpy(), orc.x) < 1e-8
+    assert res.true_resid <= 1.01e-10
+
+
+@pytest.mark.parametrize("shape", [(64, 48, 40), (61, 37, 29), (17, 9, 33)])
+def test_two_reduction_variant_fp32(s7, shape):
+    nx, ny, nz = shape
+    p = synth.varcoef(nx, ny, nz, seed=21)
+    orc = ob.bicgstab(nx, ny, nz, p.coef, p.b, tol=1e-6, maxit=1000, storage="f32")
+    with s7.stencil7_create(nx, ny, nz, gu.coef_on_device(p), storage="f32", variant=1) as op:
+        res = s7.bicgstab_solve(op, gu.to_dev(p.b), tol=1e-6, maxit=1000)
+        again = s7.bicgstab_solve(op, gu.to_dev(p.b), tol=1e-6, maxit=1000)
+    assert res.status == 0 and res.hist[-1] <= 1e-6
+    assert abs(res.iters - orc.iters) <= max(6, orc.iters // 4)
+    assert rel(res.x.cpu().numpy(), orc.x) <= 1e-4
+    assert res.true_resid <= 2e-6
+    assert again.iters == res.iters
+    assert np.array_equal(again.x.cpu().numpy(), res.x.cpu().numpy())
+
+
+def test_two_reduction_variant_degenerate_cases(s7):
+    import torch
+    nx, ny, nz = 20, 10, 12
+    p = synth.varcoef(nx, ny, nz, seed=31, dtype=np.float64)
+    with s7.stencil7_create(nx, ny, nz, gu.coef_on_device(p), storage="f64", variant=1) as op:
+        z = torch.zeros(p.n, dtype=torch.float64, device="cuda:0")
+        r0 = s7.bicgstab_solve(op, z, tol=1e-8, maxit=10)
+        assert r0.iters == 0 and r0.status == 0 and float(r0.x.abs().max()) == 0.0
+        r2 = s7.bicgstab_solve(op, gu.to_dev(p.b), tol=1e-30, maxit=7)
+        o2 = ob.bicgstab_merged(nx, ny, nz, p.coef, p.b, tol=1e-30, maxit=7)
+        assert r2.status == s7.ENOTCONV and r2.iters == 7 and len(r2.hist) == 8
+        assert np.max(np.abs(r2.hist - o2.hist) / o2.hist) < 1e-10
+        r3 = s7.bicgstab_solve(op, gu.to_dev(p.b), tol=1e-8, maxit=0)
+        assert r3.iters == 0 and r3.status == s7.ENOTCONV
+    for ce in (1, 5):
+        with s7.stencil7_create(nx, ny, nz, gu.coef_on_device(p), storage="f64", variant=1,
+                                check_every=ce) as op:
+            r = s7.bicgstab_solve(op, gu.to_dev(p.b), tol=1e-9, maxit=300)
+            assert r.status == 0
