@@ -34,6 +34,10 @@ project's design notes):
   system ``D^-1 A x = D^-1 b`` (Sec. IV: the main diagonal is all ones and
   only six diagonals are stored); ``tol`` and ``hist`` refer to that system.
 
+The same iteration serves the 3D 7-point operator (:func:`bicgstab`) and the
+2D 9-point operator of Sec. IV-A (:func:`bicgstab9`); only the operator
+differs.
+
 Status codes follow the library's: 0 converged, 3 breakdown, 4 not
 converged within ``maxit``.
 """
@@ -44,9 +48,41 @@ from dataclasses import dataclass
 
 import numpy as np
 
-from . import stencil
+from . import stencil, stencil9
 
 OK, BREAKDOWN, NOTCONV = 0, 3, 4
+
+
+class _Mesh3:
+    """The 3D 7-point operator of :mod:`oracle.stencil` on an nx x ny x nz mesh."""
+
+    def __init__(self, nx, ny, nz):
+        self.dims = (nx, ny, nz)
+
+    def system(self, coef, b, jacobi, storage):
+        if jacobi:
+            return (stencil.jacobi_scale(*self.dims, coef, storage),
+                    stencil.scale_rhs(*self.dims, coef, b))
+        return stencil.rounded(*self.dims, coef, storage), b.copy()
+
+    def apply(self, op, v):
+        return stencil.apply(*self.dims, op, v)
+
+
+class _Mesh9:
+    """The 2D 9-point operator of :mod:`oracle.stencil9` on an nx x ny mesh."""
+
+    def __init__(self, nx, ny):
+        self.dims = (nx, ny)
+
+    def system(self, coef, b, jacobi, storage):
+        if jacobi:
+            return (stencil9.jacobi_scale(*self.dims, coef, storage),
+                    stencil9.scale_rhs(*self.dims, coef, b))
+        return stencil9.rounded(*self.dims, coef, storage), b.copy()
+
+    def apply(self, op, v):
+        return stencil9.apply(*self.dims, op, v)
 
 
 @dataclass
@@ -71,23 +107,29 @@ def bicgstab(nx, ny, nz, coef, b, x0=None, tol=1e-8, maxit=500,
     ``storage`` is the type the scaled operator is rounded to (the system the
     GPU path actually holds).  Returns a :class:`Result`.
     """
-    n = nx * ny * nz
+    return _bicgstab(_Mesh3(nx, ny, nz), coef, b, x0, tol, maxit, jacobi, storage, half_step)
+
+
+def bicgstab9(nx, ny, coef, b, x0=None, tol=1e-8, maxit=500,
+              jacobi=True, storage="f64", half_step=False):
+    """:func:`bicgstab` on the 2D 9-point operator (Sec. IV-A, "SpMV (2D)");
+    ``coef`` holds ``diag`` and the eight directions of :mod:`oracle.stencil9`."""
+    return _bicgstab(_Mesh9(nx, ny), coef, b, x0, tol, maxit, jacobi, storage, half_step)
+
+
+def _bicgstab(mesh, coef, b, x0, tol, maxit, jacobi, storage, half_step):
     b = np.asarray(b, dtype=np.float64)
-    if jacobi:
-        op = stencil.jacobi_scale(nx, ny, nz, coef, storage)
-        bt = stencil.scale_rhs(nx, ny, nz, coef, b)
-    else:
-        op = stencil.rounded(nx, ny, nz, coef, storage)
-        bt = b.copy()
+    n = b.size
+    op, bt = mesh.system(coef, b, jacobi, storage)
 
     def A(v):
-        return stencil.apply(nx, ny, nz, op, v)
+        return mesh.apply(op, v)
 
     x = np.zeros(n) if x0 is None else np.asarray(x0, dtype=np.float64).copy()
     bnorm = np.sqrt(_dot(bt, bt))
     hist = [0.0]
     if bnorm == 0.0:
-        return _finish(nx, ny, nz, coef, op, b, bt, np.zeros(n), 0, [0.0], OK)
+        return _finish(mesh, coef, op, b, bt, np.zeros(n), 0, [0.0], OK)
 
     r = bt - A(x)
     rhat = r.copy()
@@ -95,7 +137,7 @@ def bicgstab(nx, ny, nz, coef, b, x0=None, tol=1e-8, maxit=500,
     rho = _dot(rhat, r)
     hist = [np.sqrt(_dot(r, r)) / bnorm]
     if hist[0] <= tol:
-        return _finish(nx, ny, nz, coef, op, b, bt, x, 0, hist, OK)
+        return _finish(mesh, coef, op, b, bt, x, 0, hist, OK)
 
     status = NOTCONV
     it = 0
@@ -144,22 +186,29 @@ def bicgstab(nx, ny, nz, coef, b, x0=None, tol=1e-8, maxit=500,
         beta = (alpha / omega) * (rho_new / rho)
         p = r + beta * (p - omega * s)
         rho = rho_new
-    return _finish(nx, ny, nz, coef, op, b, bt, x, it, hist, status)
+    return _finish(mesh, coef, op, b, bt, x, it, hist, status)
 
 
-def _finish(nx, ny, nz, coef, op, b, bt, x, it, hist, status):
+def _finish(mesh, coef, op, b, bt, x, it, hist, status):
     def rel(res, rhs):
         nb = np.linalg.norm(rhs)
         return float(np.linalg.norm(res) / nb) if nb > 0 else float(np.linalg.norm(res))
 
-    tr = rel(bt - stencil.apply(nx, ny, nz, op, x), bt)
-    tro = rel(b - stencil.apply(nx, ny, nz, coef, x), b)
+    tr = rel(bt - mesh.apply(op, x), bt)
+    tro = rel(b - mesh.apply(coef, x), b)
     return Result(x, it, np.asarray(hist, dtype=np.float64), status, tr, tro)
 
 
 def true_residual(nx, ny, nz, coef, b, x):
     """``||b - A x|| / ||b||`` in float64 on the operator ``coef``."""
     r = np.asarray(b, dtype=np.float64) - stencil.apply(nx, ny, nz, coef, x)
+    nb = np.linalg.norm(b)
+    return float(np.linalg.norm(r) / nb) if nb > 0 else float(np.linalg.norm(r))
+
+
+def true_residual9(nx, ny, coef, b, x):
+    """:func:`true_residual` for the 2D 9-point operator."""
+    r = np.asarray(b, dtype=np.float64) - stencil9.apply(nx, ny, coef, x)
     nb = np.linalg.norm(b)
     return float(np.linalg.norm(r) / nb) if nb > 0 else float(np.linalg.norm(r))
 
@@ -190,29 +239,34 @@ def bicgstab_merged(nx, ny, nz, coef, b, x0=None, tol=1e-8, maxit=500, jacobi=Tr
     accumulate from step to step (carried alone, it stalls float32 solves).
     Breakdown readings as in :func:`bicgstab`, on the direct value.
     """
-    n = nx * ny * nz
+    return _bicgstab_merged(_Mesh3(nx, ny, nz), coef, b, x0, tol, maxit, jacobi, storage)
+
+
+def bicgstab9_merged(nx, ny, coef, b, x0=None, tol=1e-8, maxit=500, jacobi=True,
+                     storage="f64"):
+    """:func:`bicgstab_merged` on the 2D 9-point operator."""
+    return _bicgstab_merged(_Mesh9(nx, ny), coef, b, x0, tol, maxit, jacobi, storage)
+
+
+def _bicgstab_merged(mesh, coef, b, x0, tol, maxit, jacobi, storage):
     b = np.asarray(b, dtype=np.float64)
-    if jacobi:
-        op = stencil.jacobi_scale(nx, ny, nz, coef, storage)
-        bt = stencil.scale_rhs(nx, ny, nz, coef, b)
-    else:
-        op = stencil.rounded(nx, ny, nz, coef, storage)
-        bt = b.copy()
+    n = b.size
+    op, bt = mesh.system(coef, b, jacobi, storage)
 
     def A(v):
-        return stencil.apply(nx, ny, nz, op, v)
+        return mesh.apply(op, v)
 
     x = np.zeros(n) if x0 is None else np.asarray(x0, dtype=np.float64).copy()
     bnorm = np.sqrt(_dot(bt, bt))
     if bnorm == 0.0:
-        return _finish(nx, ny, nz, coef, op, b, bt, np.zeros(n), 0, [0.0], OK)
+        return _finish(mesh, coef, op, b, bt, np.zeros(n), 0, [0.0], OK)
     r = bt - A(x)
     rhat = r.copy()
     p = r.copy()
     rho = _dot(rhat, r)
     hist = [np.sqrt(_dot(r, r)) / bnorm]
     if hist[0] <= tol:
-        return _finish(nx, ny, nz, coef, op, b, bt, x, 0, hist, OK)
+        return _finish(mesh, coef, op, b, bt, x, 0, hist, OK)
     # first pass: s_0 = A p_0 and (r0, s_0)
     s = A(p)
     sigma = _dot(rhat, s)
@@ -259,4 +313,4 @@ def bicgstab_merged(nx, ny, nz, coef, b, x0=None, tol=1e-8, maxit=500, jacobi=Tr
             status = BREAKDOWN
             break
         rho = rho_direct
-    return _finish(nx, ny, nz, coef, op, b, bt, x, it, hist, status)
+    return _finish(mesh, coef, op, b, bt, x, it, hist, status)

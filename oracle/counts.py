@@ -55,3 +55,26 @@ def paper_storage_words(z):
     """Per-core storage of Sec. IV: six diagonals and four vectors of length
     Z (q and r_{i+1} reuse the storage of s and y), 10 Z words."""
     return 10 * z
+
+
+def ops_per_point_9pt():
+    """Credited operations per point per BiCGStab iteration on the 2D 9-point
+    operator with a unit diagonal: two matvecs of 8 multiplications and 8
+    additions (Sec. IV-A: the diagonal's multiply-add earns no credit once
+    the diagonal is preconditioned to one), four inner products and six
+    AXPYs as in Table I.  The 9-point matvec itself performs 9 fused
+    multiply-adds, 18 operations, per point (Sec. IV-A)."""
+    matvec = 2 * 8
+    return 2 * matvec + 2 * 4 + 2 * 6
+
+
+def matvec_ops_9pt(with_diagonal=True):
+    """Operations of one 9-point matvec per point: 9 multiply-adds (18), or
+    16 without the diagonal's."""
+    return 18 if with_diagonal else 16
+
+
+def bytes_per_cell_9pt(w_coef, w_vec, w_x):
+    """The fused schedule on the 9-point operator: 8 coefficient words per
+    stencil sweep, 16 w_c + 15 w_v + 2 w_x."""
+    return 16 * w_coef + 15 * w_vec + 2 * w_x

@@ -9,7 +9,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from . import stencil
+from . import stencil, stencil9
 
 
 def dense_solve(nx, ny, nz, coef, b):
@@ -75,3 +75,31 @@ def laplacian_eigenpair(nx, ny, nz, kx, ky, kz):
     lam = sum(2.0 * (1.0 - np.cos(k * np.pi / (m + 1)))
               for k, m in ((kx, nx), (ky, ny), (kz, nz)))
     return lam, v
+
+
+def dense_solve9(nx, ny, coef, b):
+    """Direct solve of the assembled 2D 9-point matrix (LAPACK LU)."""
+    a = stencil9.assemble_dense(nx, ny, coef)
+    return np.linalg.solve(a, np.asarray(b, dtype=np.float64))
+
+
+def ninepoint_eigenpair(nx, ny, a0, ax, ay, c, j, k):
+    """Eigenpair of the constant 2D 9-point operator of tensor-product form.
+
+    With ``T`` the 1D Dirichlet neighbour-sum operator (``(T u)_i = u_{i-1} +
+    u_{i+1}``, zero outside), the operator with diagonal ``a0``, axis
+    coefficients ``ax`` (x) and ``ay`` (y) and all four corner coefficients
+    ``c`` is ``a0 I + ax T_x + ay T_y + c T_x T_y``.  The sine vectors
+    ``sin(j pi (x+1)/(nx+1)) sin(k pi (y+1)/(ny+1))`` diagonalise every
+    ``T``, with eigenvalue ``2 cos(j pi/(nx+1))`` (resp. k, ny), so the
+    eigenvalue is ``a0 + 2 ax cx + 2 ay cy + 4 c cx cy``.
+    Returns ``(lambda, v)`` with ``v`` of unit 2-norm, x-fastest.
+    """
+    tx = j * np.pi / (nx + 1)
+    ty = k * np.pi / (ny + 1)
+    vx = np.sin(tx * np.arange(1, nx + 1))
+    vy = np.sin(ty * np.arange(1, ny + 1))
+    v = np.outer(vy, vx).reshape(-1)
+    v /= np.linalg.norm(v)
+    cx, cy = np.cos(tx), np.cos(ty)
+    return a0 + 2 * ax * cx + 2 * ay * cy + 4 * c * cx * cy, v

@@ -1,4 +1,5 @@
-"""Seeded synthetic problem generator for the 7-point stencil systems.
+"""Seeded synthetic problem generator for the stencil systems (3D 7-point
+and 2D 9-point).
 
 This module is shared by the CPU oracle and by the GPU path's tests and
 benchmark.  It produces *inputs only*: raw (unscaled) stencil coefficients,
@@ -18,7 +19,10 @@ Layout convention (the same everywhere in the project): a mesh of
 Coefficient direction order is ``xm, xp, ym, yp, zm, zp`` (the neighbour at
 ``x-1``, ``x+1``, ``y-1``, ``y+1``, ``z-1``, ``z+1``), following the paper's
 naming of the six off-diagonal vectors by coordinate direction and
-plus/minus (Sec. IV-A, "SpMV (3D)").
+plus/minus (Sec. IV-A, "SpMV (3D)").  The 2D 9-point systems (Sec. IV-A,
+"SpMV (2D)") live on an ``nx*ny`` mesh (``nz = 1``, ``i = x + nx*y``) with the
+eight directions ``xm, xp, ym, yp, xmym, xpym, xmyp, xpyp`` (``DIRS9``: the
+sign of the neighbour's x and y offsets).
 """
 
 from __future__ import annotations
@@ -36,6 +40,7 @@ _M2 = np.uint64(0x94D049BB133111EB)
 _TWO_M53 = float(2.0 ** -53)
 
 DIRS = ("xm", "xp", "ym", "yp", "zm", "zp")
+DIRS9 = ("xm", "xp", "ym", "yp", "xmym", "xpym", "xmyp", "xpyp")
 
 # Stream numbers inside one seed.
 STREAM_COEF = 0      # coefficient arrays (6 directions, then the diagonal margin)
@@ -264,6 +269,54 @@ def varcoef_at(nx, ny, nz, idx, seed=0, dtype=np.float32):
         coef[d] = v
         acc += np.abs(v.astype(np.float64))
     acc += 0.01 + 0.09 * uniform_at(seed, STREAM_COEF, 6 * n + idx)
+    coef["diag"] = acc.astype(dtype)
+    u1 = 1.0 - uniform_at(seed, STREAM_RHS, 2 * idx)
+    u2 = uniform_at(seed, STREAM_RHS, 2 * idx + 1)
+    b = (np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * math.pi * u2)).astype(dtype)
+    return coef, b
+
+
+def varcoef9(nx, ny, seed=0, dtype=np.float32, rhs="normal") -> Problem:
+    """The 2D 9-point analogue of :func:`varcoef`: off-diagonals
+    ``-U[0.5,1.5]`` per cell and direction (``DIRS9``), diagonal ``sum |off|
+    + U[0.01,0.1]``, ``b ~ N(0,1)`` or ``U[-1,1]``.  Direction k of the
+    coefficient stream occupies counters ``[k*n, (k+1)*n)``, the diagonal
+    margin ``[8n, 9n)``."""
+    n = nx * ny
+    coef = {}
+    for k, d in enumerate(DIRS9):
+        arr = np.empty(n, dtype=dtype)
+        coef[d] = _fill(arr, lambda s, c, k=k: _offdiag_chunk(seed, k, n, s, c, dtype))
+    diag = np.empty(n, dtype=dtype)
+
+    def diag_chunk(s, c):
+        acc = np.zeros(c, dtype=np.float64)
+        for d in DIRS9:
+            acc += np.abs(coef[d][s:s + c].astype(np.float64))
+        acc += 0.01 + 0.09 * uniform(seed, STREAM_COEF, 8 * n + s, c)
+        return acc.astype(dtype)
+
+    coef["diag"] = _fill(diag, diag_chunk)
+    b = np.empty(n, dtype=dtype)
+    if rhs == "normal":
+        _fill(b, lambda s, c: _normal_chunk(seed, STREAM_RHS, s, c).astype(dtype))
+    else:
+        _fill(b, lambda s, c: (2.0 * uniform(seed, STREAM_RHS, s, c) - 1.0).astype(dtype))
+    return Problem(nx, ny, 1, coef, b, False, seed, "varcoef9")
+
+
+def varcoef9_at(nx, ny, idx, seed=0, dtype=np.float32):
+    """Coefficients and b of :func:`varcoef9` at cells ``idx`` only (bit for
+    bit the full generator's values)."""
+    idx = np.asarray(idx, dtype=np.int64)
+    n = nx * ny
+    coef = {}
+    acc = np.zeros(idx.shape, dtype=np.float64)
+    for k, d in enumerate(DIRS9):
+        v = _as_dtype(-(0.5 + uniform_at(seed, STREAM_COEF, k * n + idx)), dtype)
+        coef[d] = v
+        acc += np.abs(v.astype(np.float64))
+    acc += 0.01 + 0.09 * uniform_at(seed, STREAM_COEF, 8 * n + idx)
     coef["diag"] = acc.astype(dtype)
     u1 = 1.0 - uniform_at(seed, STREAM_RHS, 2 * idx)
     u2 = uniform_at(seed, STREAM_RHS, 2 * idx + 1)
