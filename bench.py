@@ -60,7 +60,21 @@ def bytes_per_cell(storage, variant=0):
         k = {"spmv_p_dot": 6 * w + 6 * w, "spmv_q_dots": 6 * w + 3 * w,
              "update_dots": 5 * w + wx + w + wx}
     return k, sum(k.values())
+def bytes_per_cell9(storage, variant=0):
+    """The same for the 2D 9-point operator: 8 coefficients per sweep
+    (16 w_c + 15 w_v + 2 w_x per step; variant 1: 16 w_c + 12 w_v + 2 w_x)."""
+    w = {"f64": 8, "f32": 4, "bf16": 2, "f16": 2}[storage]
+    wx = 8 if storage == "f64" else 4
+    if variant == 1:
+        k = {"spmv_p_dot": 8 * w + 8 * w + 2 * wx, "spmv_q_dots": 8 * w + 4 * w}
+    else:
+        k = {"spmv_p_dot": 8 * w + 6 * w, "spmv_q_dots": 8 * w + 3 * w,
+             "update_dots": 5 * w + wx + w + wx}
+    return k, sum(k.values())
+
+
 FLOPS_PER_CELL = 44          # Table I of the paper
+FLOPS_PER_CELL_9PT = 52      # Table I's dots and AXPYs with two 16-flop 9-point matvecs
 PAPER_CS1_CELL_ITERS = 548352000 / 28.1e-6   # Sec. V, CS-1, mixed 16/32-bit
 
 
@@ -71,10 +85,13 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="solve",
-                    choices=["solve", "refined", "batched", "serve", "speedup", "accuracy"],
+                    choices=["solve", "solve9", "refined", "batched", "serve", "speedup",
+                             "accuracy"],
                     help="solve: FP32 600x595x1536 (default); refined: 512^3 BF16/FP16 vs FP32 "
                          "storage with FP64 refinement; batched: 512 systems; serve: request stream")
     ap.add_argument("--edge", type=int, default=512, help="refined: cube edge")
+    ap.add_argument("--edge2d", type=int, default=22800,
+                    help="solve9: edge of the square 2D mesh (Sec. IV-A's largest: 22800)")
     ap.add_argument("--systems", type=int, default=512, help="batched: number of systems")
     ap.add_argument("--requests", type=int, default=300, help="serve: requests")
     ap.add_argument("--rate", type=float, default=30.0, help="serve: arrivals per second")
@@ -391,6 +408,105 @@ def run_ours(args):
         pg.destroy_process_group()
 
 
+def kernel_table(prof, bpc, n, peak):
+    """Per-kernel launches, average time, share and algorithmic GB/s."""
+    kern = {}
+    for k, (ms, cnt) in prof.items():
+        if cnt == 0:
+            continue
+        avg = ms / cnt
+        e = {"launches": int(cnt), "avg_ms": avg, "share": None}
+        if k in bpc:
+            gbs = bpc[k] * n / (avg / 1e3) / 1e9
+            e.update({"alg_bytes_per_launch": bpc[k] * n, "gbs": gbs, "frac": gbs / peak})
+        kern[k] = e
+    tot_ms = sum(v["avg_ms"] * v["launches"] for v in kern.values())
+    for v in kern.values():
+        v["share"] = v["avg_ms"] * v["launches"] / tot_ms if tot_ms else None
+    return kern
+
+
+def run_solve9(args):
+    """BiCGStab on the 2D 9-point operator (Sec. IV-A) at its largest mesh,
+    iteration-bounded like the 3D solve line."""
+    import torch
+    import synth
+    import paper_2010_03660_gb300 as s7
+
+    rank, local, world = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    s7.lib()
+    nx = ny = args.edge2d
+    n = nx * ny
+    iters = args.iters
+    raw = np.float64 if args.storage == "f64" else np.float32
+    prob = synth.varcoef9(nx, ny, seed=rank, dtype=raw)
+    coef_d = {k: torch.from_numpy(v).to(dev) for k, v in prob.coef.items()}
+    op = s7.stencil9_create(nx, ny, coef_d, storage=args.storage, bx=args.bx,
+                            zchunk=args.zchunk, variant=args.variant)
+    del coef_d
+    torch.cuda.empty_cache()
+    b = torch.from_numpy(prob.b).to(dev)
+    x = torch.zeros(n, dtype=b.dtype, device=dev)
+    del prob
+
+    def step():
+        x.zero_()
+        return s7.bicgstab_solve(op, b, x, tol=0.0, maxit=iters, history=True)
+
+    for _ in range(args.warmup):
+        res = step()
+    torch.cuda.synchronize()
+    s7.stencil7_profile(op, True)
+    sampler = ClockSampler(local)
+    torch.cuda.synchronize()
+    sampler.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    done = 0
+    for _ in range(args.steps):
+        res = step()
+        done += res.iters
+    ev1.record()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    prof = s7.stencil7_profile(op, False)
+    op.close()
+    elapsed_ms = ev0.elapsed_time(ev1)
+    value = n * done / (elapsed_ms / 1e3)
+    peak, peak_kind = measured_peaks()
+    bpc, iter_bpc = bytes_per_cell9(args.storage, args.variant)
+    kern = kernel_table(prof, bpc, n, peak)
+    dom = max((k for k in kern if k in bpc), key=lambda k: kern[k]["avg_ms"] * kern[k]["launches"])
+    hbm_gbs = iter_bpc * n * done / (elapsed_ms / 1e3) / 1e9
+    if rank == 0:
+        print(json.dumps({
+            "metric": "cell-iters/s & HBM GB/s (BiCGStab 9-pt 2D, %dx%d)" % (nx, ny),
+            "value": value, "unit": "cell-iters/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": args.storage,
+            "data": "synthetic (seeded SplitMix64 variable-coefficient 9-point 2D system)",
+            "config": {"workload": "bicgstab9_%s_%dx%d_%dit%s" % (args.storage, nx, ny, iters,
+                                                                  "_merged" if args.variant else ""),
+                       "cells": n, "iters_per_step": iters, "storage": args.storage,
+                       "coefficients": "per-cell off-diagonals -U[0.5,1.5] (8 directions), "
+                                       "diag = sum|off| + U[0.01,0.1]",
+                       "stop": "iteration-bounded (tol 0)",
+                       "l2": "inputs larger than L2 (working set ~%d GB), no flush"
+                             % round(n * 68 / 1e9)},
+            "hbm_gbs": hbm_gbs, "hbm_frac": hbm_gbs / peak,
+            "gflops": FLOPS_PER_CELL_9PT * value / 1e9, "ms_per_iter": elapsed_ms / done,
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": kern[dom]["gbs"],
+                         "peak": peak, "unit": "GB/s", "frac": kern[dom]["gbs"] / peak,
+                         "peak_kind": peak_kind, "traffic": None},
+            "kernels": kern, "gpu_launches": int(sum(c for _, c in prof.values())),
+            "clocks": clocks,
+            "context": {"final_rel_resid": float(res.hist[-1])}}))
+
+
 def run_e2e(args, s7, prob, dev):
     import torch
     n = prob.n
@@ -702,6 +818,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "solve9":
+        run_solve9(args)
     elif args.workload == "refined":
         run_refined(args)
     elif args.workload == "batched":

@@ -113,12 +113,14 @@ typedef struct {
                         s = A p sweep, bit 1 = the q + y = A q sweep;
                         0 = default (tuned)                                    */
   int variant;       /* 0: Algorithm 1 as printed, three reductions and three
-                        passes per step.  1: two reductions per step: (r0,
-                        r_{i+1}) follows from its recurrence (r0, r_i) -
+                        passes per step.  1: two reductions per step: beta_i
+                        takes (r0, r_{i+1}) from the recurrence (r0, r_i) -
                         alpha (r0, s_i) - omega (r0, y_i), so the x and r
                         updates of one step fuse with the p update and SpMV
-                        of the next (two passes, 104 instead of 116 bytes per
-                        cell in float32; same iterates in exact arithmetic).
+                        of the next; that fused pass also reduces (r0,
+                        r_{i+1}) directly, which the next step starts from
+                        (two passes, 104 instead of 116 bytes per cell in
+                        float32; same iterates in exact arithmetic).
                         Single solves only; batched and served solves use 0. */
 } s7_opts;
 
@@ -130,6 +132,53 @@ typedef struct {
  * S7_ENOMEM if device memory runs out (nothing is leaked). */
 int stencil7_create(stencil7_t* out, int nx, int ny, int nz,
                     const s7_coeffs* coeffs, const s7_opts* opts);
+
+/* ---- the 2D 9-point operator (Sec. IV-A, "SpMV (2D)") ----
+ * A 2D mesh of nx*ny cells, x-fastest (cell (x, y) is element i = x + nx*y),
+ * with the 9-point stencil
+ *   (A v)_i = diag_i v_i + xm_i v_{i-1} + xp_i v_{i+1} + ym_i v_{i-nx}
+ *           + yp_i v_{i+nx} + xmym_i v_{i-1-nx} + xpym_i v_{i+1-nx}
+ *           + xmyp_i v_{i-1+nx} + xpyp_i v_{i+1+nx},
+ * the diagonal directions named by the signs of the neighbour's x and y
+ * offsets; neighbours outside the mesh contribute zero.  The handle is a
+ * stencil7_t like any other: stencil7_apply, stencil7_residual(_noalloc),
+ * bicgstab_solve and bicgstab_solve_refined take it unchanged (vectors have
+ * nx*ny elements; stencil7_info reports nz = 1).  bicgstab_solve_batched and
+ * the server take 7-point operators only. */
+typedef enum {
+  S9_ROWS = 0,     /* array e holds, at element i, A_{i, i+e}: row i's
+                      coefficient of its neighbour i+e                       */
+  S9_COLUMNS = 1   /* array e holds, at element j, A_{j+e, j}: the factor by
+                      which v_j enters (A v)_{j+e} -- the column storage of
+                      the paper's 2D mapping; entries whose target j+e is
+                      off-mesh are ignored                                  */
+} s9_layout;
+
+typedef struct {
+  const void* diag;
+  const void* xm;
+  const void* xp;
+  const void* ym;
+  const void* yp;
+  const void* xmym;
+  const void* xpym;
+  const void* xmyp;
+  const void* xpyp;
+  s7_dtype dtype;    /* S7_F64 or S7_F32; nx*ny elements per array (no
+                        constant mode); host or device memory               */
+  int layout;        /* s9_layout                                           */
+} s9_coeffs;
+
+/* Create a 9-point operator handle.  Like stencil7_create: the coefficients
+ * are copied to library-owned device memory (column layout converted to
+ * rows), scaled to a unit diagonal in float64 and rounded once to the
+ * storage type unless opts->no_jacobi.  In opts, bx is the number of threads
+ * across a row strip (each VEC cells, <= 512), zchunk the rows per thread
+ * block, by must be 0 or 1, and stages / pipe_kinds are ignored.  nx, ny >= 1,
+ * nx*ny < 2^40.  Errors as for stencil7_create (S7_EINVAL also for a bad
+ * layout). */
+int stencil9_create(stencil7_t* out, int nx, int ny, const s9_coeffs* coeffs,
+                    const s7_opts* opts);
 
 /* Release a handle and all device memory it owns.  NULL is accepted. */
 int stencil7_destroy(stencil7_t h);

@@ -11,7 +11,9 @@ GPU is visible, calls raise.
 Layout: a mesh vector has ``nx*ny*nz`` elements, x fastest
 (``i = x + nx*(y + ny*z)``).  Coefficients: ``diag`` and the six
 off-diagonals ``xm, xp, ym, yp, zm, zp`` (Sec. IV-A of the paper names them by
-axis and sign).
+axis and sign).  :func:`stencil9_create` builds the 2D 9-point operator of
+Sec. IV-A on an ``nx*ny`` mesh (``i = x + nx*y``; directions ``DIRS9``); its
+handle works with every single-system entry point.
 """
 
 from __future__ import annotations
@@ -26,7 +28,7 @@ from . import _build
 
 __all__ = [
     "S7_F64", "S7_F32", "S7_BF16", "S7_F16", "S7Error", "Operator", "lib", "EXPORTS",
-    "stencil7_create", "stencil7_destroy", "stencil7_info", "stencil7_apply",
+    "stencil7_create", "stencil9_create", "stencil7_destroy", "stencil7_info", "stencil7_apply",
     "stencil7_residual", "stencil7_residual_noalloc", "bicgstab_solve",
     "bicgstab_solve_refined", "bicgstab_solve_batched", "stencil7_profile", "s7_last_error",
     "s7_version", "Server", "s7_server_create", "s7_server_submit", "s7_server_poll",
@@ -38,11 +40,13 @@ OK, EINVAL, ENOMEM, EBREAKDOWN, ENOTCONV, ETIMEOUT, ECUDA, EAGAIN, ECANCELED = r
 STATUS_NAMES = {0: "ok", 1: "einval", 2: "enomem", 3: "breakdown", 4: "notconv",
                 5: "timeout", 6: "ecuda", 7: "eagain", 8: "canceled"}
 DIRS = ("xm", "xp", "ym", "yp", "zm", "zp")
+DIRS9 = ("xm", "xp", "ym", "yp", "xmym", "xpym", "xmyp", "xpyp")
+S9_ROWS, S9_COLUMNS = 0, 1
 _STORAGE = {"f64": S7_F64, "f32": S7_F32, "bf16": S7_BF16, "f16": S7_F16}
 
 # Entry points declared in include/stencil7.h (checked by the tests).
 EXPORTS = (
-    "stencil7_create", "stencil7_destroy", "stencil7_info", "stencil7_apply",
+    "stencil7_create", "stencil9_create", "stencil7_destroy", "stencil7_info", "stencil7_apply",
     "stencil7_residual", "stencil7_residual_noalloc", "bicgstab_solve",
     "bicgstab_solve_refined", "bicgstab_solve_batched", "stencil7_profile", "s7_last_error",
     "s7_version", "s7_server_create", "s7_server_submit", "s7_server_poll", "s7_server_wait",
@@ -62,6 +66,11 @@ class s7_coeffs(C.Structure):
     _fields_ = [("diag", C.c_void_p), ("xm", C.c_void_p), ("xp", C.c_void_p),
                 ("ym", C.c_void_p), ("yp", C.c_void_p), ("zm", C.c_void_p),
                 ("zp", C.c_void_p), ("dtype", C.c_int), ("constant", C.c_int)]
+
+
+class s9_coeffs(C.Structure):
+    _fields_ = [("diag", C.c_void_p)] + [(k, C.c_void_p) for k in DIRS9] + \
+               [("dtype", C.c_int), ("layout", C.c_int)]
 
 
 class s7_opts(C.Structure):
@@ -120,6 +129,7 @@ def lib():
     P = C.POINTER
     sig = {
         "stencil7_create": (i, [P(vp), i, i, i, P(s7_coeffs), P(s7_opts)]),
+        "stencil9_create": (i, [P(vp), i, i, P(s9_coeffs), P(s7_opts)]),
         "stencil7_destroy": (i, [vp]),
         "stencil7_info": (i, [vp, P(i), P(i), P(i), P(i), P(C.c_size_t)]),
         "stencil7_apply": (i, [vp, vp, vp, i, vp]),
@@ -297,6 +307,39 @@ def stencil7_create(nx, ny, nz, coef, storage="f32", jacobi=True, keep_true=Fals
     _check(lib().stencil7_create(C.byref(h), nx, ny, nz, C.byref(cs), C.byref(op)))
     del keep
     return Operator(h.value, nx, ny, nz, st)
+
+
+def stencil9_create(nx, ny, coef, storage="f32", jacobi=True, keep_true=False, bx=0,
+                    zchunk=0, check_every=0, variant=0, layout="rows"):
+    """Create a 2D 9-point operator from raw coefficients.
+
+    ``coef`` maps ``diag`` and the eight directions of ``DIRS9`` to
+    arrays/tensors of ``nx*ny`` float32 or float64 values (all the same
+    type).  ``layout="rows"``: array e holds row i's coefficient of its
+    neighbour i+e; ``"columns"``: array e holds, at cell j, the factor by
+    which v_j enters the output at j+e (the paper's column storage).  The
+    returned :class:`Operator` has ``nz = 1``.
+    """
+    names = ("diag",) + DIRS9
+    raw_dt = _dtype_code(coef["diag"])
+    keep, ptrs = [], {}
+    for k in names:
+        a = coef[k]
+        if _numel(a) != nx * ny:
+            raise ValueError("coefficient %s has %d elements, expected %d" % (k, _numel(a), nx * ny))
+        if _dtype_code(a) != raw_dt:
+            raise ValueError("all coefficients must have the same dtype")
+        keep.append(a)
+        ptrs[k] = _ptr(a)
+    lay = {"rows": S9_ROWS, "columns": S9_COLUMNS}[layout] if isinstance(layout, str) else layout
+    cs = s9_coeffs(ptrs["diag"], *[ptrs[k] for k in DIRS9], raw_dt, lay)
+    st = _STORAGE[storage] if isinstance(storage, str) else int(storage)
+    op = s7_opts(st, 0 if jacobi else 1, 1 if keep_true else 0, bx, 0, zchunk, check_every,
+                 0, 0, variant)
+    h = C.c_void_p()
+    _check(lib().stencil9_create(C.byref(h), nx, ny, C.byref(cs), C.byref(op)))
+    del keep
+    return Operator(h.value, nx, ny, 1, st)
 
 
 def stencil7_destroy(op):

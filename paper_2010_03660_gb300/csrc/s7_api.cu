@@ -194,6 +194,21 @@ void default_tile(int nx, int ny, int nz, int vec, int nsm, Tile* t) {
   t->by = by;
   t->zchunk = (int)zc;
 }
+
+void default_tile9(int nx, int ny, int vec, int nsm, Tile* t) {
+  const int runs = (nx + vec - 1) / vec;
+  const int ntx = (runs + 127) / 128;
+  const int bx = (runs + ntx - 1) / ntx;    // <= 128 runs per strip, balanced strips
+  // rows per block: about eight blocks per SM, long enough that the two
+  // extra rows each chunk reads stay a small fraction
+  const long long target = (long long)nsm * 8;
+  long long rc = ((long long)ntx * ny + target - 1) / target;
+  rc = std::max(8LL, std::min(4096LL, rc));
+  if (rc > ny) rc = ny;
+  t->bx = bx;
+  t->by = 1;
+  t->zchunk = (int)rc;
+}
 }  // namespace s7
 
 // ---------------------------------------------------------------------------
@@ -227,10 +242,10 @@ static void release(Handle* h) {
   if (w.h_sc) cudaFreeHost(w.h_sc);
   w.h_sc = nullptr;
   w.ready = false;
-  for (int d = 0; d < 6; ++d) dfree(h, &h->c[d], n * ts);
+  for (int d = 0; d < 8; ++d) dfree(h, &h->c[d], n * ts);
   dfree(h, &h->diag, n * ts);
   dfree(h, &h->d, n * dsize(xtype(h)));
-  for (int d = 0; d < 7; ++d) dfree(h, (void**)&h->tc[d], n * 4);
+  for (int d = 0; d < 9; ++d) dfree(h, (void**)&h->tc[d], n * 4);
   dfree(h, &h->small, 256);
   prof_free(h);
   if (h->ev) cudaEventDestroy(h->ev);
@@ -418,6 +433,126 @@ extern "C" int stencil7_create(stencil7_t* out, int nx, int ny, int nz, const s7
   return S7_OK;
 
 fail_out:
+  release(h);
+  delete h;
+  return rc;
+}
+
+extern "C" int stencil9_create(stencil7_t* out, int nx, int ny, const s9_coeffs* c,
+                               const s7_opts* o) {
+  if (!out) return fail(S7_EINVAL, "stencil9_create: out is NULL");
+  *out = nullptr;
+  if (!c) return fail(S7_EINVAL, "stencil9_create: coeffs is NULL");
+  if (nx < 1 || ny < 1) return fail(S7_EINVAL, "stencil9_create: sizes must be >= 1");
+  const long long n = (long long)nx * ny;
+  if (n >= (1LL << 40)) return fail(S7_EINVAL, "stencil9_create: mesh too large");
+  if (c->dtype != S7_F64 && c->dtype != S7_F32)
+    return fail(S7_EINVAL, "stencil9_create: raw coefficients must be S7_F64 or S7_F32");
+  if (c->layout != S9_ROWS && c->layout != S9_COLUMNS)
+    return fail(S7_EINVAL, "stencil9_create: layout must be S9_ROWS or S9_COLUMNS");
+  const void* raw_in[9] = {c->xm, c->xp, c->ym, c->yp, c->xmym, c->xpym, c->xmyp, c->xpyp,
+                           c->diag};
+  for (int d = 0; d < 9; ++d)
+    if (!raw_in[d]) return fail(S7_EINVAL, "stencil9_create: coefficient pointer %d is NULL", d);
+  s7_opts opts;
+  memset(&opts, 0, sizeof opts);
+  if (o) opts = *o;
+  if (opts.by > 1) return fail(S7_EINVAL, "stencil9_create: by must be 0 or 1");
+  if (opts.variant < 0 || opts.variant > 1)
+    return fail(S7_EINVAL, "stencil9_create: variant must be 0 or 1");
+  bind_caller_device();
+  const Engine* eng = engine_for(opts.storage);
+  if (!eng) return fail(S7_EINVAL, "stencil9_create: unknown storage type %d", (int)opts.storage);
+
+  stencil7_op* h = new (std::nothrow) stencil7_op();
+  if (!h) return fail(S7_ENOMEM, "stencil9_create: host allocation failed");
+  h->nx = nx;
+  h->ny = ny;
+  h->nz = 1;
+  h->n = n;
+  h->stencil = 9;
+  h->storage = opts.storage;
+  h->jacobi = opts.no_jacobi ? 0 : 1;
+  h->keep_true = opts.keep_true ? 1 : 0;
+  h->constant = 0;
+  cudaGetDevice(&h->device);
+  default_tile9(nx, ny, eng->vec, num_sms(), &h->tile);
+  if (opts.bx > 0) h->tile.bx = opts.bx;
+  if (opts.zchunk > 0) h->tile.zchunk = std::min(opts.zchunk, ny);
+  if (h->tile.bx > 512) {
+    delete h;
+    return fail(S7_EINVAL, "stencil9_create: bx must be <= 512");
+  }
+  {
+    const double est_us = std::max(15.0, 130.0 * (double)n / 6.0e6);
+    int ce = (int)std::min(64.0, std::max(2.0, 1000.0 / est_us));
+    h->check_every = opts.check_every > 0 ? opts.check_every : ce;
+  }
+  h->stages = 1;        // the 9-point sweeps load directly
+  h->pipe_kinds = 0;
+  h->variant = opts.variant;
+  if (!eng->smem_ok(h)) {
+    delete h;
+    return fail(S7_EINVAL, "stencil9_create: tile too large for shared memory");
+  }
+
+  int rc = S7_OK;
+  cudaError_t e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    rc = cuda_fail(e, "stream/event creation");
+    release(h);
+    delete h;
+    return rc;
+  }
+  const size_t ts = eng->t_size;
+  const void* raw_dev[9];
+  void* stage[9] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  if ((rc = dmalloc(h, &h->small, 256))) goto fail9;
+  for (int d = 0; d < 8; ++d)
+    if ((rc = dmalloc(h, &h->c[d], (size_t)n * ts))) goto fail9;
+  if (!h->jacobi && (rc = dmalloc(h, &h->diag, (size_t)n * ts))) goto fail9;
+  if (h->jacobi && (rc = dmalloc(h, &h->d, (size_t)n * dsize(xtype(h))))) goto fail9;
+  if (h->keep_true)
+    for (int d = 0; d < 9; ++d)
+      if ((rc = dmalloc(h, (void**)&h->tc[d], (size_t)n * 4))) goto fail9;
+  {
+    // stage host arrays on the device, one at a time as needed
+    const size_t rs = dsize(c->dtype);
+    for (int d = 0; d < 9 && rc == S7_OK; ++d) {
+      if (on_device(raw_in[d])) {
+        raw_dev[d] = raw_in[d];
+        continue;
+      }
+      void* p = nullptr;
+      if ((e = cudaMalloc(&p, (size_t)n * rs)) != cudaSuccess) {
+        cudaGetLastError();
+        rc = fail(S7_ENOMEM, "staging coefficients: %s", cudaGetErrorString(e));
+        break;
+      }
+      stage[d] = p;
+      if ((e = cudaMemcpyAsync(p, raw_in[d], (size_t)n * rs, cudaMemcpyDefault, h->stream)) !=
+          cudaSuccess) {
+        rc = cuda_fail(e, "copying coefficients");
+        break;
+      }
+      raw_dev[d] = p;
+    }
+    if (rc == S7_OK) {
+      int bad = 0;
+      rc = eng->scale9(h, raw_dev, c->dtype, c->layout == S9_COLUMNS, h->stream, &bad);
+      if (rc) rc = fail(rc, "coefficient scaling failed: %s", cudaGetErrorString(cudaGetLastError()));
+      else if (bad) rc = fail(S7_EINVAL, "stencil9_create: %d zero or non-finite diagonal entries", bad);
+    }
+    cudaStreamSynchronize(h->stream);
+    for (int d = 0; d < 9; ++d)
+      if (stage[d]) cudaFree(stage[d]);
+    if (rc) goto fail9;
+  }
+  *out = h;
+  return S7_OK;
+
+fail9:
   release(h);
   delete h;
   return rc;
@@ -986,6 +1121,8 @@ extern "C" int bicgstab_solve_batched(int nsys, const stencil7_t* hs_in, const v
   for (int j = 0; j < nsys; ++j) {
     hs[j] = hs_in[j];
     if (!hs[j] || !b[j] || !x[j]) return fail(S7_EINVAL, "bicgstab_solve_batched: NULL system %d", j);
+    if (hs[j]->stencil != 7)
+      return fail(S7_EINVAL, "bicgstab_solve_batched: system %d is not a 7-point operator", j);
     if (hs[j]->storage != hs[0]->storage || hs[j]->device != hs[0]->device)
       return fail(S7_EINVAL, "bicgstab_solve_batched: mixed storage types or devices");
     if (maxit[j] < 0 || !(tol[j] >= 0.0))

@@ -11,6 +11,7 @@
 #include "s7_handle.h"
 #include "s7_step.cuh"
 #include "s7_sweep.cuh"
+#include "s7_sweep9.cuh"
 
 namespace s7 {
 
@@ -173,7 +174,26 @@ inline int pointwise_grid(long long n, int per_thread) {
   return (int)std::max(1LL, std::min(want, cap));
 }
 
+// A 2D 9-point mesh is a Geom with ny = 1, nz = rows, plane = nx, tiles
+// of bx runs by one row (see s7_sweep9.cuh).
+inline Geom make_geom9(const Handle* h, int vec) {
+  Geom g;
+  g.nx = h->nx;
+  g.ny = 1;
+  g.nz = h->ny;
+  const int runs = (h->nx + vec - 1) / vec;
+  g.bx = std::min(h->tile.bx, runs);
+  g.by = 1;
+  g.tiles_x = (runs + g.bx - 1) / g.bx;
+  g.tiles_y = 1;
+  g.zchunk = std::min(h->tile.zchunk, h->ny);
+  g.nchunks = (h->ny + g.zchunk - 1) / g.zchunk;
+  g.plane = h->nx;
+  return g;
+}
+
 inline Geom make_geom(const Handle* h, int vec) {
+  if (h->stencil == 9) return make_geom9(h, vec);
   Geom g;
   g.nx = h->nx;
   g.ny = h->ny;
@@ -234,6 +254,30 @@ int launch_sweep1(const Geom& g, const CoefView<CT, A>& cf, const P& pol, Scalar
   return cudaGetLastError() == cudaSuccess ? S7_OK : S7_ECUDA;
 }
 
+template <class CT, class A, int VEC, class Src, class Epi>
+int launch_sweep9(const Geom& g, const CoefView9<CT, A>& cf, const Src& src, const Epi& epi,
+                  Scalars* sc, bool vl, cudaStream_t st) {
+  const int threads = ((g.bx + 31) / 32) * 32;
+  const size_t smem = sweep9_smem<A, VEC>(g);
+  void (*kern)(Geom, CoefView9<CT, A>, Src, Epi, Scalars*) =
+      vl ? k_sweep9<CT, A, VEC, true, Src, Epi> : k_sweep9<CT, A, VEC, false, Src, Epi>;
+  if (allow_smem((const void*)kern, smem, st)) return S7_ECUDA;
+  kern<<<s7_nblocks(g), threads, smem, st>>>(g, cf, src, epi, sc);
+  return cudaGetLastError() == cudaSuccess ? S7_OK : S7_ECUDA;
+}
+
+template <class CT, class A, int VEC, class P>
+int launch_sweep9_1(const Geom& g, const CoefView9<CT, A>& cf, const P& pol, Scalars* sc,
+                    bool vl, cudaStream_t st) {
+  const int threads = ((g.bx + 31) / 32) * 32;
+  const size_t smem = sweep9_smem<A, VEC>(g);
+  void (*kern)(Geom, CoefView9<CT, A>, P, Scalars*) =
+      vl ? k_sweep9_1<CT, A, VEC, true, P> : k_sweep9_1<CT, A, VEC, false, P>;
+  if (allow_smem((const void*)kern, smem, st)) return S7_ECUDA;
+  kern<<<s7_nblocks(g), threads, smem, st>>>(g, cf, pol, sc);
+  return cudaGetLastError() == cudaSuccess ? S7_OK : S7_ECUDA;
+}
+
 template <class T_, class X_, class DT_, class A_>
 struct EngineImpl {
   typedef T_ T;
@@ -256,6 +300,47 @@ struct EngineImpl {
     cf.diag = h->jacobi ? nullptr : (const T*)h->diag;
     cf.cdiag = h->jacobi ? AA(1) : (AA)h->cconst[6];
     return cf;
+  }
+
+  template <class AA>
+  static CoefView9<T, AA> stored9(const Handle* h) {
+    CoefView9<T, AA> cf;
+    for (int d = 0; d < 8; ++d) cf.c[d] = (const T*)h->c[d];
+    cf.diag = h->jacobi ? nullptr : (const T*)h->diag;
+    cf.cdiag = AA(1);
+    return cf;
+  }
+
+  // One sweep of the stored operator (7- or 9-point) with policies src/epi.
+  template <class AA, int V, class Src, class Epi>
+  static int run_sweep(const Handle* h, const Src& src, const Epi& epi, Scalars* sc, bool vl,
+                       cudaStream_t st) {
+    const Geom g = make_geom(h, V);
+    if (h->stencil == 9) return launch_sweep9<T, AA, V>(g, stored9<AA>(h), src, epi, sc, vl, st);
+    return launch_sweep<T, AA, V>(g, stored<AA>(h), src, epi, sc, vl, st);
+  }
+
+  // One float64 sweep of the raw float32 operator kept by keep_true.
+  template <int V, class Src, class Epi>
+  static int run_true_sweep(const Handle* h, const Src& src, const Epi& epi, Scalars* sc,
+                            bool vl, cudaStream_t st) {
+    const Geom g = make_geom(h, V);
+    if (h->stencil == 9) {
+      CoefView9<float, double> cf;
+      for (int d = 0; d < 8; ++d) cf.c[d] = h->tc[d];
+      cf.diag = h->tc[8];
+      cf.cdiag = 1.0;
+      return launch_sweep9<float, double, V>(g, cf, src, epi, sc, vl, st);
+    }
+    CoefView<float, double> cf;
+    for (int d = 0; d < 6; ++d) {
+      cf.c[d] = h->tc[d];
+      cf.cc[d] = 0.0;
+    }
+    cf.diag = h->tc[6];
+    cf.cdiag = 1.0;
+    cf.constant = 0;
+    return launch_sweep<float, double, V>(g, cf, src, epi, sc, vl, st);
   }
 
   static int scale(Handle* h, const void* const raw[7], s7_dtype raw_dt, cudaStream_t st, int* bad) {
@@ -282,16 +367,49 @@ struct EngineImpl {
     return cudaGetLastError() == cudaSuccess ? S7_OK : S7_ECUDA;
   }
 
+  static int scale9(Handle* h, const void* const raw[9], s7_dtype raw_dt, int columns,
+                    cudaStream_t st, int* bad) {
+    // neighbour offsets of xm xp ym yp xmym xpym xmyp xpyp, and the index of
+    // the opposite direction (the column array a row entry comes from)
+    static const int DX[8] = {-1, 1, 0, 0, -1, 1, -1, 1};
+    static const int DY[8] = {0, 0, -1, 1, -1, -1, 1, 1};
+    static const int OPP[8] = {1, 0, 3, 2, 7, 6, 5, 4};
+    const long long n = h->n;
+    const int grid = pointwise_grid(n, 4);
+    unsigned int* d_bad = (unsigned int*)h->small;
+    cudaMemsetAsync(d_bad, 0, sizeof(unsigned int), st);
+#define S7_SCALE9(RT)                                                                             \
+  {                                                                                               \
+    const RT* dg = (const RT*)raw[8];                                                             \
+    k_keep_diag<RT, DT><<<grid, 256, 0, st>>>(n, dg, (DT*)h->d, d_bad);                           \
+    for (int d = 0; d < 8; ++d) {                                                                 \
+      const RT* src = (const RT*)raw[columns ? OPP[d] : d];                                       \
+      k_scale9<RT, T><<<grid, 256, 0, st>>>(n, h->nx, h->ny, src, DX[d], DY[d], columns, dg,      \
+                                            (T*)h->c[d], h->jacobi);                              \
+      if (h->keep_true)                                                                           \
+        k_scale9<RT, float><<<grid, 256, 0, st>>>(n, h->nx, h->ny, src, DX[d], DY[d], columns,    \
+                                                  dg, h->tc[d], 0);                               \
+    }                                                                                             \
+    if (!h->jacobi) k_scale<RT, T><<<grid, 256, 0, st>>>(n, dg, dg, (T*)h->diag, 0);              \
+    if (h->keep_true) k_cast<RT, float><<<grid, 256, 0, st>>>(n, dg, h->tc[8]);                    \
+  }
+    if (raw_dt == S7_F64) S7_SCALE9(double) else S7_SCALE9(float)
+#undef S7_SCALE9
+    unsigned int hb = 0;
+    cudaMemcpyAsync(&hb, d_bad, sizeof hb, cudaMemcpyDeviceToHost, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess) return S7_ECUDA;
+    *bad = (int)hb;
+    return cudaGetLastError() == cudaSuccess ? S7_OK : S7_ECUDA;
+  }
+
   static int apply(Handle* h, const void* x, void* y, cudaStream_t st) {
-    const Geom g = make_geom(h, VEC);
     SrcPlain<T, A> src{(const T*)x};
     EpiStore<T, A> epi{(T*)y};
     const bool vl = (h->nx % VEC == 0) && aligned16(x) && aligned16(y);
-    return launch_sweep<T, A, VEC>(g, stored<A>(h), src, epi, nullptr, vl, st);
+    return run_sweep<A, VEC>(h, src, epi, nullptr, vl, st);
   }
 
   static int init(Handle* h, const void* b, cudaStream_t st) {
-    const Geom g = make_geom(h, VEC);
     Workspace& w = h->ws;
     SrcPlain<X, A> src{(const X*)w.x};
     EpiResid<X, T, DT, A> epi;
@@ -306,13 +424,14 @@ struct EngineImpl {
     epi.counter = CNT_INIT;
     epi.mode = 0;
     const bool vl = (h->nx % VEC == 0) && aligned16(b);
-    return launch_sweep<T, A, VEC>(g, stored<A>(h), src, epi, w.sc, vl, st);
+    return run_sweep<A, VEC>(h, src, epi, w.sc, vl, st);
   }
 
   // The pipelined sweeps serve the common case: Jacobi-scaled per-cell
   // coefficients, rows of whole 16-byte vectors, at most 256 threads.
   static bool pipelined(const Handle* h, const Geom& g, int kind) {
-    return h->stages >= 2 && ((h->pipe_kinds >> kind) & 1) && h->jacobi && !h->constant &&
+    return h->stencil == 7 && h->stages >= 2 && ((h->pipe_kinds >> kind) & 1) && h->jacobi &&
+           !h->constant &&
            h->nx % VEC == 0 &&
            g.bx * g.by <= 256 &&
            step_smem_bytes<T, A, VEC>(g.bx, g.by, h->stages, kind) <= 200 * 1024;
@@ -349,6 +468,18 @@ struct EngineImpl {
               cudaSuccess)
         rc = S7_ECUDA;
     };
+    if (h->stencil == 9) {
+      const size_t b9 = sweep9_smem<A, VEC>(g);
+      set((const void*)k_sweep9<T, A, VEC, true, SrcPUpdate<T, A>, EpiS<T, A>>, b9);
+      set((const void*)k_sweep9<T, A, VEC, false, SrcPUpdate<T, A>, EpiS<T, A>>, b9);
+      set((const void*)k_sweep9<T, A, VEC, true, SrcQ<T, A>, EpiY<T, A>>, b9);
+      set((const void*)k_sweep9<T, A, VEC, false, SrcQ<T, A>, EpiY<T, A>>, b9);
+      set((const void*)k_sweep9<T, A, VEC, true, SrcQ2<T, A>, EpiYMerged<T, A>>, b9);
+      set((const void*)k_sweep9<T, A, VEC, false, SrcQ2<T, A>, EpiYMerged<T, A>>, b9);
+      set((const void*)k_sweep9_1<T, A, VEC, true, MergedPass<T, X, A>>, b9);
+      set((const void*)k_sweep9_1<T, A, VEC, false, MergedPass<T, X, A>>, b9);
+      return rc;
+    }
     for (int kind = 0; kind < 2; ++kind) {
       if (!pipelined(h, g, kind)) continue;
       const size_t b = step_smem_bytes<T, A, VEC>(g.bx, g.by, h->stages, kind);
@@ -374,7 +505,6 @@ struct EngineImpl {
   static int step_kernel(Handle* h, int which, cudaStream_t st) {
     const Geom g = make_geom(h, VEC);
     Workspace& w = h->ws;
-    const CoefView<T, A> cf = stored<A>(h);
     const bool vl = (h->nx % VEC == 0);
     if (which < 2 && pipelined(h, g, which)) {
       if (which == 0)
@@ -395,7 +525,7 @@ struct EngineImpl {
       ea.sbuf[1] = (T*)w.s[1];
       ea.rh = (const T*)w.rh;
       ea.parts = w.parts;
-      return launch_sweep<T, A, VEC>(g, cf, sa, ea, w.sc, vl, st);
+      return run_sweep<A, VEC>(h, sa, ea, w.sc, vl, st);
     }
     if (which == 1) {
       SrcQ<T, A> sb;
@@ -405,7 +535,7 @@ struct EngineImpl {
       EpiY<T, A> eb;
       eb.y_out = (T*)w.y;
       eb.parts = w.parts;
-      return launch_sweep<T, A, VEC>(g, cf, sb, eb, w.sc, vl, st);
+      return run_sweep<A, VEC>(h, sb, eb, w.sc, vl, st);
     }
     k_update<T, X, A, VEC><<<pointwise_grid(h->n / VEC + 1, 1), 256, 0, st>>>(
         h->n, (const T*)w.p[0], (const T*)w.p[1], (const T*)w.s[0], (const T*)w.s[1],
@@ -417,7 +547,6 @@ struct EngineImpl {
     if (which == 0) return step_kernel(h, 0, st);   // s_0 = A p_0 at step 0
     const Geom g = make_geom(h, VEC);
     Workspace& w = h->ws;
-    const CoefView<T, A> cf = stored<A>(h);
     const bool vl = (h->nx % VEC == 0);
     if (which == 1) {
       SrcQ2<T, A> sb;
@@ -429,7 +558,7 @@ struct EngineImpl {
       eb.y_out = (T*)w.y;
       eb.rh = (const T*)w.rh;
       eb.parts = w.parts;
-      return launch_sweep<T, A, VEC>(g, cf, sb, eb, w.sc, vl, st);
+      return run_sweep<A, VEC>(h, sb, eb, w.sc, vl, st);
     }
     MergedPass<T, X, A> m;
     m.rbuf[0] = (T*)w.r;
@@ -443,12 +572,12 @@ struct EngineImpl {
     m.x = (X*)w.x;
     m.parts = w.parts;
     m.hist = w.hist;
-    return launch_sweep1<T, A, VEC>(g, cf, m, w.sc, vl, st);
+    if (h->stencil == 9) return launch_sweep9_1<T, A, VEC>(g, stored9<A>(h), m, w.sc, vl, st);
+    return launch_sweep1<T, A, VEC>(g, stored<A>(h), m, w.sc, vl, st);
   }
 
   // ||b~ - A~ x|| and ||b~|| with float64 accumulation -> sc->res[0], res[1].
   static int true_resid(Handle* h, const void* b, cudaStream_t st) {
-    const Geom g = make_geom(h, VEC);
     Workspace& w = h->ws;
     SrcPlain<X, double> src{(const X*)w.x};
     EpiResid<X, T, DT, double> epi;
@@ -463,7 +592,7 @@ struct EngineImpl {
     epi.counter = CNT_RES;
     epi.mode = 1;
     const bool vl = (h->nx % VEC == 0) && aligned16(b);
-    return launch_sweep<T, double, VEC>(g, stored<double>(h), src, epi, w.sc, vl, st);
+    return run_sweep<double, VEC>(h, src, epi, w.sc, vl, st);
   }
 
   template <class XT>
@@ -471,15 +600,6 @@ struct EngineImpl {
     Workspace& w = h->ws;
     if (h->keep_true) {
       constexpr int V = 16 / (int)sizeof(XT) < 4 ? 16 / (int)sizeof(XT) : 4;
-      const Geom g = make_geom(h, V);
-      CoefView<float, double> cf;
-      for (int d = 0; d < 6; ++d) {
-        cf.c[d] = h->tc[d];
-        cf.cc[d] = 0.0;
-      }
-      cf.diag = h->tc[6];
-      cf.cdiag = 1.0;
-      cf.constant = 0;
       SrcPlain<XT, double> src{x};
       EpiResid<XT, XT, float, double> epi;
       epi.b = b;
@@ -493,9 +613,8 @@ struct EngineImpl {
       epi.counter = CNT_RES;
       epi.mode = 1;
       const bool vl = (h->nx % V == 0) && aligned16(b) && aligned16(x) && (!r || aligned16(r));
-      return launch_sweep<float, double, V>(g, cf, src, epi, w.sc, vl, st);
+      return run_true_sweep<V>(h, src, epi, w.sc, vl, st);
     }
-    const Geom g = make_geom(h, VEC);
     SrcPlain<XT, double> src{x};
     EpiResid<XT, XT, DT, double> epi;
     epi.b = b;
@@ -509,7 +628,7 @@ struct EngineImpl {
     epi.counter = CNT_RES;
     epi.mode = 1;
     const bool vl = (h->nx % VEC == 0) && aligned16(b) && aligned16(x) && (!r || aligned16(r));
-    return launch_sweep<T, double, VEC>(g, stored<double>(h), src, epi, w.sc, vl, st);
+    return run_sweep<double, VEC>(h, src, epi, w.sc, vl, st);
   }
 
   static int raw_resid(Handle* h, const void* b, const void* x, void* r, s7_dtype dt, cudaStream_t st) {
@@ -534,15 +653,6 @@ struct EngineImpl {
     SrcPlain<XT, double> src{x};
     if (h->keep_true) {
       constexpr int V = 16 / (int)sizeof(XT) < 4 ? 16 / (int)sizeof(XT) : 4;
-      const Geom g = make_geom(h, V);
-      CoefView<float, double> cf;
-      for (int d = 0; d < 6; ++d) {
-        cf.c[d] = h->tc[d];
-        cf.cc[d] = 0.0;
-      }
-      cf.diag = h->tc[6];
-      cf.cdiag = 1.0;
-      cf.constant = 0;
       EpiResid<XT, XT, float, double> e2;
       e2.b = b;
       e2.dinv = nullptr;
@@ -554,13 +664,11 @@ struct EngineImpl {
       e2.parts = parts;
       e2.counter = CNT_RES;
       e2.mode = 1;
-      return launch_sweep<float, double, V>(g, cf, src, e2, sc, (h->nx % V == 0) && al, st);
+      return run_true_sweep<V>(h, src, e2, sc, (h->nx % V == 0) && al, st);
     }
-    const Geom g = make_geom(h, VEC);
     epi.dmul = (h->jacobi && !h->constant) ? (const DT*)h->d : nullptr;
     epi.dmc = (h->jacobi && h->constant) ? h->cconst[6] : 1.0;
-    return launch_sweep<T, double, VEC>(g, stored<double>(h), src, epi, sc,
-                                        (h->nx % VEC == 0) && al, st);
+    return run_sweep<double, VEC>(h, src, epi, sc, (h->nx % VEC == 0) && al, st);
   }
 
   static int raw_resid_into(Handle* h, const void* b, const void* x, void* r, s7_dtype dt,
@@ -597,6 +705,7 @@ struct EngineImpl {
 
   static int smem_ok(const Handle* h) {
     const Geom g = make_geom(h, VEC);
+    if (h->stencil == 9) return g.bx <= 512 && sweep9_smem<double, VEC>(g) <= 200 * 1024;
     const size_t smem = (size_t)3 * (g.by + 2) * (g.bx * VEC + 2 * VEC) * sizeof(double);
     return smem <= 200 * 1024 && g.bx * g.by <= 512;
   }
@@ -693,7 +802,8 @@ struct EngineImpl {
   }
 
   static const Engine* get() {
-    static const Engine e = {sizeof(T), sizeof(X), sizeof(DT), VEC, &scale, &apply, &init, &step_kernel,
+    static const Engine e = {sizeof(T), sizeof(X), sizeof(DT), VEC, &scale, &scale9, &apply, &init,
+                             &step_kernel,
                              &true_resid, &raw_resid, &cast, &parts_needed, &smem_ok,
                              &raw_resid_into, &raw_resid_blocks, &prepare_capture,
                              &merged_kernel,

@@ -43,19 +43,23 @@ struct Tile {
 };
 
 struct Handle {
-  int nx, ny, nz;
+  int nx, ny, nz;             // a 2D 9-point mesh has nz = 1
   long long n;
+  int stencil = 7;            // 7: 3D 7-point operator; 9: 2D 9-point operator
   s7_dtype storage;
   int jacobi;       // 1: stored operator is D^-1 A (unit diagonal)
   int keep_true;
   int constant;
   int device;
-  // stored operator (element type = storage)
-  void* c[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  // stored operator (element type = storage): xm xp ym yp zm zp, or for the
+  // 9-point operator xm xp ym yp xmym xpym xmyp xpyp
+  void* c[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   void* diag = nullptr;       // raw diagonal (no_jacobi) in storage type
   double cconst[7] = {0, 0, 0, 0, 0, 0, 0};  // constant scaled coefficients; [6] = diag
   void* d = nullptr;          // kept diagonal for b scaling (float64 / float32)
-  float* tc[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // raw float32
+  // raw operator in float32 (keep_true): the directions, then the diagonal
+  // (tc[6] for the 7-point operator, tc[8] for the 9-point one)
+  float* tc[9] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   Tile tile;
   int check_every;
   int stages;                 // step-sweep pipeline depth (1 = direct loads)
@@ -83,6 +87,10 @@ struct Engine {
   int vec;         // cells per thread in the sweeps
   // scale raw coefficients (device, dtype raw_dt) into the handle
   int (*scale)(Handle* h, const void* const raw[7], s7_dtype raw_dt, cudaStream_t st, int* bad);
+  // the same for the 9-point operator: raw = xm xp ym yp xmym xpym xmyp xpyp
+  // diag, in row layout or (columns = 1) the paper's column layout
+  int (*scale9)(Handle* h, const void* const raw[9], s7_dtype raw_dt, int columns,
+                cudaStream_t st, int* bad);
   int (*apply)(Handle* h, const void* x, void* y, cudaStream_t st);
   int (*init)(Handle* h, const void* b, cudaStream_t st);
   // one kernel of a BiCGStab step: 0 = p update + s = A p + (r0,s);
@@ -133,6 +141,8 @@ int ensure_ws(Handle* h, int maxit);
 
 // Shape of the sweep grid for a handle (same for every sweep of the handle).
 void default_tile(int nx, int ny, int nz, int vec, int nsm, Tile* t);
+// The same for a 2D 9-point mesh: bx threads per row strip, zchunk rows.
+void default_tile9(int nx, int ny, int vec, int nsm, Tile* t);
 
 }  // namespace s7
 
