@@ -139,9 +139,10 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel, n_cells):
+def ncu_traffic(kernel, n_cells, table="kernels"):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, scaled
-    to a launch over n_cells; None if absent or taken on other kernel code."""
+    to a launch over n_cells; None if absent or taken on other kernel code.
+    `table`: "kernels" (3D 7-point) or "kernels_9pt" (2D 9-point)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
@@ -150,7 +151,7 @@ def ncu_traffic(kernel, n_cells):
         return None
     if d.get("source_hash") != kernel_source_hash():
         return None
-    k = d.get("kernels", {}).get(kernel)
+    k = d.get(table, {}).get(kernel)
     if not k:
         return None
     return k["dram_bytes_per_launch"] * n_cells / k["cells"]
@@ -501,7 +502,9 @@ def run_solve9(args):
             "gflops": FLOPS_PER_CELL_9PT * value / 1e9, "ms_per_iter": elapsed_ms / done,
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": kern[dom]["gbs"],
                          "peak": peak, "unit": "GB/s", "frac": kern[dom]["gbs"] / peak,
-                         "peak_kind": peak_kind, "traffic": None},
+                         "peak_kind": peak_kind,
+                         "traffic": ncu_traffic(dom, n, "kernels_9pt")
+                         if (args.storage == "f32" and args.variant == 0) else None},
             "kernels": kern, "gpu_launches": int(sum(c for _, c in prof.values())),
             "clocks": clocks,
             "context": {"final_rel_resid": float(res.hist[-1])}}))
