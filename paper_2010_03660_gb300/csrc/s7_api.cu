@@ -241,6 +241,10 @@ static void release(Handle* h) {
   dfree(h, &w.ref_r, n * 8);
   if (w.h_sc) cudaFreeHost(w.h_sc);
   w.h_sc = nullptr;
+  for (int k = 0; k < 2; ++k) {
+    if (w.snap[k]) cudaEventDestroy(w.snap[k]);
+    w.snap[k] = nullptr;
+  }
   w.ready = false;
   for (int d = 0; d < 8; ++d) dfree(h, &h->c[d], n * ts);
   dfree(h, &h->diag, n * ts);
@@ -600,7 +604,9 @@ int s7::ensure_ws(Handle* h, int maxit) {
     if ((rc = dmalloc(h, (void**)&w.parts, w.parts_n * 8))) return rc;
     if ((rc = dmalloc(h, (void**)&w.sc, sizeof(Scalars)))) return rc;
     CK(cudaMemset(w.sc, 0, sizeof(Scalars)));
-    if (!w.h_sc) CK(cudaMallocHost((void**)&w.h_sc, sizeof(Scalars)));
+    if (!w.h_sc) CK(cudaMallocHost((void**)&w.h_sc, 2 * sizeof(Scalars)));
+    for (int k = 0; k < 2; ++k)
+      if (!w.snap[k]) CK(cudaEventCreateWithFlags(&w.snap[k], cudaEventDisableTiming));
     w.ready = true;
   }
   if (maxit + 1 > w.hist_cap) {
@@ -772,6 +778,24 @@ static void prof_collect(Handle* h) {
   h->prof_ev_used = 0;
 }
 
+// Account the first m pending records (complete) and keep the rest pending.
+static void prof_take(Handle* h, int m) {
+  for (int i = 0; i < m; ++i) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, h->prof_ev[2 * i], h->prof_ev[2 * i + 1]) == cudaSuccess) {
+      h->prof_ms[h->prof_kind[i]] += ms;
+      h->prof_n[h->prof_kind[i]] += 1;
+    }
+  }
+  cudaGetLastError();
+  for (int i = m; i < h->prof_ev_used; ++i) {
+    std::swap(h->prof_ev[2 * (i - m)], h->prof_ev[2 * i]);
+    std::swap(h->prof_ev[2 * (i - m) + 1], h->prof_ev[2 * i + 1]);
+    h->prof_kind[i - m] = h->prof_kind[i];
+  }
+  h->prof_ev_used -= m;
+}
+
 static int prof_begin(Handle* h, int kind, cudaStream_t st) {
   if (!h->prof) return -1;
   if (h->prof_ev_used == h->prof_ev_cap) {
@@ -911,26 +935,50 @@ static int solve_core(Handle* h, const void* bdev, double tol, int maxit, SolveO
     if (rc) return fail(rc, "first pass launch failed");
   }
   if (!h->prof && (rc = capture_graph(h))) return rc;
+  // Launches of `per` steps run one ahead of the host's check of the device
+  // stop flag: while the host waits for the copy of the scalars after launch
+  // k, launch k+1 is already queued, so the device never idles on the host.
+  // Each launch is followed by a copy of the scalars into its own pinned
+  // mirror.  The launch queued after the stop is seen runs kernels that
+  // return at entry; its profiling records, if any, are dropped.
   const int per = std::max(1, h->check_every);
   const int max_launch = maxit / per + 3;
-  int launches = 0;
+  int mark[2] = {0, 0};  // profiling records issued up to each snapshot
+  auto snapshot = [&](int slot) -> int {
+    CK(cudaMemcpyAsync(hs + slot, w.sc, sizeof(Scalars), cudaMemcpyDeviceToHost, st));
+    CK(cudaEventRecord(w.snap[slot], st));
+    mark[slot] = h->prof_ev_used;
+    return S7_OK;
+  };
+  if ((rc = snapshot(0))) return rc;
+  int cur = 0, issued = 0;
   for (;;) {
-    CK(cudaMemcpyAsync(hs, w.sc, sizeof(Scalars), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    if (h->prof) prof_collect(h);
-    if (hs->done) break;
-    if (++launches > max_launch)
-      return fail(S7_ECUDA, "solve did not terminate after %d launches", launches - 1);
-    if (h->prof) {
-      for (int k = 0; k < per; ++k)
-        if ((rc = run_step(h, st))) return fail(rc, "step launch failed");
-    } else {
-      CK(cudaGraphLaunch(w.graph, st));
+    if (issued <= max_launch) {
+      if (h->prof) {
+        for (int k = 0; k < per; ++k)
+          if ((rc = run_step(h, st))) return fail(rc, "step launch failed");
+      } else {
+        CK(cudaGraphLaunch(w.graph, st));
+      }
+      ++issued;
+      if ((rc = snapshot(1 - cur))) return rc;
     }
+    CK(cudaEventSynchronize(w.snap[cur]));
+    if (h->prof) {
+      prof_take(h, mark[cur]);
+      mark[1 - cur] -= mark[cur];
+      mark[cur] = 0;
+    }
+    if (hs[cur].done) break;
+    if (issued > max_launch)
+      return fail(S7_ECUDA, "solve did not terminate after %d launches", issued);
+    cur = 1 - cur;
   }
-  so->iters = hs->iter;
-  so->status = hs->status;
-  so->bnorm = hs->bnorm;
+  CK(cudaStreamSynchronize(st));
+  if (h->prof) h->prof_ev_used = 0;
+  so->iters = hs[cur].iter;
+  so->status = hs[cur].status;
+  so->bnorm = hs[cur].bnorm;
   return S7_OK;
 }
 

@@ -27,7 +27,9 @@ struct Workspace {
   double* hist = nullptr;  // device residual history
   int hist_cap = 0;
   Scalars* sc = nullptr;   // device scalars
-  Scalars* h_sc = nullptr; // pinned host mirror
+  Scalars* h_sc = nullptr; // pinned host mirrors (two: the solve loop checks one
+                           // while the next launch's copy is in flight)
+  cudaEvent_t snap[2] = {nullptr, nullptr};  // completion of each mirror's copy
   void* r2 = nullptr;      // second r buffer (two-reduction variant)
   void* ref_x = nullptr;   // float64 iterate of the refined solver
   void* ref_b = nullptr;   // float64 right-hand side of the refined solver

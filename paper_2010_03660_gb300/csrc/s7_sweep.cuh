@@ -525,10 +525,12 @@ struct EpiResid {
     for (int k = 0; k < VEC; ++k) {
       A rhs = bv[k];
       A av = out[k];
+      // unit scales (no Jacobi scaling, or a raw residual) skip the
+      // division and multiplication: float64 division is costly here
       if (dinv) rhs = rhs / dv[k];
-      else rhs = rhs / dc;
+      else if (dc != A(1)) rhs = rhs / dc;
       if (dmul) av = av * dv[k];
-      else av = av * dmc;
+      else if (dmc != A(1)) av = av * dmc;
       const A rk = rhs - av;
       rv[k] = as_stored<T>(rk);
       // a solve's start residual enters the recurrence as stored; a reported
