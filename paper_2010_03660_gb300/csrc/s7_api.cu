@@ -317,14 +317,19 @@ extern "C" int stencil7_create(stencil7_t* out, int nx, int ny, int nz, const s7
   // 2-stage pipeline helps the p/s sweep, whose register version is limited
   // by occupancy, and not the q/y sweep.  16-bit storage (512^2 planes):
   // both sweeps are bound by the per-plane latency chain at half the bytes
-  // per cell, so both take a 3-stage pipeline.
-  const bool half = opts.storage == S7_BF16 || opts.storage == S7_F16;
-  h->stages = opts.stages > 0 ? std::min(opts.stages, 4) : (half ? 3 : 2);
-  h->pipe_kinds = opts.pipe_kinds > 0 ? (opts.pipe_kinds & 3) : (half ? 3 : 1);
+  // per cell, so both take a 3-stage pipeline.  The two-reduction variant's
+  // passes carry more streams per cell (r0 in the q/y pass; r, s, y, p and x
+  // in the fused pass), and both run fastest with 2 stages for every
+  // storage type (deeper stages cost occupancy).
   if (opts.variant < 0 || opts.variant > 1) {
     delete h;
     return fail(S7_EINVAL, "stencil7_create: variant must be 0 or 1");
   }
+  const bool half = opts.storage == S7_BF16 || opts.storage == S7_F16;
+  const int def_stages = opts.variant == 1 ? 2 : (half ? 3 : 2);
+  const int def_kinds = opts.variant == 1 ? 3 : (half ? 3 : 1);
+  h->stages = opts.stages > 0 ? std::min(opts.stages, 4) : def_stages;
+  h->pipe_kinds = opts.pipe_kinds > 0 ? (opts.pipe_kinds & 3) : def_kinds;
   h->variant = opts.variant;
   if (!eng->smem_ok(h)) {
     delete h;

@@ -429,8 +429,11 @@ struct EngineImpl {
 
   // The pipelined sweeps serve the common case: Jacobi-scaled per-cell
   // coefficients, rows of whole 16-byte vectors, at most 256 threads.
+  // Kinds 0, 3 (p/s sweeps) follow bit 0 of pipe_kinds, kinds 1, 2 (q/y
+  // sweeps) bit 1.
   static bool pipelined(const Handle* h, const Geom& g, int kind) {
-    return h->stencil == 7 && h->stages >= 2 && ((h->pipe_kinds >> kind) & 1) && h->jacobi &&
+    const int bit = (kind == 0 || kind == 3) ? 0 : 1;
+    return h->stencil == 7 && h->stages >= 2 && ((h->pipe_kinds >> bit) & 1) && h->jacobi &&
            !h->constant &&
            h->nx % VEC == 0 &&
            g.bx * g.by <= 256 &&
@@ -450,6 +453,10 @@ struct EngineImpl {
     a.sbuf[1] = (T*)w.s[1];
     a.y = (T*)w.y;
     a.parts = w.parts;
+    a.rbuf[0] = (T*)w.r;
+    a.rbuf[1] = (T*)w.r2;
+    a.x = w.x;
+    a.hist = w.hist;
     const size_t smem = step_smem_bytes<T, A, VEC>(g.bx, g.by, STAGES, KIND);
     void (*kern)(Geom, StepArgs<T>, Scalars*) = k_step<T, A, VEC, KIND, STAGES>;
     if (allow_smem((const void*)kern, smem, st)) return S7_ECUDA;
@@ -480,15 +487,10 @@ struct EngineImpl {
       set((const void*)k_sweep9_1<T, A, VEC, false, MergedPass<T, X, A>>, b9);
       return rc;
     }
-    for (int kind = 0; kind < 2; ++kind) {
+    for (int kind = 0; kind < 4; ++kind) {
       if (!pipelined(h, g, kind)) continue;
       const size_t b = step_smem_bytes<T, A, VEC>(g.bx, g.by, h->stages, kind);
-      if (h->stages == 4)
-        set(kind == 0 ? (const void*)k_step<T, A, VEC, 0, 4> : (const void*)k_step<T, A, VEC, 1, 4>, b);
-      else if (h->stages == 3)
-        set(kind == 0 ? (const void*)k_step<T, A, VEC, 0, 3> : (const void*)k_step<T, A, VEC, 1, 3>, b);
-      else
-        set(kind == 0 ? (const void*)k_step<T, A, VEC, 0, 2> : (const void*)k_step<T, A, VEC, 1, 2>, b);
+      set(step_fn(kind, h->stages), b);
     }
     const size_t gb = (size_t)3 * (g.by + 2) * (g.bx * VEC + 2 * VEC) * sizeof(A);
     set((const void*)k_sweep<T, A, VEC, true, SrcPUpdate<T, A>, EpiS<T, A>>, gb);
@@ -502,17 +504,31 @@ struct EngineImpl {
     return rc;
   }
 
+  static const void* step_fn(int kind, int stages) {
+    static const void* const fns[4][3] = {
+        {(const void*)k_step<T, A, VEC, 0, 2>, (const void*)k_step<T, A, VEC, 0, 3>,
+         (const void*)k_step<T, A, VEC, 0, 4>},
+        {(const void*)k_step<T, A, VEC, 1, 2>, (const void*)k_step<T, A, VEC, 1, 3>,
+         (const void*)k_step<T, A, VEC, 1, 4>},
+        {(const void*)k_step<T, A, VEC, 2, 2>, (const void*)k_step<T, A, VEC, 2, 3>,
+         (const void*)k_step<T, A, VEC, 2, 4>},
+        {(const void*)k_step<T, A, VEC, 3, 2>, (const void*)k_step<T, A, VEC, 3, 3>,
+         (const void*)k_step<T, A, VEC, 3, 4>}};
+    return fns[kind][std::min(std::max(stages, 2), 4) - 2];
+  }
+
+  template <int KIND>
+  static int launch_step_any(const Handle* h, const Geom& g, cudaStream_t st) {
+    return h->stages == 4 ? launch_step<KIND, 4>(h, g, st)
+         : h->stages == 3 ? launch_step<KIND, 3>(h, g, st) : launch_step<KIND, 2>(h, g, st);
+  }
+
   static int step_kernel(Handle* h, int which, cudaStream_t st) {
     const Geom g = make_geom(h, VEC);
     Workspace& w = h->ws;
     const bool vl = (h->nx % VEC == 0);
-    if (which < 2 && pipelined(h, g, which)) {
-      if (which == 0)
-        return h->stages == 4 ? launch_step<0, 4>(h, g, st)
-             : h->stages == 3 ? launch_step<0, 3>(h, g, st) : launch_step<0, 2>(h, g, st);
-      return h->stages == 4 ? launch_step<1, 4>(h, g, st)
-           : h->stages == 3 ? launch_step<1, 3>(h, g, st) : launch_step<1, 2>(h, g, st);
-    }
+    if (which < 2 && pipelined(h, g, which))
+      return which == 0 ? launch_step_any<0>(h, g, st) : launch_step_any<1>(h, g, st);
     if (which == 0) {
       SrcPUpdate<T, A> sa;
       sa.r = (const T*)w.r;
@@ -548,6 +564,8 @@ struct EngineImpl {
     const Geom g = make_geom(h, VEC);
     Workspace& w = h->ws;
     const bool vl = (h->nx % VEC == 0);
+    if (pipelined(h, g, which + 1))
+      return which == 1 ? launch_step_any<2>(h, g, st) : launch_step_any<3>(h, g, st);
     if (which == 1) {
       SrcQ2<T, A> sb;
       sb.rbuf[0] = (T*)w.r;

@@ -11,7 +11,15 @@
 // Stage k (for output plane z = z0 + k) holds: coef(z), r0_hat(z) and the
 // inputs at plane z+1 (rows y0-1 .. y0+by, each the aligned span
 // [x0-VEC, x0+bx*VEC+VEC), so the x halo cells come from the neighbouring
-// 16-byte vectors).  Cells outside the mesh are zero-filled by the copy.
+// 16-byte vectors), and for the fused pass of the two-reduction variant the
+// iterate x of the block's own cells at plane z+1.  Cells outside the mesh
+// are zero-filled by the copy.
+//
+// Kinds: 0 = p update + s = A p + (r0,s); 1 = q + y = A q + (q,y),(y,y);
+// two-reduction variant: 2 = q + y = A q + (q,y),(y,y),(r0,y); 3 = the fused
+// pass (x, r updates of step i, p_{i+1}, s_{i+1} = A p_{i+1}, (r0,s),
+// (r,r), (r0,r)).  Kinds 2 and 3 compute exactly what the register sweeps
+// with SrcQ2/EpiYMerged and MergedPass compute, in the same order.
 //
 // Barriers: one per plane.  At step k a thread waits for its own copies of
 // stage k, then __syncthreads() makes all of stage k and the vector plane z
@@ -57,7 +65,8 @@ template <int N> __device__ __forceinline__ void cp_async_wait() {
 
 // Pointers of one pipelined sweep.  KIND 0: p_i = r + beta (p_{i-1} - omega
 // s_{i-1}) formed on the fly, s_i = A p_i, (r0,s_i).  KIND 1: q = r - alpha s
-// formed on the fly, y = A q, (q,y), (y,y).
+// formed on the fly, y = A q, (q,y), (y,y).  Kinds 2 and 3 read r from rbuf
+// by step parity; kind 3 also updates x and writes the history.
 template <class T>
 struct StepArgs {
   const T* c[6];
@@ -67,16 +76,32 @@ struct StepArgs {
   T* sbuf[2];
   T* y;
   double* parts;
+  T* rbuf[2];
+  void* x;
+  double* hist;
+};
+
+// The iterate's type for storage type T (float64 for float64 storage).
+template <class T> struct IterOf { typedef float t; };
+template <> struct IterOf<double> { typedef double t; };
+
+// Staged arrays per kind: inputs with halo, r0_hat tile, x tile.
+template <int KIND> struct KindShape {
+  static constexpr int nin = KIND == 0 ? 3 : (KIND == 3 ? 4 : 2);
+  static constexpr bool rh = KIND != 1;
+  static constexpr bool x = KIND == 3;
 };
 
 template <class T, int VEC>
 struct StepLayout {
   int TW, W, rows;     // tile width (elements), padded row pitch, rows incl. halo
   int coef_sz, rh_sz, in_sz, stage_sz;  // in elements of T
+  int x_off, x_bytes;  // iterate tile: byte offset in the stage, bytes
 };
 
 template <class T, int VEC>
-__host__ __device__ inline StepLayout<T, VEC> step_layout(int bx, int by, int nin, bool rh) {
+__host__ __device__ inline StepLayout<T, VEC> step_layout(int bx, int by, int nin, bool rh,
+                                                        int x_size = 0) {
   StepLayout<T, VEC> L;
   L.TW = bx * VEC;
   L.W = L.TW + 2 * VEC;
@@ -85,6 +110,8 @@ __host__ __device__ inline StepLayout<T, VEC> step_layout(int bx, int by, int ni
   L.rh_sz = rh ? by * L.TW : 0;
   L.in_sz = nin * L.rows * L.W;
   L.stage_sz = L.coef_sz + L.rh_sz + L.in_sz;
+  L.x_off = (int)(((size_t)L.stage_sz * sizeof(T) + 15) / 16 * 16);
+  L.x_bytes = x_size * by * L.TW;
   return L;
 }
 
@@ -92,12 +119,24 @@ __host__ __device__ inline StepLayout<T, VEC> step_layout(int bx, int by, int ni
 // stages start on a 16-byte boundary (vector shared-memory accesses).
 template <class T, int VEC>
 __host__ __device__ inline size_t stage_stride_bytes(const StepLayout<T, VEC>& L) {
-  return ((size_t)L.stage_sz * sizeof(T) + 15) / 16 * 16;
+  return ((size_t)L.x_off + L.x_bytes + 15) / 16 * 16;
+}
+
+template <class T, int VEC, int KIND>
+__host__ __device__ inline StepLayout<T, VEC> kind_layout(int bx, int by) {
+  return step_layout<T, VEC>(bx, by, KindShape<KIND>::nin, KindShape<KIND>::rh,
+                             KindShape<KIND>::x ? (int)sizeof(typename IterOf<T>::t) : 0);
 }
 
 template <class T, class A, int VEC>
 __host__ __device__ inline size_t step_smem_bytes(int bx, int by, int stages, int kind) {
-  const StepLayout<T, VEC> L = step_layout<T, VEC>(bx, by, kind == 0 ? 3 : 2, kind == 0);
+  StepLayout<T, VEC> L;
+  switch (kind) {
+    case 0: L = kind_layout<T, VEC, 0>(bx, by); break;
+    case 1: L = kind_layout<T, VEC, 1>(bx, by); break;
+    case 2: L = kind_layout<T, VEC, 2>(bx, by); break;
+    default: L = kind_layout<T, VEC, 3>(bx, by); break;
+  }
   const size_t ring = (size_t)3 * L.rows * L.W * sizeof(A);
   return (size_t)stages * stage_stride_bytes(L) + ring;
 }
@@ -108,19 +147,25 @@ __global__ void __launch_bounds__(256) k_step(Geom g, StepArgs<T> a, Scalars* sc
   __shared__ double red[32 * 4];
   if (*((volatile int*)&sc->done)) return;
 
+  typedef typename IterOf<T>::t X;
   const int it = sc->iter;
   const bool odd = (it & 1) != 0;
   const bool first = (KIND == 0) && it == 0;
   const A beta = (A)sc->beta, omega = (A)sc->omega, alpha = (A)sc->alpha;
   // inputs of the on-the-fly vector
-  const T* in0 = a.r;
+  const T* in0 = KIND >= 2 ? (odd ? a.rbuf[1] : a.rbuf[0]) : a.r;
   const T* in1 = (KIND == 0) ? (odd ? a.pbuf[0] : a.pbuf[1]) : (odd ? a.sbuf[1] : a.sbuf[0]);
-  const T* in2 = (KIND == 0) ? (odd ? a.sbuf[0] : a.sbuf[1]) : nullptr;
-  const int nin = (KIND == 0) ? (first ? 1 : 3) : 2;
-  T* p_out = odd ? a.pbuf[1] : a.pbuf[0];
-  T* out = (KIND == 0) ? (odd ? a.sbuf[1] : a.sbuf[0]) : a.y;
+  const T* in2 = (KIND == 0) ? (odd ? a.sbuf[0] : a.sbuf[1]) : (KIND == 3 ? a.y : nullptr);
+  const T* in3 = (KIND == 3) ? (odd ? a.pbuf[1] : a.pbuf[0]) : nullptr;
+  const int nin = (KIND == 0) ? (first ? 1 : 3) : KindShape<KIND>::nin;
+  // kind 0 writes p_i; kind 3 writes p_{i+1}, r_{i+1} (the other parity)
+  T* p_out = (KIND == 3) ? (odd ? a.pbuf[0] : a.pbuf[1]) : (odd ? a.pbuf[1] : a.pbuf[0]);
+  T* r_out = odd ? a.rbuf[0] : a.rbuf[1];
+  X* xg = reinterpret_cast<X*>(a.x);
+  T* out = (KIND == 0) ? (odd ? a.sbuf[1] : a.sbuf[0])
+         : (KIND == 3) ? (odd ? a.sbuf[0] : a.sbuf[1]) : a.y;
 
-  const StepLayout<T, VEC> L = step_layout<T, VEC>(g.bx, g.by, KIND == 0 ? 3 : 2, KIND == 0);
+  const StepLayout<T, VEC> L = kind_layout<T, VEC, KIND>(g.bx, g.by);
   const size_t sstride = stage_stride_bytes(L);
   auto stage_buf = [&](int k) { return reinterpret_cast<T*>(s7_smem + (size_t)k * sstride); };
   A* ring = reinterpret_cast<A*>(s7_smem + (size_t)STAGES * sstride);
@@ -161,13 +206,17 @@ __global__ void __launch_bounds__(256) k_step(Geom g, StepArgs<T> a, Scalars* sc
     const long long gi = own ? (long long)z * g.plane + row : 0;
 #pragma unroll
     for (int d = 0; d < 6; ++d) cp_async<VB>(buf + d * g.by * L.TW + sc_own, a.c[d] + gi, own ? VB : 0);
-    if (KIND == 0) cp_async<VB>(buf + L.coef_sz + sc_own, a.rh + gi, own ? VB : 0);
+    if (KindShape<KIND>::rh) cp_async<VB>(buf + L.coef_sz + sc_own, a.rh + gi, own ? VB : 0);
     const int zi = z + 1;
     if (zi >= g.nz) return;
     const long long gb = (long long)zi * g.plane + row;
+    if (KindShape<KIND>::x) {
+      X* xb = reinterpret_cast<X*>(reinterpret_cast<unsigned char*>(buf) + L.x_off) + sc_own;
+      cp_async<VEC * (int)sizeof(X)>(xb, xg + (own ? gb : 0), own ? VEC * (int)sizeof(X) : 0);
+    }
     T* ib = buf + L.coef_sz + L.rh_sz + so;
     for (int sidx = 0; sidx < nin; ++sidx) {
-      const T* base = sidx == 0 ? in0 : (sidx == 1 ? in1 : in2);
+      const T* base = sidx == 0 ? in0 : (sidx == 1 ? in1 : (sidx == 2 ? in2 : in3));
       T* d = ib + sidx * PL;
       cp_async<VB>(d, base + (own ? gb : 0), own ? VB : 0);
       if (ty == 0) cp_async<VB>(d - L.W, base + (v_top ? gb - g.nx : 0), v_top ? VB : 0);
@@ -177,21 +226,42 @@ __global__ void __launch_bounds__(256) k_step(Geom g, StepArgs<T> a, Scalars* sc
     }
   };
 
+  // p_{i+1} of the fused pass from r_i, s_i, y_i, p_i (as MergedPass forms it)
+  auto form_merged = [&](A rv, A sv, A yv, A pv, A& q, A& rn) -> A {
+    q = q_of(rv, sv, alpha);
+    rn = as_stored<T>(fma(-omega, yv, q));
+    return as_stored<T>(fma(beta, fma(-omega, sv, pv), rn));
+  };
   // value of the on-the-fly vector from staged inputs (index e in a plane)
   auto form = [&](const T* inb, int e) -> A {
     const A rv = to_acc<A>(inb[e]);
-    if (KIND == 1) return q_of(rv, to_acc<A>(inb[PL + e]), alpha);
+    if (KIND == 1 || KIND == 2) return q_of(rv, to_acc<A>(inb[PL + e]), alpha);
+    if (KIND == 3) {
+      A q, rn;
+      return form_merged(rv, to_acc<A>(inb[PL + e]), to_acc<A>(inb[2 * PL + e]),
+                         to_acc<A>(inb[3 * PL + e]), q, rn);
+    }
     if (first) return rv;
     return as_stored<T>(fma(beta, fma(-omega, to_acc<A>(inb[2 * PL + e]), to_acc<A>(inb[PL + e])), rv));
   };
   // the same for a run of VEC cells starting at e (one vector load per input)
   auto form_run = [&](const T* inb, int e, A (&v)[VEC]) {
     ldv<T, VEC>(inb + e, v);
-    if (KIND == 1) {
+    if (KIND == 1 || KIND == 2) {
       A sv[VEC];
       ldv<T, VEC>(inb + PL + e, sv);
 #pragma unroll
       for (int j = 0; j < VEC; ++j) v[j] = q_of(v[j], sv[j], alpha);
+    } else if (KIND == 3) {
+      A sv[VEC], yv[VEC], pv[VEC];
+      ldv<T, VEC>(inb + PL + e, sv);
+      ldv<T, VEC>(inb + 2 * PL + e, yv);
+      ldv<T, VEC>(inb + 3 * PL + e, pv);
+#pragma unroll
+      for (int j = 0; j < VEC; ++j) {
+        A q, rn;
+        v[j] = form_merged(v[j], sv[j], yv[j], pv[j], q, rn);
+      }
     } else if (!first) {
       A pv[VEC], sv[VEC];
       ldv<T, VEC>(inb + PL + e, pv);
@@ -204,9 +274,14 @@ __global__ void __launch_bounds__(256) k_step(Geom g, StepArgs<T> a, Scalars* sc
   // prologue: the vector at z0-1 (own) and z0 (own + ring) from global memory,
   // then the first STAGES-1 stages in flight
   A vm[VEC], vc[VEC], vp[VEC];
+  A rn_c[VEC], rn_p[VEC];   // kind 3: r_{i+1} of own cells at planes z, z+1
+  zero(rn_c);
+  zero(rn_p);
   {
     SrcPUpdate<T, A> sa;
     SrcQ<T, A> sb;
+    SrcQ2<T, A> sq;
+    MergedPass<T, X, A> mp;
     if (KIND == 0) {
       sa.r = a.r;
       sa.pbuf[0] = a.pbuf[0];
@@ -214,24 +289,54 @@ __global__ void __launch_bounds__(256) k_step(Geom g, StepArgs<T> a, Scalars* sc
       sa.sbuf[0] = a.sbuf[0];
       sa.sbuf[1] = a.sbuf[1];
       sa.setup(sc);
-    } else {
+    } else if (KIND == 1) {
       sb.r = a.r;
       sb.sbuf[0] = a.sbuf[0];
       sb.sbuf[1] = a.sbuf[1];
       sb.setup(sc);
+    } else if (KIND == 2) {
+      sq.rbuf[0] = a.rbuf[0];
+      sq.rbuf[1] = a.rbuf[1];
+      sq.sbuf[0] = a.sbuf[0];
+      sq.sbuf[1] = a.sbuf[1];
+      sq.setup(sc);
+    } else {
+      for (int k = 0; k < 2; ++k) {
+        mp.rbuf[k] = a.rbuf[k];
+        mp.pbuf[k] = a.pbuf[k];
+        mp.sbuf[k] = a.sbuf[k];
+      }
+      mp.y = a.y;
+      mp.rh = a.rh;
+      mp.x = xg;
+      mp.parts = a.parts;
+      mp.hist = a.hist;
+      mp.setup(sc);
     }
     auto prod = [&](long long i, int nv, A (&v)[VEC], bool write) {
       if (KIND == 0) sa.template produce<VEC, true>(i, nv, v, write);
-      else sb.template produce<VEC, true>(i, nv, v, write);
+      else if (KIND == 1) sb.template produce<VEC, true>(i, nv, v, write);
+      else if (KIND == 2) sq.template produce<VEC, true>(i, nv, v, write);
+      else mp.template produce<VEC, true>(i, nv, v, write);
     };
-    auto prod1 = [&](long long i) -> A { return KIND == 0 ? sa.produce1(i) : sb.produce1(i); };
+    auto prod1 = [&](long long i) -> A {
+      return KIND == 0 ? sa.produce1(i)
+           : KIND == 1 ? sb.produce1(i) : KIND == 2 ? sq.produce1(i) : mp.produce1(i);
+    };
     if (z0 > 0 && own) prod((long long)(z0 - 1) * g.plane + row, VEC, vm, false);
     else zero(vm);
     A* rb = ring;
     if (has_cell) {
       const long long base = (long long)z0 * g.plane + row;
-      if (own) prod(base, VEC, vc, true);
-      else zero(vc);
+      if (own) {
+        prod(base, VEC, vc, true);
+        // the fused pass keeps r_{i+1} of its own cells for the epilogue
+        if (KIND == 3)
+#pragma unroll
+          for (int j = 0; j < VEC; ++j) rn_c[j] = mp.ring0[j];
+      } else {
+        zero(vc);
+      }
       sm_store<A, VEC>(rb + so, vc);
       if (ty == 0) {
         A h[VEC];
@@ -258,7 +363,8 @@ __global__ void __launch_bounds__(256) k_step(Geom g, StepArgs<T> a, Scalars* sc
     cp_async_commit();
   }
 
-  DotAcc<A, 2> acc;
+  DotAcc<A, (KIND >= 2 ? 3 : 2)> acc;
+  constexpr int I2 = KIND >= 2 ? 2 : 1;   // third sum (kinds 2, 3 only)
   acc.init();
   for (int k = 0; k < nsteps; ++k) {
     const int z = z0 + k;
@@ -277,8 +383,29 @@ __global__ void __launch_bounds__(256) k_step(Geom g, StepArgs<T> a, Scalars* sc
     if (z + 1 < g.nz) {
       const bool ring_needed = z + 1 < z1;
       if (has_cell) {
-        if (own) form_run(inb, so, vp);
-        else zero(vp);
+        if (KIND == 3 && own && ring_needed) {
+          // own cells of plane z+1: x and r updates of step i, p_{i+1}
+          A rv[VEC], sv[VEC], yv[VEC], pv[VEC], xv[VEC], q[VEC];
+          ldv<T, VEC>(inb + so, rv);
+          ldv<T, VEC>(inb + PL + so, sv);
+          ldv<T, VEC>(inb + 2 * PL + so, yv);
+          ldv<T, VEC>(inb + 3 * PL + so, pv);
+          ldv<X, VEC>(reinterpret_cast<const X*>(reinterpret_cast<const unsigned char*>(st) +
+                                                 L.x_off) + sc_own, xv);
+#pragma unroll
+          for (int j = 0; j < VEC; ++j) {
+            vp[j] = form_merged(rv[j], sv[j], yv[j], pv[j], q[j], rn_p[j]);
+            xv[j] = fma(omega, q[j], fma(alpha, pv[j], xv[j]));
+          }
+          const long long gz = (long long)(z + 1) * g.plane + row;
+          store_run<X, VEC, true, true>(xg + gz, VEC, xv);
+          store_run<T, VEC, true, true>(r_out + gz, VEC, rn_p);
+          store_run<T, VEC, true, true>(p_out + gz, VEC, vp);
+        } else if (own) {
+          form_run(inb, so, vp);
+        } else {
+          zero(vp);
+        }
         if (ring_needed) {
           sm_store<A, VEC>(nb + so, vp);
           if (KIND == 0 && own) store_run<T, VEC, true, true>(p_out + (long long)(z + 1) * g.plane + row, VEC, vp);
@@ -329,11 +456,29 @@ __global__ void __launch_bounds__(256) k_step(Geom g, StepArgs<T> a, Scalars* sc
         ldv<T, VEC>(st + L.coef_sz + sc_own, hv);
 #pragma unroll
         for (int j = 0; j < VEC; ++j) acc.part[0] = fma(hv[j], o[j], acc.part[0]);
-      } else {
+      } else if (KIND == 1) {
 #pragma unroll
         for (int j = 0; j < VEC; ++j) {
           acc.part[0] = fma(vc[j], o[j], acc.part[0]);
           acc.part[1] = fma(o[j], o[j], acc.part[1]);
+        }
+      } else if (KIND == 2) {
+        A hv[VEC];
+        ldv<T, VEC>(st + L.coef_sz + sc_own, hv);
+#pragma unroll
+        for (int j = 0; j < VEC; ++j) {
+          acc.part[0] = fma(vc[j], o[j], acc.part[0]);
+          acc.part[1] = fma(o[j], o[j], acc.part[1]);
+          acc.part[I2] = fma(hv[j], o[j], acc.part[I2]);
+        }
+      } else {
+        A hv[VEC];
+        ldv<T, VEC>(st + L.coef_sz + sc_own, hv);
+#pragma unroll
+        for (int j = 0; j < VEC; ++j) {
+          acc.part[0] = fma(hv[j], o[j], acc.part[0]);
+          acc.part[1] = fma(rn_c[j], rn_c[j], acc.part[1]);
+          acc.part[I2] = fma(hv[j], rn_c[j], acc.part[I2]);
         }
       }
     }
@@ -342,12 +487,21 @@ __global__ void __launch_bounds__(256) k_step(Geom g, StepArgs<T> a, Scalars* sc
     for (int j = 0; j < VEC; ++j) {
       vm[j] = vc[j];
       vc[j] = vp[j];
+      if (KIND == 3) rn_c[j] = rn_p[j];
     }
   }
   cp_async_wait<0>();
   acc.fold();
   const int nb_total = s7_nblocks(g);
-  if (KIND == 0) {
+  if (KIND >= 2) {
+    double v[3] = {acc.tot[0], acc.tot[1], acc.tot[I2]}, tot[3];
+    block_sum<3>(v, red);
+    if (grid_combine<3>(a.parts, &sc->counter[KIND == 2 ? CNT_B : CNT_C], nb_total, bid, v, tot,
+                        red) && t == 0) {
+      if (KIND == 2) merged_q_finish(sc, tot[0], tot[1], tot[2]);
+      else merged_pass_finish(sc, a.hist, tot[0], tot[1], tot[2]);
+    }
+  } else if (KIND == 0) {
     double v[1] = {acc.tot[0]}, tot[1];
     block_sum<1>(v, red);
     if (grid_combine<1>(a.parts, &sc->counter[CNT_A], nb_total, bid, v, tot, red) && t == 0) {

@@ -615,6 +615,58 @@ struct SrcQ2 {
   }
 };
 
+// Scalars after the q/y pass of the two-reduction variant: omega_i, and
+// beta_i from the recurrence (r0, r_{i+1}) = (r0, r_i) - alpha (r0, s_i) -
+// omega (r0, y_i); sigma = (r0, s_i) is in res[3].  Last block, thread 0.
+__device__ inline void merged_q_finish(Scalars* sc, double qy, double yy, double ry) {
+  if (yy == 0.0) {
+    sc->special = 1;
+    sc->omega = 0.0;
+    sc->beta = 0.0;
+    sc->rho_next = 0.0;
+    return;
+  }
+  const double om = qy / yy;
+  if (om == 0.0 || !isfinite(om)) {
+    sc->status = 3;
+    sc->done = 1;
+    return;
+  }
+  sc->omega = om;
+  const double rn = sc->rho - sc->alpha * sc->res[3] - om * ry;
+  sc->rho_next = rn;
+  sc->beta = (sc->alpha / om) * (rn / sc->rho);
+}
+
+// Scalars after the fused pass: history, stopping test, breakdown on the
+// directly reduced (r0, r_{i+1}), which becomes rho for alpha_{i+1}.
+__device__ inline void merged_pass_finish(Scalars* sc, double* hist, double sigma, double rr,
+                                          double rho_direct) {
+  const int it = sc->iter + 1;
+  const double h = sqrt(rr) / sc->bnorm;
+  if (hist) hist[it] = h;
+  sc->iter = it;
+  sc->res[2] = h;
+  if (sc->special) {
+    sc->status = (h <= sc->tol) ? 0 : 3;
+    sc->done = 1;
+  } else if (h <= sc->tol) {
+    sc->status = 0;
+    sc->done = 1;
+  } else if (rho_direct == 0.0 || !isfinite(rho_direct) || sigma == 0.0 || !isfinite(sigma)) {
+    sc->status = 3;
+    sc->done = 1;
+  } else {
+    sc->rho = rho_direct;
+    sc->alpha = rho_direct / sigma;
+    sc->res[3] = sigma;
+    if (it >= sc->maxit) {
+      sc->status = 4;
+      sc->done = 1;
+    }
+  }
+}
+
 // y_i = A q_i stored; (q,y), (y,y), (r0,y) reduced; omega_i, rho_{i+1}, beta_i.
 template <class T, class A>
 struct EpiYMerged {
@@ -651,27 +703,8 @@ struct EpiYMerged {
     acc.fold();
     double v[3] = {acc.tot[0], acc.tot[1], acc.tot[2]}, tot[3];
     block_sum<3>(v, red);
-    if (grid_combine<3>(parts, &sc->counter[CNT_B], nblocks, bid, v, tot, red) && threadIdx.x == 0) {
-      const double qy = tot[0], yy = tot[1], ry = tot[2];
-      if (yy == 0.0) {
-        sc->special = 1;
-        sc->omega = 0.0;
-        sc->beta = 0.0;
-        sc->rho_next = 0.0;
-      } else {
-        const double om = qy / yy;
-        if (om == 0.0 || !isfinite(om)) {
-          sc->status = 3;
-          sc->done = 1;
-        } else {
-          sc->omega = om;
-          // (r0, r_{i+1}) = (r0, r_i) - alpha (r0, s_i) - omega (r0, y_i)
-          const double rn = sc->rho - sc->alpha * sc->res[3] - om * ry;
-          sc->rho_next = rn;
-          sc->beta = (sc->alpha / om) * (rn / sc->rho);
-        }
-      }
-    }
+    if (grid_combine<3>(parts, &sc->counter[CNT_B], nblocks, bid, v, tot, red) && threadIdx.x == 0)
+      merged_q_finish(sc, tot[0], tot[1], tot[2]);
   }
 };
 
@@ -784,32 +817,8 @@ struct MergedPass {
     acc.fold();
     double v[3] = {acc.tot[0], acc.tot[1], acc.tot[2]}, tot[3];
     block_sum<3>(v, red);
-    if (grid_combine<3>(parts, &sc->counter[CNT_C], nblocks, bid, v, tot, red) && threadIdx.x == 0) {
-      const double sigma = tot[0], rr = tot[1], rho_direct = tot[2];
-      const int it = sc->iter + 1;
-      const double h = sqrt(rr) / sc->bnorm;
-      if (hist) hist[it] = h;
-      sc->iter = it;
-      sc->res[2] = h;
-      if (sc->special) {
-        sc->status = (h <= sc->tol) ? 0 : 3;
-        sc->done = 1;
-      } else if (h <= sc->tol) {
-        sc->status = 0;
-        sc->done = 1;
-      } else if (rho_direct == 0.0 || !isfinite(rho_direct) || sigma == 0.0 || !isfinite(sigma)) {
-        sc->status = 3;
-        sc->done = 1;
-      } else {
-        sc->rho = rho_direct;
-        sc->alpha = rho_direct / sigma;
-        sc->res[3] = sigma;
-        if (it >= sc->maxit) {
-          sc->status = 4;
-          sc->done = 1;
-        }
-      }
-    }
+    if (grid_combine<3>(parts, &sc->counter[CNT_C], nblocks, bid, v, tot, red) && threadIdx.x == 0)
+      merged_pass_finish(sc, hist, tot[0], tot[1], tot[2]);
   }
 };
 

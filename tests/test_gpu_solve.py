@@ -180,6 +180,29 @@ def test_pipeline_depth_does_not_change_results(s7, shape):
         assert np.array_equal(o.x.cpu().numpy(), outs[0].x.cpu().numpy())
 
 
+@pytest.mark.parametrize("storage", ["f32", "f64", "bf16", "f16"])
+@pytest.mark.parametrize("shape", [(64, 48, 40), (40, 31, 70), (8, 3, 5)])
+def test_pipeline_depth_two_reduction_variant(s7, storage, shape):
+    # the pipelined q/y and fused passes (kinds 2 and 3) against the
+    # direct-load sweeps with the same policies and tile: bit for bit.  (A
+    # different tile regroups the float64 block sums of the sweeps; in this
+    # variant (r0, r) is one of them, and its partials need not sum exactly.)
+    nx, ny, nz = shape
+    raw = np.float64 if storage == "f64" else np.float32
+    p = synth.varcoef(nx, ny, nz, seed=46, dtype=raw)
+    tol = 1e-6 if storage in ("f32", "f64") else 1e-3
+    outs = []
+    for stages, by, kinds in ((1, 0, 0), (2, 0, 3), (3, 0, 1), (2, 0, 2), (4, 0, 3), (3, 0, 3)):
+        with s7.stencil7_create(nx, ny, nz, gu.coef_on_device(p), storage=storage, variant=1,
+                                stages=stages, by=by, pipe_kinds=kinds) as op:
+            outs.append(s7.bicgstab_solve(op, gu.to_dev(p.b), tol=tol, maxit=300))
+    assert outs[0].status == 0
+    for o in outs[1:]:
+        assert o.iters == outs[0].iters and o.status == outs[0].status
+        assert np.array_equal(o.hist, outs[0].hist)
+        assert np.array_equal(o.x.cpu().numpy(), outs[0].x.cpu().numpy())
+
+
 @pytest.mark.parametrize("storage", ["f64", "bf16", "f16"])
 def test_pipeline_depth_other_storage(s7, storage):
     nx, ny, nz = 48, 20, 30
