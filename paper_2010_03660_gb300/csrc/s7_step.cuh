@@ -216,7 +216,8 @@ __global__ void __launch_bounds__(256) k_step(Geom g, StepArgs<T> a, Scalars* sc
     }
     T* ib = buf + L.coef_sz + L.rh_sz + so;
     for (int sidx = 0; sidx < nin; ++sidx) {
-      const T* base = sidx == 0 ? in0 : (sidx == 1 ? in1 : (sidx == 2 ? in2 : in3));
+      const T* base =
+          sidx == 0 ? in0 : (sidx == 1 ? in1 : ((KIND == 3 && sidx == 3) ? in3 : in2));
       T* d = ib + sidx * PL;
       cp_async<VB>(d, base + (own ? gb : 0), own ? VB : 0);
       if (ty == 0) cp_async<VB>(d - L.W, base + (v_top ? gb - g.nx : 0), v_top ? VB : 0);
