@@ -113,6 +113,8 @@ def parse():
     ap.add_argument("--zchunk", type=int, default=0, help="z planes per block (0 = tuned)")
     ap.add_argument("--stages", type=int, default=0,
                     help="cp.async pipeline depth of the step sweeps (0 = tuned, 1 = none)")
+    ap.add_argument("--step-cells", type=int, default=0,
+                    help="cells per thread in the pipelined sweeps (0 = tuned; 8 for 16-bit)")
     ap.add_argument("--pipe-kinds", type=int, default=0,
                     help="sweeps using the pipeline: bit 0 p/s sweep, bit 1 q/y sweep (0 = tuned)")
     ap.add_argument("--ref-sample-nz", type=int, default=8)
@@ -316,7 +318,7 @@ def run_ours(args):
     coef_d = {k: torch.from_numpy(v).to(dev) for k, v in prob.coef.items()}
     op = s7.stencil7_create(nx, ny, nz, coef_d, storage=args.storage, bx=args.bx, by=args.by,
                             zchunk=args.zchunk, variant=args.variant, stages=args.stages,
-                            pipe_kinds=args.pipe_kinds)
+                            pipe_kinds=args.pipe_kinds, step_cells=args.step_cells)
     del coef_d
     torch.cuda.empty_cache()
     b = torch.from_numpy(prob.b).to(dev)

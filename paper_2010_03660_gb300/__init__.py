@@ -77,7 +77,7 @@ class s7_opts(C.Structure):
     _fields_ = [("storage", C.c_int), ("no_jacobi", C.c_int), ("keep_true", C.c_int),
                 ("bx", C.c_int), ("by", C.c_int), ("zchunk", C.c_int),
                 ("check_every", C.c_int), ("stages", C.c_int), ("pipe_kinds", C.c_int),
-                ("variant", C.c_int)]
+                ("variant", C.c_int), ("step_cells", C.c_int)]
 
 
 class s7_batch_opts(C.Structure):
@@ -269,7 +269,7 @@ class Operator:
 
 def stencil7_create(nx, ny, nz, coef, storage="f32", jacobi=True, keep_true=False,
                     bx=0, by=0, zchunk=0, check_every=0, constant=None, stages=0,
-                    pipe_kinds=0, variant=0):
+                    pipe_kinds=0, variant=0, step_cells=0):
     """Create an operator from raw coefficients.
 
     ``coef`` maps ``diag, xm, xp, ym, yp, zm, zp`` to arrays/tensors of
@@ -302,7 +302,7 @@ def stencil7_create(nx, ny, nz, coef, storage="f32", jacobi=True, keep_true=Fals
                    ptrs["zm"], ptrs["zp"], raw_dt, 1 if constant else 0)
     st = _STORAGE[storage] if isinstance(storage, str) else int(storage)
     op = s7_opts(st, 0 if jacobi else 1, 1 if keep_true else 0, bx, by, zchunk, check_every,
-                 stages, pipe_kinds, variant)
+                 stages, pipe_kinds, variant, step_cells)
     h = C.c_void_p()
     _check(lib().stencil7_create(C.byref(h), nx, ny, nz, C.byref(cs), C.byref(op)))
     del keep

@@ -316,20 +316,28 @@ extern "C" int stencil7_create(stencil7_t* out, int nx, int ny, int nz, const s7
   // Defaults measured on GB300.  float32/float64 (600x595 planes): a
   // 2-stage pipeline helps the p/s sweep, whose register version is limited
   // by occupancy, and not the q/y sweep.  16-bit storage (512^2 planes):
-  // both sweeps are bound by the per-plane latency chain at half the bytes
-  // per cell, so both take a 3-stage pipeline.  The two-reduction variant's
-  // passes carry more streams per cell (r0 in the q/y pass; r, s, y, p and x
-  // in the fused pass), and both run fastest with 2 stages for every
-  // storage type (deeper stages cost occupancy).
+  // both sweeps are bound by instruction issue at half the bytes per cell;
+  // 8 cells (one 16-byte copy per array) per thread halve the per-cell
+  // overhead, and both sweeps take a 2-stage pipeline (1.57 vs 1.84 ms per
+  // step at 4 cells and 3 stages).  The two-reduction variant's passes
+  // carry more streams per cell (r0 in the q/y pass; r, s, y, p and x in the
+  // fused pass), and both run fastest with 2 stages for every storage type
+  // (deeper stages cost occupancy).
   if (opts.variant < 0 || opts.variant > 1) {
     delete h;
     return fail(S7_EINVAL, "stencil7_create: variant must be 0 or 1");
   }
   const bool half = opts.storage == S7_BF16 || opts.storage == S7_F16;
-  const int def_stages = opts.variant == 1 ? 2 : (half ? 3 : 2);
-  const int def_kinds = opts.variant == 1 ? 3 : (half ? 3 : 1);
+  const int def_stages = 2;
+  const int def_kinds = (opts.variant == 1 || half) ? 3 : 1;
   h->stages = opts.stages > 0 ? std::min(opts.stages, 4) : def_stages;
   h->pipe_kinds = opts.pipe_kinds > 0 ? (opts.pipe_kinds & 3) : def_kinds;
+  if (opts.step_cells != 0 && opts.step_cells != eng->vec && !(half && opts.step_cells == 8)) {
+    delete h;
+    return fail(S7_EINVAL, "stencil7_create: step_cells must be 0, %d%s", eng->vec,
+                half ? " or 8" : "");
+  }
+  h->step_vec = opts.step_cells > 0 ? opts.step_cells : (half ? 8 : eng->vec);
   h->variant = opts.variant;
   if (!eng->smem_ok(h)) {
     delete h;
@@ -499,6 +507,7 @@ extern "C" int stencil9_create(stencil7_t* out, int nx, int ny, const s9_coeffs*
   }
   h->stages = 1;        // the 9-point sweeps load directly
   h->pipe_kinds = 0;
+  h->step_vec = eng->vec;
   h->variant = opts.variant;
   if (!eng->smem_ok(h)) {
     delete h;

@@ -288,6 +288,9 @@ struct EngineImpl {
   // keeps 4 cells (8-byte vectors) so per-thread state, and with it
   // occupancy, matches the float32 kernels
   static constexpr int VEC = sizeof(T) >= 4 ? 16 / (int)sizeof(T) : 4;
+  // the other width the pipelined sweeps can take: 8 cells (16 bytes) of
+  // 16-bit storage per thread, which halves their per-cell overhead
+  static constexpr int VW = sizeof(T) == 2 ? 8 : VEC;
 
   template <class AA>
   static CoefView<T, AA> stored(const Handle* h) {
@@ -431,16 +434,26 @@ struct EngineImpl {
   // coefficients, rows of whole 16-byte vectors, at most 256 threads.
   // Kinds 0, 3 (p/s sweeps) follow bit 0 of pipe_kinds, kinds 1, 2 (q/y
   // sweeps) bit 1.
+  template <int V = VEC>
   static bool pipelined(const Handle* h, const Geom& g, int kind) {
     const int bit = (kind == 0 || kind == 3) ? 0 : 1;
     return h->stencil == 7 && h->stages >= 2 && ((h->pipe_kinds >> bit) & 1) && h->jacobi &&
            !h->constant &&
-           h->nx % VEC == 0 &&
+           h->nx % V == 0 &&
            g.bx * g.by <= 256 &&
-           step_smem_bytes<T, A, VEC>(g.bx, g.by, h->stages, kind) <= 200 * 1024;
+           step_smem_bytes<T, A, V>(g.bx, g.by, h->stages, kind) <= 200 * 1024;
   }
 
-  template <int KIND, int STAGES>
+  // Geometry of the pipelined sweeps at V cells per thread: the tile keeps
+  // its width in cells (fewer threads across it when V > VEC).
+  static Geom step_geom(const Handle* h, int v) {
+    if (v == VEC) return make_geom(h, VEC);
+    Handle t = *h;
+    t.tile.bx = std::max(1, h->tile.bx * VEC / v);
+    return make_geom(&t, v);
+  }
+
+  template <int KIND, int STAGES, int V = VEC>
   static int launch_step(const Handle* h, const Geom& g, cudaStream_t st) {
     const Workspace& w = h->ws;
     StepArgs<T> a;
@@ -457,8 +470,8 @@ struct EngineImpl {
     a.rbuf[1] = (T*)w.r2;
     a.x = w.x;
     a.hist = w.hist;
-    const size_t smem = step_smem_bytes<T, A, VEC>(g.bx, g.by, STAGES, KIND);
-    void (*kern)(Geom, StepArgs<T>, Scalars*) = k_step<T, A, VEC, KIND, STAGES>;
+    const size_t smem = step_smem_bytes<T, A, V>(g.bx, g.by, STAGES, KIND);
+    void (*kern)(Geom, StepArgs<T>, Scalars*) = k_step<T, A, V, KIND, STAGES>;
     if (allow_smem((const void*)kern, smem, st)) return S7_ECUDA;
     const int threads = ((g.bx * g.by + 31) / 32) * 32;
     kern<<<s7_nblocks(g), threads, smem, st>>>(g, a, w.sc);
@@ -487,10 +500,15 @@ struct EngineImpl {
       set((const void*)k_sweep9_1<T, A, VEC, false, MergedPass<T, X, A>>, b9);
       return rc;
     }
+    const Geom gw = step_geom(h, VW);
     for (int kind = 0; kind < 4; ++kind) {
-      if (!pipelined(h, g, kind)) continue;
-      const size_t b = step_smem_bytes<T, A, VEC>(g.bx, g.by, h->stages, kind);
-      set(step_fn(kind, h->stages), b);
+      if (h->step_vec == VW && VW != VEC) {
+        if (!pipelined<VW>(h, gw, kind)) continue;
+        set(step_fn<VW>(kind, h->stages), step_smem_bytes<T, A, VW>(gw.bx, gw.by, h->stages, kind));
+      } else {
+        if (!pipelined(h, g, kind)) continue;
+        set(step_fn<VEC>(kind, h->stages), step_smem_bytes<T, A, VEC>(g.bx, g.by, h->stages, kind));
+      }
     }
     const size_t gb = (size_t)3 * (g.by + 2) * (g.bx * VEC + 2 * VEC) * sizeof(A);
     set((const void*)k_sweep<T, A, VEC, true, SrcPUpdate<T, A>, EpiS<T, A>>, gb);
@@ -504,31 +522,49 @@ struct EngineImpl {
     return rc;
   }
 
+  template <int V>
   static const void* step_fn(int kind, int stages) {
     static const void* const fns[4][3] = {
-        {(const void*)k_step<T, A, VEC, 0, 2>, (const void*)k_step<T, A, VEC, 0, 3>,
-         (const void*)k_step<T, A, VEC, 0, 4>},
-        {(const void*)k_step<T, A, VEC, 1, 2>, (const void*)k_step<T, A, VEC, 1, 3>,
-         (const void*)k_step<T, A, VEC, 1, 4>},
-        {(const void*)k_step<T, A, VEC, 2, 2>, (const void*)k_step<T, A, VEC, 2, 3>,
-         (const void*)k_step<T, A, VEC, 2, 4>},
-        {(const void*)k_step<T, A, VEC, 3, 2>, (const void*)k_step<T, A, VEC, 3, 3>,
-         (const void*)k_step<T, A, VEC, 3, 4>}};
+        {(const void*)k_step<T, A, V, 0, 2>, (const void*)k_step<T, A, V, 0, 3>,
+         (const void*)k_step<T, A, V, 0, 4>},
+        {(const void*)k_step<T, A, V, 1, 2>, (const void*)k_step<T, A, V, 1, 3>,
+         (const void*)k_step<T, A, V, 1, 4>},
+        {(const void*)k_step<T, A, V, 2, 2>, (const void*)k_step<T, A, V, 2, 3>,
+         (const void*)k_step<T, A, V, 2, 4>},
+        {(const void*)k_step<T, A, V, 3, 2>, (const void*)k_step<T, A, V, 3, 3>,
+         (const void*)k_step<T, A, V, 3, 4>}};
     return fns[kind][std::min(std::max(stages, 2), 4) - 2];
   }
 
-  template <int KIND>
+  template <int KIND, int V = VEC>
   static int launch_step_any(const Handle* h, const Geom& g, cudaStream_t st) {
-    return h->stages == 4 ? launch_step<KIND, 4>(h, g, st)
-         : h->stages == 3 ? launch_step<KIND, 3>(h, g, st) : launch_step<KIND, 2>(h, g, st);
+    return h->stages == 4 ? launch_step<KIND, 4, V>(h, g, st)
+         : h->stages == 3 ? launch_step<KIND, 3, V>(h, g, st) : launch_step<KIND, 2, V>(h, g, st);
+  }
+
+  // The pipelined form of step kind `kind` if it applies (rc in *rc), at the
+  // handle's width.
+  template <int KIND>
+  static bool try_pipelined(const Handle* h, cudaStream_t st, int* rc) {
+    if (h->step_vec == VW && VW != VEC) {
+      const Geom gw = step_geom(h, VW);
+      if (!pipelined<VW>(h, gw, KIND)) return false;
+      *rc = launch_step_any<KIND, VW>(h, gw, st);
+      return true;
+    }
+    const Geom g = make_geom(h, VEC);
+    if (!pipelined(h, g, KIND)) return false;
+    *rc = launch_step_any<KIND>(h, g, st);
+    return true;
   }
 
   static int step_kernel(Handle* h, int which, cudaStream_t st) {
     const Geom g = make_geom(h, VEC);
     Workspace& w = h->ws;
     const bool vl = (h->nx % VEC == 0);
-    if (which < 2 && pipelined(h, g, which))
-      return which == 0 ? launch_step_any<0>(h, g, st) : launch_step_any<1>(h, g, st);
+    int rc = S7_OK;
+    if (which == 0 && try_pipelined<0>(h, st, &rc)) return rc;
+    if (which == 1 && try_pipelined<1>(h, st, &rc)) return rc;
     if (which == 0) {
       SrcPUpdate<T, A> sa;
       sa.r = (const T*)w.r;
@@ -564,8 +600,9 @@ struct EngineImpl {
     const Geom g = make_geom(h, VEC);
     Workspace& w = h->ws;
     const bool vl = (h->nx % VEC == 0);
-    if (pipelined(h, g, which + 1))
-      return which == 1 ? launch_step_any<2>(h, g, st) : launch_step_any<3>(h, g, st);
+    int rc = S7_OK;
+    if (which == 1 && try_pipelined<2>(h, st, &rc)) return rc;
+    if (which == 2 && try_pipelined<3>(h, st, &rc)) return rc;
     if (which == 1) {
       SrcQ2<T, A> sb;
       sb.rbuf[0] = (T*)w.r;
@@ -717,6 +754,7 @@ struct EngineImpl {
     size_t m = 0;
     const int vecs[3] = {VEC, 2, 4};
     for (int v : vecs) m = std::max(m, (size_t)s7_nblocks(make_geom(h, v)));
+    m = std::max(m, (size_t)s7_nblocks(step_geom(h, VW)));
     m = std::max(m, (size_t)pointwise_grid(h->n / VEC + 1, 1));
     return 4 * m;
   }

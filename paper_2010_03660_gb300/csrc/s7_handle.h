@@ -67,6 +67,7 @@ struct Handle {
   int stages;                 // step-sweep pipeline depth (1 = direct loads)
   int pipe_kinds;             // bit k: sweep k of a step uses the pipeline
   int variant;                // 0: three reductions per step; 1: two (merged passes)
+  int step_vec = 0;           // cells per thread in the pipelined sweeps
   size_t bytes = 0;           // device bytes held
   void* small = nullptr;      // 256 bytes of device scratch (flags)
   cudaStream_t stream = nullptr;   // private stream (captures, solves)

@@ -92,16 +92,58 @@ template <int KIND> struct KindShape {
   static constexpr bool x = KIND == 3;
 };
 
+// The register-form producer of each kind: it forms the two planes before
+// the pipeline starts (and, for the block's own cells of its first plane,
+// writes what that kind writes).
+template <int KIND, class T, class X, class A> struct KindSrc;
+template <class T, class X, class A> struct KindSrc<0, T, X, A> { typedef SrcPUpdate<T, A> type; };
+template <class T, class X, class A> struct KindSrc<1, T, X, A> { typedef SrcQ<T, A> type; };
+template <class T, class X, class A> struct KindSrc<2, T, X, A> { typedef SrcQ2<T, A> type; };
+template <class T, class X, class A> struct KindSrc<3, T, X, A> { typedef MergedPass<T, X, A> type; };
+
+template <class T, class X, class A>
+__device__ __forceinline__ void init_src(SrcPUpdate<T, A>& p, const StepArgs<T>& a, X*) {
+  p.r = a.r;
+  p.pbuf[0] = a.pbuf[0];
+  p.pbuf[1] = a.pbuf[1];
+  p.sbuf[0] = a.sbuf[0];
+  p.sbuf[1] = a.sbuf[1];
+}
+template <class T, class X, class A>
+__device__ __forceinline__ void init_src(SrcQ<T, A>& p, const StepArgs<T>& a, X*) {
+  p.r = a.r;
+  p.sbuf[0] = a.sbuf[0];
+  p.sbuf[1] = a.sbuf[1];
+}
+template <class T, class X, class A>
+__device__ __forceinline__ void init_src(SrcQ2<T, A>& p, const StepArgs<T>& a, X*) {
+  p.rbuf[0] = a.rbuf[0];
+  p.rbuf[1] = a.rbuf[1];
+  p.sbuf[0] = a.sbuf[0];
+  p.sbuf[1] = a.sbuf[1];
+}
+template <class T, class X, class A>
+__device__ __forceinline__ void init_src(MergedPass<T, X, A>& p, const StepArgs<T>& a, X* x) {
+  for (int k = 0; k < 2; ++k) {
+    p.rbuf[k] = a.rbuf[k];
+    p.pbuf[k] = a.pbuf[k];
+    p.sbuf[k] = a.sbuf[k];
+  }
+  p.y = a.y;
+  p.rh = a.rh;
+  p.x = x;
+  p.parts = a.parts;
+  p.hist = a.hist;
+}
+
 template <class T, int VEC>
 struct StepLayout {
   int TW, W, rows;     // tile width (elements), padded row pitch, rows incl. halo
   int coef_sz, rh_sz, in_sz, stage_sz;  // in elements of T
-  int x_off, x_bytes;  // iterate tile: byte offset in the stage, bytes
 };
 
 template <class T, int VEC>
-__host__ __device__ inline StepLayout<T, VEC> step_layout(int bx, int by, int nin, bool rh,
-                                                        int x_size = 0) {
+__host__ __device__ inline StepLayout<T, VEC> step_layout(int bx, int by, int nin, bool rh) {
   StepLayout<T, VEC> L;
   L.TW = bx * VEC;
   L.W = L.TW + 2 * VEC;
@@ -110,35 +152,46 @@ __host__ __device__ inline StepLayout<T, VEC> step_layout(int bx, int by, int ni
   L.rh_sz = rh ? by * L.TW : 0;
   L.in_sz = nin * L.rows * L.W;
   L.stage_sz = L.coef_sz + L.rh_sz + L.in_sz;
-  L.x_off = (int)(((size_t)L.stage_sz * sizeof(T) + 15) / 16 * 16);
-  L.x_bytes = x_size * by * L.TW;
   return L;
 }
 
-// Bytes of one stage, rounded up so every stage and the ring after the
-// stages start on a 16-byte boundary (vector shared-memory accesses).
+// Bytes of the staged T arrays of one stage, rounded up so every stage (and
+// the iterate tile after them, and the ring after the stages) starts on a
+// 16-byte boundary (vector shared-memory accesses).
 template <class T, int VEC>
 __host__ __device__ inline size_t stage_stride_bytes(const StepLayout<T, VEC>& L) {
-  return ((size_t)L.x_off + L.x_bytes + 15) / 16 * 16;
+  return ((size_t)L.stage_sz * sizeof(T) + 15) / 16 * 16;
+}
+
+// Bytes of one stage of kind KIND: the T arrays, then (kind 3) the tile of
+// the iterate x.
+template <class T, int VEC, int KIND>
+__host__ __device__ inline size_t kind_stride_bytes(const StepLayout<T, VEC>& L) {
+  if (!KindShape<KIND>::x) return stage_stride_bytes(L);
+  return (stage_stride_bytes(L) + sizeof(typename IterOf<T>::t) * L.TW * (L.rows - 2) + 15) /
+         16 * 16;
 }
 
 template <class T, int VEC, int KIND>
 __host__ __device__ inline StepLayout<T, VEC> kind_layout(int bx, int by) {
-  return step_layout<T, VEC>(bx, by, KindShape<KIND>::nin, KindShape<KIND>::rh,
-                             KindShape<KIND>::x ? (int)sizeof(typename IterOf<T>::t) : 0);
+  return step_layout<T, VEC>(bx, by, KindShape<KIND>::nin, KindShape<KIND>::rh);
+}
+
+template <class T, class A, int VEC, int KIND>
+__host__ __device__ inline size_t kind_smem_bytes(int bx, int by, int stages) {
+  const StepLayout<T, VEC> L = kind_layout<T, VEC, KIND>(bx, by);
+  const size_t ring = (size_t)3 * L.rows * L.W * sizeof(A);
+  return (size_t)stages * kind_stride_bytes<T, VEC, KIND>(L) + ring;
 }
 
 template <class T, class A, int VEC>
 __host__ __device__ inline size_t step_smem_bytes(int bx, int by, int stages, int kind) {
-  StepLayout<T, VEC> L;
   switch (kind) {
-    case 0: L = kind_layout<T, VEC, 0>(bx, by); break;
-    case 1: L = kind_layout<T, VEC, 1>(bx, by); break;
-    case 2: L = kind_layout<T, VEC, 2>(bx, by); break;
-    default: L = kind_layout<T, VEC, 3>(bx, by); break;
+    case 0: return kind_smem_bytes<T, A, VEC, 0>(bx, by, stages);
+    case 1: return kind_smem_bytes<T, A, VEC, 1>(bx, by, stages);
+    case 2: return kind_smem_bytes<T, A, VEC, 2>(bx, by, stages);
+    default: return kind_smem_bytes<T, A, VEC, 3>(bx, by, stages);
   }
-  const size_t ring = (size_t)3 * L.rows * L.W * sizeof(A);
-  return (size_t)stages * stage_stride_bytes(L) + ring;
 }
 
 template <class T, class A, int VEC, int KIND, int STAGES>
@@ -166,7 +219,7 @@ __global__ void __launch_bounds__(256) k_step(Geom g, StepArgs<T> a, Scalars* sc
          : (KIND == 3) ? (odd ? a.sbuf[0] : a.sbuf[1]) : a.y;
 
   const StepLayout<T, VEC> L = kind_layout<T, VEC, KIND>(g.bx, g.by);
-  const size_t sstride = stage_stride_bytes(L);
+  const size_t sstride = kind_stride_bytes<T, VEC, KIND>(L);
   auto stage_buf = [&](int k) { return reinterpret_cast<T*>(s7_smem + (size_t)k * sstride); };
   A* ring = reinterpret_cast<A*>(s7_smem + (size_t)STAGES * sstride);
   const int PL = L.rows * L.W;
@@ -206,13 +259,19 @@ __global__ void __launch_bounds__(256) k_step(Geom g, StepArgs<T> a, Scalars* sc
     const long long gi = own ? (long long)z * g.plane + row : 0;
 #pragma unroll
     for (int d = 0; d < 6; ++d) cp_async<VB>(buf + d * g.by * L.TW + sc_own, a.c[d] + gi, own ? VB : 0);
-    if (KindShape<KIND>::rh) cp_async<VB>(buf + L.coef_sz + sc_own, a.rh + gi, own ? VB : 0);
+    if constexpr (KindShape<KIND>::rh) cp_async<VB>(buf + L.coef_sz + sc_own, a.rh + gi, own ? VB : 0);
     const int zi = z + 1;
     if (zi >= g.nz) return;
     const long long gb = (long long)zi * g.plane + row;
-    if (KindShape<KIND>::x) {
-      X* xb = reinterpret_cast<X*>(reinterpret_cast<unsigned char*>(buf) + L.x_off) + sc_own;
-      cp_async<VEC * (int)sizeof(X)>(xb, xg + (own ? gb : 0), own ? VEC * (int)sizeof(X) : 0);
+    if constexpr (KindShape<KIND>::x) {
+      X* xb = reinterpret_cast<X*>(reinterpret_cast<unsigned char*>(buf) +
+                                   stage_stride_bytes(L)) + sc_own;
+      constexpr int XB = VEC * (int)sizeof(X);
+      constexpr int XC = XB > 16 ? 16 : XB;      // bytes per copy
+      constexpr int XE = XC / (int)sizeof(X);    // elements per copy
+#pragma unroll
+      for (int c = 0; c < XB / XC; ++c)
+        cp_async<XC>(xb + c * XE, xg + (own ? gb + c * XE : 0), own ? XC : 0);
     }
     T* ib = buf + L.coef_sz + L.rh_sz + so;
     for (int sidx = 0; sidx < nin; ++sidx) {
@@ -236,8 +295,8 @@ __global__ void __launch_bounds__(256) k_step(Geom g, StepArgs<T> a, Scalars* sc
   // value of the on-the-fly vector from staged inputs (index e in a plane)
   auto form = [&](const T* inb, int e) -> A {
     const A rv = to_acc<A>(inb[e]);
-    if (KIND == 1 || KIND == 2) return q_of(rv, to_acc<A>(inb[PL + e]), alpha);
-    if (KIND == 3) {
+    if constexpr (KIND == 1 || KIND == 2) return q_of(rv, to_acc<A>(inb[PL + e]), alpha);
+    if constexpr (KIND == 3) {
       A q, rn;
       return form_merged(rv, to_acc<A>(inb[PL + e]), to_acc<A>(inb[2 * PL + e]),
                          to_acc<A>(inb[3 * PL + e]), q, rn);
@@ -248,12 +307,12 @@ __global__ void __launch_bounds__(256) k_step(Geom g, StepArgs<T> a, Scalars* sc
   // the same for a run of VEC cells starting at e (one vector load per input)
   auto form_run = [&](const T* inb, int e, A (&v)[VEC]) {
     ldv<T, VEC>(inb + e, v);
-    if (KIND == 1 || KIND == 2) {
+    if constexpr (KIND == 1 || KIND == 2) {
       A sv[VEC];
       ldv<T, VEC>(inb + PL + e, sv);
 #pragma unroll
       for (int j = 0; j < VEC; ++j) v[j] = q_of(v[j], sv[j], alpha);
-    } else if (KIND == 3) {
+    } else if constexpr (KIND == 3) {
       A sv[VEC], yv[VEC], pv[VEC];
       ldv<T, VEC>(inb + PL + e, sv);
       ldv<T, VEC>(inb + 2 * PL + e, yv);
@@ -279,51 +338,13 @@ __global__ void __launch_bounds__(256) k_step(Geom g, StepArgs<T> a, Scalars* sc
   zero(rn_c);
   zero(rn_p);
   {
-    SrcPUpdate<T, A> sa;
-    SrcQ<T, A> sb;
-    SrcQ2<T, A> sq;
-    MergedPass<T, X, A> mp;
-    if (KIND == 0) {
-      sa.r = a.r;
-      sa.pbuf[0] = a.pbuf[0];
-      sa.pbuf[1] = a.pbuf[1];
-      sa.sbuf[0] = a.sbuf[0];
-      sa.sbuf[1] = a.sbuf[1];
-      sa.setup(sc);
-    } else if (KIND == 1) {
-      sb.r = a.r;
-      sb.sbuf[0] = a.sbuf[0];
-      sb.sbuf[1] = a.sbuf[1];
-      sb.setup(sc);
-    } else if (KIND == 2) {
-      sq.rbuf[0] = a.rbuf[0];
-      sq.rbuf[1] = a.rbuf[1];
-      sq.sbuf[0] = a.sbuf[0];
-      sq.sbuf[1] = a.sbuf[1];
-      sq.setup(sc);
-    } else {
-      for (int k = 0; k < 2; ++k) {
-        mp.rbuf[k] = a.rbuf[k];
-        mp.pbuf[k] = a.pbuf[k];
-        mp.sbuf[k] = a.sbuf[k];
-      }
-      mp.y = a.y;
-      mp.rh = a.rh;
-      mp.x = xg;
-      mp.parts = a.parts;
-      mp.hist = a.hist;
-      mp.setup(sc);
-    }
+    typename KindSrc<KIND, T, X, A>::type src;
+    init_src(src, a, xg);
+    src.setup(sc);
     auto prod = [&](long long i, int nv, A (&v)[VEC], bool write) {
-      if (KIND == 0) sa.template produce<VEC, true>(i, nv, v, write);
-      else if (KIND == 1) sb.template produce<VEC, true>(i, nv, v, write);
-      else if (KIND == 2) sq.template produce<VEC, true>(i, nv, v, write);
-      else mp.template produce<VEC, true>(i, nv, v, write);
+      src.template produce<VEC, true>(i, nv, v, write);
     };
-    auto prod1 = [&](long long i) -> A {
-      return KIND == 0 ? sa.produce1(i)
-           : KIND == 1 ? sb.produce1(i) : KIND == 2 ? sq.produce1(i) : mp.produce1(i);
-    };
+    auto prod1 = [&](long long i) -> A { return src.produce1(i); };
     if (z0 > 0 && own) prod((long long)(z0 - 1) * g.plane + row, VEC, vm, false);
     else zero(vm);
     A* rb = ring;
@@ -332,9 +353,10 @@ __global__ void __launch_bounds__(256) k_step(Geom g, StepArgs<T> a, Scalars* sc
       if (own) {
         prod(base, VEC, vc, true);
         // the fused pass keeps r_{i+1} of its own cells for the epilogue
-        if (KIND == 3)
+        if constexpr (KIND == 3) {
 #pragma unroll
-          for (int j = 0; j < VEC; ++j) rn_c[j] = mp.ring0[j];
+          for (int j = 0; j < VEC; ++j) rn_c[j] = src.ring0[j];
+        }
       } else {
         zero(vc);
       }
@@ -384,28 +406,32 @@ __global__ void __launch_bounds__(256) k_step(Geom g, StepArgs<T> a, Scalars* sc
     if (z + 1 < g.nz) {
       const bool ring_needed = z + 1 < z1;
       if (has_cell) {
-        if (KIND == 3 && own && ring_needed) {
-          // own cells of plane z+1: x and r updates of step i, p_{i+1}
-          A rv[VEC], sv[VEC], yv[VEC], pv[VEC], xv[VEC], q[VEC];
-          ldv<T, VEC>(inb + so, rv);
-          ldv<T, VEC>(inb + PL + so, sv);
-          ldv<T, VEC>(inb + 2 * PL + so, yv);
-          ldv<T, VEC>(inb + 3 * PL + so, pv);
-          ldv<X, VEC>(reinterpret_cast<const X*>(reinterpret_cast<const unsigned char*>(st) +
-                                                 L.x_off) + sc_own, xv);
+        bool formed = false;
+        if constexpr (KIND == 3) {
+          if (own && ring_needed) {
+            // own cells of plane z+1: x and r updates of step i, p_{i+1}
+            A rv[VEC], sv[VEC], yv[VEC], pv[VEC], xv[VEC], q[VEC];
+            ldv<T, VEC>(inb + so, rv);
+            ldv<T, VEC>(inb + PL + so, sv);
+            ldv<T, VEC>(inb + 2 * PL + so, yv);
+            ldv<T, VEC>(inb + 3 * PL + so, pv);
+            ldv<X, VEC>(reinterpret_cast<const X*>(reinterpret_cast<const unsigned char*>(st) +
+                                                   stage_stride_bytes(L)) + sc_own, xv);
 #pragma unroll
-          for (int j = 0; j < VEC; ++j) {
-            vp[j] = form_merged(rv[j], sv[j], yv[j], pv[j], q[j], rn_p[j]);
-            xv[j] = fma(omega, q[j], fma(alpha, pv[j], xv[j]));
+            for (int j = 0; j < VEC; ++j) {
+              vp[j] = form_merged(rv[j], sv[j], yv[j], pv[j], q[j], rn_p[j]);
+              xv[j] = fma(omega, q[j], fma(alpha, pv[j], xv[j]));
+            }
+            const long long gz = (long long)(z + 1) * g.plane + row;
+            store_run<X, VEC, true, true>(xg + gz, VEC, xv);
+            store_run<T, VEC, true, true>(r_out + gz, VEC, rn_p);
+            store_run<T, VEC, true, true>(p_out + gz, VEC, vp);
+            formed = true;
           }
-          const long long gz = (long long)(z + 1) * g.plane + row;
-          store_run<X, VEC, true, true>(xg + gz, VEC, xv);
-          store_run<T, VEC, true, true>(r_out + gz, VEC, rn_p);
-          store_run<T, VEC, true, true>(p_out + gz, VEC, vp);
-        } else if (own) {
-          form_run(inb, so, vp);
-        } else {
-          zero(vp);
+        }
+        if (!formed) {
+          if (own) form_run(inb, so, vp);
+          else zero(vp);
         }
         if (ring_needed) {
           sm_store<A, VEC>(nb + so, vp);
@@ -452,18 +478,18 @@ __global__ void __launch_bounds__(256) k_step(Geom g, StepArgs<T> a, Scalars* sc
         o[j] = as_stored<T>(s);
       }
       store_run<T, VEC, true, true>(out + (long long)z * g.plane + row, VEC, o);
-      if (KIND == 0) {
+      if constexpr (KIND == 0) {
         A hv[VEC];
         ldv<T, VEC>(st + L.coef_sz + sc_own, hv);
 #pragma unroll
         for (int j = 0; j < VEC; ++j) acc.part[0] = fma(hv[j], o[j], acc.part[0]);
-      } else if (KIND == 1) {
+      } else if constexpr (KIND == 1) {
 #pragma unroll
         for (int j = 0; j < VEC; ++j) {
           acc.part[0] = fma(vc[j], o[j], acc.part[0]);
           acc.part[1] = fma(o[j], o[j], acc.part[1]);
         }
-      } else if (KIND == 2) {
+      } else if constexpr (KIND == 2) {
         A hv[VEC];
         ldv<T, VEC>(st + L.coef_sz + sc_own, hv);
 #pragma unroll
@@ -488,13 +514,13 @@ __global__ void __launch_bounds__(256) k_step(Geom g, StepArgs<T> a, Scalars* sc
     for (int j = 0; j < VEC; ++j) {
       vm[j] = vc[j];
       vc[j] = vp[j];
-      if (KIND == 3) rn_c[j] = rn_p[j];
+      if constexpr (KIND == 3) rn_c[j] = rn_p[j];
     }
   }
   cp_async_wait<0>();
   acc.fold();
   const int nb_total = s7_nblocks(g);
-  if (KIND >= 2) {
+  if constexpr (KIND >= 2) {
     double v[3] = {acc.tot[0], acc.tot[1], acc.tot[I2]}, tot[3];
     block_sum<3>(v, red);
     if (grid_combine<3>(a.parts, &sc->counter[KIND == 2 ? CNT_B : CNT_C], nb_total, bid, v, tot,
@@ -502,7 +528,7 @@ __global__ void __launch_bounds__(256) k_step(Geom g, StepArgs<T> a, Scalars* sc
       if (KIND == 2) merged_q_finish(sc, tot[0], tot[1], tot[2]);
       else merged_pass_finish(sc, a.hist, tot[0], tot[1], tot[2]);
     }
-  } else if (KIND == 0) {
+  } else if constexpr (KIND == 0) {
     double v[1] = {acc.tot[0]}, tot[1];
     block_sum<1>(v, red);
     if (grid_combine<1>(a.parts, &sc->counter[CNT_A], nb_total, bid, v, tot, red) && t == 0) {

@@ -203,6 +203,39 @@ def test_pipeline_depth_two_reduction_variant(s7, storage, shape):
         assert np.array_equal(o.x.cpu().numpy(), outs[0].x.cpu().numpy())
 
 
+@pytest.mark.parametrize("storage", ["bf16", "f16"])
+@pytest.mark.parametrize("variant", [0, 1])
+def test_16bit_eight_cells_per_thread(s7, storage, variant):
+    """The pipelined sweeps at 8 cells (16 bytes) per thread: the same
+    method; only the grouping of the float32 partial sums changes, so the
+    history agrees with the 4-cell form to the storage precision, the
+    solution to what the tolerance allows, and a refined solve reaches
+    1e-10 on the true operator."""
+    nx, ny, nz = 64, 40, 36
+    p = synth.varcoef(nx, ny, nz, seed=47)
+    # plain solves stop above each format's plateau (bf16 stalls near 1e-3)
+    tol = 1e-2 if storage == "bf16" else 1e-3
+    res = {}
+    for cells in (4, 8):
+        with s7.stencil7_create(nx, ny, nz, gu.coef_on_device(p), storage=storage,
+                                keep_true=True, variant=variant, step_cells=cells) as op:
+            r = s7.bicgstab_solve(op, gu.to_dev(p.b), tol=tol, maxit=200)
+            again = s7.bicgstab_solve(op, gu.to_dev(p.b), tol=tol, maxit=200)
+            assert np.array_equal(r.x.cpu().numpy(), again.x.cpu().numpy())
+            rr = s7.bicgstab_solve_refined(op, gu.to_dev(p.b.astype(np.float64)), tol=1e-10,
+                                           max_outer=40, inner_maxit=100, inner_tol=1e-2)
+            assert rr.status == 0 and rr.hist[-1] <= 1e-10
+            xr = rr.x.cpu().numpy()
+            assert ob.true_residual(nx, ny, nz, p.coef, p.b.astype(np.float64), xr) <= 1.5e-10
+            res[cells] = r
+    a, b = res[4], res[8]
+    assert a.status == b.status == 0 and abs(a.iters - b.iters) <= max(3, a.iters // 4)
+    k = min(len(a.hist), len(b.hist), 6)
+    u = 2.0 ** -8 if storage == "bf16" else 2.0 ** -11
+    assert np.max(np.abs(a.hist[:k] - b.hist[:k]) / a.hist[:k]) < 50 * u
+    assert rel(b.x.cpu().numpy(), a.x.cpu().numpy().astype(np.float64)) < 0.05
+
+
 @pytest.mark.parametrize("storage", ["f64", "bf16", "f16"])
 def test_pipeline_depth_other_storage(s7, storage):
     nx, ny, nz = 48, 20, 30
