@@ -587,7 +587,8 @@ def run_refined(args):
     idx = rng.integers(0, p.n, 2000)
     for storage, inner_tol in (("bf16", 1e-2), ("f16", 1e-2), ("f16", 1e-3), ("f32", 1e-5),
                                ("f32", 1e-2)):
-        op = s7.stencil7_create(e, e, e, coef, storage=storage, keep_true=True)
+        op = s7.stencil7_create(e, e, e, coef, storage=storage, keep_true=True,
+                                variant=args.variant)
         for tol in (1e-8, 1e-10):
             def fn():
                 return s7.bicgstab_solve_refined(op, b, tol=tol, max_outer=80, inner_maxit=200,
@@ -613,7 +614,8 @@ def run_refined(args):
     base = min(runs["f32_in1e-05_tol1e-08"]["ms"], runs["f32_in0.01_tol1e-08"]["ms"])
     out = {"metric": "time to relative residual 1e-10, mixed precision (BF16 storage) + FP64 refinement",
            "value": runs["bf16_in0.01_tol1e-10"]["ms"] / 1e3, "unit": "s", "higher_is_better": False,
-           "workload": "refined_%d^3" % e, "dtype": "bf16/f16/f32 storage, f32 arithmetic, f64 outer",
+           "workload": "refined_%d^3%s" % (e, "_merged" if args.variant else ""),
+           "dtype": "bf16/f16/f32 storage, f32 arithmetic, f64 outer",
            "data": "synthetic (seed 2)", "runs": runs,
            "speedup_vs_best_fp32_storage_to_1e-8": {
                k: base / runs["%s_tol1e-08" % k]["ms"] for k in ("bf16_in0.01", "f16_in0.01",
