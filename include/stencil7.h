@@ -122,9 +122,10 @@ typedef struct {
                         (two passes, 104 instead of 116 bytes per cell in
                         float32; same iterates in exact arithmetic).
                         Single solves only; batched and served solves use 0. */
-  int step_cells;    /* cells per thread in the pipelined sweeps: 4, or for
-                        16-bit storage 8 (one 16-byte copy per array and
-                        thread); 0 = default (8 for 16-bit storage, else 4) */
+  int step_cells;    /* cells per thread in the pipelined sweeps: the width
+                        of the other sweeps (4; 2 for float64), or for 16-bit
+                        storage 8 (one 16-byte copy per array and thread);
+                        0 = default (8 for 16-bit storage)                    */
 } s7_opts;
 
 /* Create an operator handle.  Copies the coefficients to library-owned device

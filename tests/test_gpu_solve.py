@@ -186,7 +186,9 @@ def test_pipeline_depth_two_reduction_variant(s7, storage, shape):
     # the pipelined q/y and fused passes (kinds 2 and 3) against the
     # direct-load sweeps with the same policies and tile: bit for bit.  (A
     # different tile regroups the float64 block sums of the sweeps; in this
-    # variant (r0, r) is one of them, and its partials need not sum exactly.)
+    # variant (r0, r) is one of them, and its partials need not sum exactly.
+    # 16-bit storage is compared at 4 cells per thread, the register form's
+    # grouping of the float32 partial sums.)
     nx, ny, nz = shape
     raw = np.float64 if storage == "f64" else np.float32
     p = synth.varcoef(nx, ny, nz, seed=46, dtype=raw)
@@ -194,7 +196,8 @@ def test_pipeline_depth_two_reduction_variant(s7, storage, shape):
     outs = []
     for stages, by, kinds in ((1, 0, 0), (2, 0, 3), (3, 0, 1), (2, 0, 2), (4, 0, 3), (3, 0, 3)):
         with s7.stencil7_create(nx, ny, nz, gu.coef_on_device(p), storage=storage, variant=1,
-                                stages=stages, by=by, pipe_kinds=kinds) as op:
+                                stages=stages, by=by, pipe_kinds=kinds,
+                                step_cells=4 if storage in ("bf16", "f16") else 0) as op:
             outs.append(s7.bicgstab_solve(op, gu.to_dev(p.b), tol=tol, maxit=300))
     assert outs[0].status == 0
     for o in outs[1:]:
@@ -243,8 +246,10 @@ def test_pipeline_depth_other_storage(s7, storage):
     p = synth.varcoef(nx, ny, nz, seed=45, dtype=raw)
     outs = []
     for stages, kinds in ((1, 0), (2, 3), (3, 3), (2, 1)):
+        # 4 cells per thread: the register form's grouping of partial sums
         with s7.stencil7_create(nx, ny, nz, gu.coef_on_device(p), storage=storage,
-                                stages=stages, pipe_kinds=kinds) as op:
+                                stages=stages, pipe_kinds=kinds,
+                                step_cells=4 if storage in ("bf16", "f16") else 0) as op:
             outs.append(s7.bicgstab_solve(op, gu.to_dev(p.b), tol=1e-3, maxit=60))
     for o in outs[1:]:
         assert o.iters == outs[0].iters
