@@ -1111,7 +1111,8 @@ struct BatchPolicy {
   int zchunk;
 };
 
-// Autotuned policies by batch signature (storage, systems, log2 cells).
+// Autotuned policies by batch signature (storage, systems, log2 cells,
+// pipelined).
 std::map<std::tuple<int, int, int, int>, BatchPolicy> g_policy;
 std::mutex g_policy_mu;
 
@@ -1145,20 +1146,23 @@ struct BatchBuffers {
 }  // namespace
 
 // Lay out the batch for policy p: descriptors (host + device), block offsets.
+// `pipe`: the batch runs the pipelined step sweeps (tiles in units of the
+// engine's wide vector).
 static int batch_layout(int nsys, Handle* const* hs, const void* const* bdev, const Engine* eng,
                         const BatchPolicy& p, BatchBuffers& bb, const std::vector<size_t>& hist_off,
                         const std::vector<size_t>& parts_off, int* sweep_blocks, int* upd_blocks,
-                        size_t* smem, cudaStream_t st) {
+                        size_t* smem, int pipe, cudaStream_t st) {
   int b0 = 0, u0 = 0;
   size_t sm = 0;
   for (int j = 0; j < nsys; ++j) {
-    const Tile t = batch_tile(hs[j], eng->vec, p);
+    const Tile t = batch_tile(hs[j], pipe ? eng->vec_wide : eng->vec, p);
     int nb = 0, ub = 0;
     eng->fill_desc(hs[j], bb.h_desc.data() + (size_t)j * eng->desc_size, t, bdev[j],
-                   bb.parts + parts_off[j], bb.hist + hist_off[j], bb.sc + j, b0, u0, &nb, &ub);
+                   bb.parts + parts_off[j], bb.hist + hist_off[j], bb.sc + j, b0, u0, &nb, &ub,
+                   pipe);
     b0 += nb;
     u0 += ub;
-    sm = std::max(sm, eng->batched_smem(hs[j], t));
+    sm = std::max(sm, eng->batched_smem(hs[j], t, pipe));
   }
   *sweep_blocks = b0;
   *upd_blocks = u0;
@@ -1199,6 +1203,10 @@ extern "C" int bicgstab_solve_batched(int nsys, const stencil7_t* hs_in, const v
   bind_handle_device(hs[0]);
   const Engine* eng = engine_for(hs[0]->storage);
   const s7_dtype xt = xtype(hs[0]);
+  // the pipelined step sweeps when every system qualifies
+  int pipe = 1;
+  for (int j = 0; j < nsys; ++j) pipe &= eng->batch_pipe_ok(hs[j]);
+  const int bvec = pipe ? eng->vec_wide : eng->vec;
   cudaStream_t us = (cudaStream_t)stream;
   cudaStream_t st = nullptr;
   cudaEvent_t ev = nullptr;
@@ -1242,10 +1250,10 @@ extern "C" int bicgstab_solve_batched(int nsys, const stencil7_t* hs_in, const v
                                opts.zchunk > 0 ? opts.zchunk : 16});
     for (int j = 0; j < nsys; ++j) {
       Handle* h = hs[j];
-      const long long runs = (h->nx + eng->vec - 1) / eng->vec;
+      const long long runs = (h->nx + bvec - 1) / bvec;
       long long cap = 4096;  // update blocks
       for (const BatchPolicy& q : pols) {
-        const Tile t = batch_tile(h, eng->vec, q);
+        const Tile t = batch_tile(h, bvec, q);
         const long long nb = ((runs + t.bx - 1) / t.bx) * ((h->ny + t.by - 1) / t.by) *
                              ((h->nz + t.zchunk - 1) / t.zchunk);
         cap = std::max(cap, nb);
@@ -1270,7 +1278,7 @@ extern "C" int bicgstab_solve_batched(int nsys, const stencil7_t* hs_in, const v
   {
     int l2 = 0;
     while ((1LL << l2) < cells) ++l2;
-    const auto key = std::make_tuple((int)hs[0]->storage, nsys, l2, 0);
+    const auto key = std::make_tuple((int)hs[0]->storage, nsys, l2, pipe);
     bool have = false;
     if (opts.threads > 0 || opts.zchunk > 0 || opts.no_autotune) {
       pol.threads = opts.threads > 0 ? std::max(64, std::min(256, opts.threads)) : 128;
@@ -1295,14 +1303,14 @@ extern "C" int bicgstab_solve_batched(int nsys, const stencil7_t* hs_in, const v
         for (int zi = 0; zi < 3; ++zi) {
           BatchPolicy c{cand_t[ti], cand_z[zi]};
           if ((rc = batch_layout(nsys, hs.data(), bdev.data(), eng, c, bb, hist_off, parts_off,
-                                 &sweep_blocks, &upd_blocks, &smem, st)))
+                                 &sweep_blocks, &upd_blocks, &smem, pipe, st)))
             goto tune_out;
-          if (eng->batched_prepare(smem)) { rc = fail(S7_ECUDA, "batched kernel attributes"); goto tune_out; }
+          if (eng->batched_prepare(smem, pipe)) { rc = fail(S7_ECUDA, "batched kernel attributes"); goto tune_out; }
           // warm, then time two probes
-          if ((rc = eng->launch_batched(3, bb.desc, nsys, sweep_blocks, c.threads, smem, st))) goto tune_out;
+          if ((rc = eng->launch_batched(3, bb.desc, nsys, sweep_blocks, c.threads, smem, st, pipe))) goto tune_out;
           cudaEventRecord(e0, st);
           for (int r = 0; r < 2 && rc == S7_OK; ++r)
-            rc = eng->launch_batched(3, bb.desc, nsys, sweep_blocks, c.threads, smem, st);
+            rc = eng->launch_batched(3, bb.desc, nsys, sweep_blocks, c.threads, smem, st, pipe);
           cudaEventRecord(e1, st);
           if (rc) goto tune_out;
           if ((e = cudaEventSynchronize(e1)) != cudaSuccess) { rc = cuda_fail(e, "autotune"); goto tune_out; }
@@ -1323,9 +1331,9 @@ extern "C" int bicgstab_solve_batched(int nsys, const stencil7_t* hs_in, const v
   }
   threads = pol.threads;
   if ((rc = batch_layout(nsys, hs.data(), bdev.data(), eng, pol, bb, hist_off, parts_off,
-                         &sweep_blocks, &upd_blocks, &smem, st)))
+                         &sweep_blocks, &upd_blocks, &smem, pipe, st)))
     goto out;
-  if (eng->batched_prepare(smem)) { rc = fail(S7_ECUDA, "batched kernel attributes"); goto out; }
+  if (eng->batched_prepare(smem, pipe)) { rc = fail(S7_ECUDA, "batched kernel attributes"); goto out; }
   // scalars: tol, maxit
   for (int j = 0; j < nsys; ++j) {
     Scalars& s = bb.h_sc[j];
@@ -1335,8 +1343,8 @@ extern "C" int bicgstab_solve_batched(int nsys, const stencil7_t* hs_in, const v
     s.status = S7_ENOTCONV;
   }
   if ((e = cudaMemcpyAsync(bb.sc, bb.h_sc, (size_t)nsys * sizeof(Scalars), cudaMemcpyHostToDevice, st)) != cudaSuccess) { rc = cuda_fail(e, "scalars"); goto out; }
-  if ((rc = eng->launch_batched(2, bb.desc, nsys, sweep_blocks, threads, smem, st)) ||
-      (rc = eng->launch_batched(5, bb.desc, nsys, 0, 0, 0, st))) {
+  if ((rc = eng->launch_batched(2, bb.desc, nsys, sweep_blocks, threads, smem, st, pipe)) ||
+      (rc = eng->launch_batched(5, bb.desc, nsys, 0, 0, 0, st, pipe))) {
     rc = fail(rc, "batched start launch failed: %s", cudaGetErrorString(cudaGetLastError()));
     goto out;
   }
@@ -1345,9 +1353,9 @@ extern "C" int bicgstab_solve_batched(int nsys, const stencil7_t* hs_in, const v
     cudaGraph_t g = nullptr;
     if ((e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) { rc = cuda_fail(e, "capture"); goto out; }
     for (int k = 0; k < ce && rc == S7_OK; ++k) {
-      rc = eng->launch_batched(0, bb.desc, nsys, sweep_blocks, threads, smem, st);
-      if (!rc) rc = eng->launch_batched(1, bb.desc, nsys, sweep_blocks, threads, smem, st);
-      if (!rc) rc = eng->launch_batched(4, bb.desc, nsys, upd_blocks, 256, 0, st);
+      rc = eng->launch_batched(0, bb.desc, nsys, sweep_blocks, threads, smem, st, pipe);
+      if (!rc) rc = eng->launch_batched(1, bb.desc, nsys, sweep_blocks, threads, smem, st, pipe);
+      if (!rc) rc = eng->launch_batched(4, bb.desc, nsys, upd_blocks, 256, 0, st, pipe);
     }
     e = cudaStreamEndCapture(st, &g);
     if (rc || e != cudaSuccess) {

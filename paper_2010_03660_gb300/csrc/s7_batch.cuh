@@ -10,6 +10,7 @@
 // whose members converge at different steps.
 #pragma once
 
+#include "s7_step.cuh"
 #include "s7_sweep.cuh"
 
 namespace s7 {
@@ -125,6 +126,38 @@ __global__ void __launch_bounds__(256) k_sweep_batched(const SysDesc<T, X>* __re
     if (d.vl) sweep_body<T, A, VEC, true>(g, cf, src, epi, nullptr, bid, d.nblocks, sm, red);
     else sweep_body<T, A, VEC, false>(g, cf, src, epi, nullptr, bid, d.nblocks, sm, red);
   }
+}
+
+// The pipelined sweeps (kinds 0, 1 of s7_step.cuh) over a batch whose
+// systems all qualify (Jacobi-scaled per-cell operators, rows of whole
+// VEC-cell vectors); each system's geometry in its descriptor is for VEC
+// cells per thread.
+template <class T, class X, class A, int VEC, int KIND, int STAGES>
+__global__ void __launch_bounds__(256) k_step_batched(const SysDesc<T, X>* __restrict__ sys,
+                                                      int nsys) {
+  extern __shared__ __align__(16) unsigned char s7_smem[];
+  __shared__ double red[32 * 4];
+  __shared__ int s_sys;
+  if (threadIdx.x == 0) s_sys = find_system(sys, nsys, (int)blockIdx.x, false);
+  __syncthreads();
+  const SysDesc<T, X>& d = sys[s_sys];
+  if (*((volatile int*)&d.sc->done)) return;
+  StepArgs<T> a;
+  for (int k = 0; k < 6; ++k) a.c[k] = d.c[k];
+  a.r = d.r;
+  a.rh = d.rh;
+  a.pbuf[0] = d.p[0];
+  a.pbuf[1] = d.p[1];
+  a.sbuf[0] = d.s[0];
+  a.sbuf[1] = d.s[1];
+  a.y = d.y;
+  a.parts = d.parts;
+  a.rbuf[0] = d.r;
+  a.rbuf[1] = d.r;
+  a.x = d.x;
+  a.hist = d.hist;
+  step_body<T, A, VEC, KIND, STAGES>(d.g, a, d.sc, (int)blockIdx.x - d.block0, d.nblocks, s7_smem,
+                                     red);
 }
 
 template <class T, class X, class A, int VEC>

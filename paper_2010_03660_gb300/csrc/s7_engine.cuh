@@ -769,12 +769,12 @@ struct EngineImpl {
   // ---- batched solves ----
   typedef SysDesc<T, X> Desc;
 
-  static Geom geom_tile(const Handle* h, const Tile& t) {
+  static Geom geom_tile(const Handle* h, const Tile& t, int v) {
     Geom g;
     g.nx = h->nx;
     g.ny = h->ny;
     g.nz = h->nz;
-    const int runs = (h->nx + VEC - 1) / VEC;
+    const int runs = (h->nx + v - 1) / v;
     g.bx = std::min(t.bx, runs);
     g.by = std::min(t.by, h->ny);
     g.tiles_x = (runs + g.bx - 1) / g.bx;
@@ -785,12 +785,23 @@ struct EngineImpl {
     return g;
   }
 
+  // Batched pipelined sweeps: VW cells per thread, 2 stages; the q/y sweep
+  // too for 16-bit storage (as for single solves).
+  static constexpr int SB = 2;
+  static constexpr bool kPipeQ = sizeof(T) == 2;
+
+  static int batch_pipe_ok(const Handle* h) {
+    return h->stencil == 7 && h->jacobi && !h->constant && h->nx % VW == 0;
+  }
+
   static void fill_desc(Handle* h, void* out, const Tile& t, const void* b, double* parts,
-                        double* hist, Scalars* sc, int block0, int ublock0, int* nb, int* unb) {
+                        double* hist, Scalars* sc, int block0, int ublock0, int* nb, int* unb,
+                        int pipe) {
+    const int v = pipe ? VW : VEC;
     Desc d;
     memset(&d, 0, sizeof d);
-    d.g = geom_tile(h, t);
-    d.vl = (h->nx % VEC == 0) && aligned16(b);
+    d.g = geom_tile(h, t, v);
+    d.vl = (h->nx % v == 0) && aligned16(b);
     d.block0 = block0;
     d.nblocks = s7_nblocks(d.g);
     d.ublock0 = ublock0;
@@ -824,27 +835,52 @@ struct EngineImpl {
     *unb = d.unblocks;
   }
 
-  static size_t batched_smem(const Handle* h, const Tile& t) {
-    const Geom g = geom_tile(h, t);
-    return (size_t)3 * (g.by + 2) * (g.bx * VEC + 2 * VEC) * sizeof(A);
+  static size_t batched_smem(const Handle* h, const Tile& t, int pipe) {
+    const int v = pipe ? VW : VEC;
+    const Geom g = geom_tile(h, t, v);
+    size_t m = (size_t)3 * (g.by + 2) * (g.bx * v + 2 * v) * sizeof(A);
+    if (pipe) {
+      m = std::max(m, step_smem_bytes<T, A, VW>(g.bx, g.by, SB, 0));
+      if (kPipeQ) m = std::max(m, step_smem_bytes<T, A, VW>(g.bx, g.by, SB, 1));
+    }
+    return m;
   }
 
-  static int batched_prepare(size_t smem) {
+  static int batched_prepare(size_t smem, int pipe) {
     if (smem <= kSmemNoOptIn) return S7_OK;
-    const void* ks[4] = {(const void*)k_sweep_batched<T, X, DT, A, VEC, 0>,
-                         (const void*)k_sweep_batched<T, X, DT, A, VEC, 1>,
-                         (const void*)k_sweep_batched<T, X, DT, A, VEC, 2>,
-                         (const void*)k_sweep_batched<T, X, DT, A, VEC, 3>};
-    for (const void* k : ks)
-      if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+    const void* reg[4] = {(const void*)k_sweep_batched<T, X, DT, A, VEC, 0>,
+                          (const void*)k_sweep_batched<T, X, DT, A, VEC, 1>,
+                          (const void*)k_sweep_batched<T, X, DT, A, VEC, 2>,
+                          (const void*)k_sweep_batched<T, X, DT, A, VEC, 3>};
+    const void* wide[5] = {(const void*)k_step_batched<T, X, A, VW, 0, SB>,
+                           (const void*)k_step_batched<T, X, A, VW, 1, SB>,
+                           (const void*)k_sweep_batched<T, X, DT, A, VW, 1>,
+                           (const void*)k_sweep_batched<T, X, DT, A, VW, 2>,
+                           (const void*)k_sweep_batched<T, X, DT, A, VW, 3>};
+    const void* const* ks = pipe ? wide : reg;
+    const int nk = pipe ? 5 : 4;
+    for (int k = 0; k < nk; ++k)
+      if (cudaFuncSetAttribute(ks[k], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
           cudaSuccess)
         return S7_ECUDA;
     return S7_OK;
   }
 
   static int launch_batched(int kind, const void* descs, int nsys, int blocks, int threads,
-                            size_t smem, cudaStream_t st) {
+                            size_t smem, cudaStream_t st, int pipe) {
     const Desc* d = (const Desc*)descs;
+    if (pipe && kind <= 3) {
+      switch (kind) {
+        case 0: k_step_batched<T, X, A, VW, 0, SB><<<blocks, threads, smem, st>>>(d, nsys); break;
+        case 1:
+          if (kPipeQ) k_step_batched<T, X, A, VW, 1, SB><<<blocks, threads, smem, st>>>(d, nsys);
+          else k_sweep_batched<T, X, DT, A, VW, 1><<<blocks, threads, smem, st>>>(d, nsys);
+          break;
+        case 2: k_sweep_batched<T, X, DT, A, VW, 2><<<blocks, threads, smem, st>>>(d, nsys); break;
+        default: k_sweep_batched<T, X, DT, A, VW, 3><<<blocks, threads, smem, st>>>(d, nsys); break;
+      }
+      return cudaGetLastError() == cudaSuccess ? S7_OK : S7_ECUDA;
+    }
     switch (kind) {
       case 0: k_sweep_batched<T, X, DT, A, VEC, 0><<<blocks, threads, smem, st>>>(d, nsys); break;
       case 1: k_sweep_batched<T, X, DT, A, VEC, 1><<<blocks, threads, smem, st>>>(d, nsys); break;
@@ -858,13 +894,13 @@ struct EngineImpl {
   }
 
   static const Engine* get() {
-    static const Engine e = {sizeof(T), sizeof(X), sizeof(DT), VEC, &scale, &scale9, &apply, &init,
-                             &step_kernel,
+    static const Engine e = {sizeof(T), sizeof(X), sizeof(DT), VEC, VW, &scale, &scale9, &apply,
+                             &init, &step_kernel,
                              &true_resid, &raw_resid, &cast, &parts_needed, &smem_ok,
                              &raw_resid_into, &raw_resid_blocks, &prepare_capture,
                              &merged_kernel,
-                             sizeof(Desc), &fill_desc, &batched_smem, &launch_batched,
-                             &batched_prepare};
+                             sizeof(Desc), &batch_pipe_ok, &fill_desc, &batched_smem,
+                             &launch_batched, &batched_prepare};
     return &e;
   }
 };

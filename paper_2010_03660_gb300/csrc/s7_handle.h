@@ -88,6 +88,7 @@ struct Engine {
   size_t x_size;   // iterate element size (8 or 4)
   size_t d_size;   // kept-diagonal element size
   int vec;         // cells per thread in the sweeps
+  int vec_wide;    // cells per thread of the pipelined sweeps at their widest
   // scale raw coefficients (device, dtype raw_dt) into the handle
   int (*scale)(Handle* h, const void* const raw[7], s7_dtype raw_dt, cudaStream_t st, int* bad);
   // the same for the 9-point operator: raw = xm xp ym yp xmym xpym xmyp xpyp
@@ -115,18 +116,23 @@ struct Engine {
   // x, r update + p/s pass of the next step
   int (*merged_kernel)(Handle* h, int which, cudaStream_t st);
   // ---- batched solves (s7_batch.cuh) ----
+  // A batch is "pipelined" when every system qualifies (batch_pipe_ok):
+  // its step sweeps then run the cp.async-pipelined bodies at vec_wide
+  // cells per thread, and every sweep of the batch uses that geometry (the
+  // tile t is then in units of vec_wide cells).
   size_t desc_size;
+  int (*batch_pipe_ok)(const Handle* h);
   // Fill the batch descriptor of system h (host memory) for tile t with
   // sweep blocks starting at block0 and update blocks at ublock0; returns
   // the block counts.
   void (*fill_desc)(Handle* h, void* desc, const Tile& t, const void* b, double* parts,
                     double* hist, Scalars* sc, int block0, int ublock0, int* nblocks,
-                    int* unblocks);
-  size_t (*batched_smem)(const Handle* h, const Tile& t);
+                    int* unblocks, int pipe);
+  size_t (*batched_smem)(const Handle* h, const Tile& t, int pipe);
   // kind 0..3: batched sweeps (see s7_batch.cuh), 4: update, 5: history start
   int (*launch_batched)(int kind, const void* descs, int nsys, int blocks, int threads,
-                        size_t smem, cudaStream_t st);
-  int (*batched_prepare)(size_t smem);
+                        size_t smem, cudaStream_t st, int pipe);
+  int (*batched_prepare)(size_t smem, int pipe);
 };
 
 const Engine* engine_f64();

@@ -20,6 +20,13 @@
 // arithmetic is independent of the others in the batch (own blocks, own
 // reductions, a fixed tile policy), so its result does not depend on what
 // else was running.
+//
+// A request with per-cell coefficients is held with its x extent padded to
+// a multiple of the engine's wide vector: padding cells have a unit
+// diagonal, no couplings and a zero right-hand side, so every vector stays
+// exactly zero there and the solution on the real cells is unchanged.  With
+// all rows made of whole vectors, the batch's step sweeps run the
+// cp.async-pipelined bodies.
 #include <math.h>
 #include <string.h>
 
@@ -59,6 +66,31 @@ __global__ void k_axpy_x(long long n, double s, const X* d, double* x) {
     x[i] = fma(s, (double)d[i], x[i]);
 }
 
+// dst (rows of nxp) from src (rows of nx): padding cells get `fill`.
+template <class V>
+__global__ void k_pad(long long rows, int nx, int nxp, const V* __restrict__ src,
+                      V* __restrict__ dst, V fill) {
+  const long long n = rows * nxp;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long row = i / nxp;
+    const int x = (int)(i - row * nxp);
+    dst[i] = x < nx ? src[row * nx + x] : fill;
+  }
+}
+
+// dst (rows of nx) from src (rows of nxp).
+template <class V>
+__global__ void k_unpad(long long rows, int nx, int nxp, const V* __restrict__ src,
+                        V* __restrict__ dst) {
+  const long long n = rows * nx;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long row = i / nx;
+    dst[i] = src[row * nxp + (i - row * nx)];
+  }
+}
+
 template <class S, class D>
 __global__ void k_conv(long long n, const S* a, D* b) {
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -80,7 +112,9 @@ struct Req {
   int status = S7_EAGAIN;
   int outer = 0, inner_total = 0;
   double resid = 0, s = 0, rel0 = 0;
-  long long n = 0;
+  long long n = 0;       // cells held (x extent padded to nxp)
+  long long n_in = 0;    // cells of the request
+  int nxp = 0;
   size_t bytes = 0;
   int slot = -1;
   stencil7_t h = nullptr;
@@ -123,16 +157,17 @@ struct s7_server {
 
 namespace {
 
-size_t request_bytes(const s7_server* S, long long n) {
+size_t request_bytes(const s7_server* S, long long n, int raw_size) {
   // stored operator, kept diagonal, true float32 operator, seven Krylov
   // vectors, x and b in float32, three float64 refinement vectors, and the
-  // float32 staging of the raw coefficients while the operator is created
+  // staging of the raw coefficients (seven arrays and one more while a
+  // padded operator is formed) while the operator is created
   const size_t ts = S->eng->t_size;
-  return (size_t)n * (6 * ts + 4 + 28 + 7 * ts + 8 + 24 + 28) + (1 << 20);
+  return (size_t)n * (6 * ts + 4 + 28 + 7 * ts + 8 + 24 + 8 * (size_t)raw_size) + (1 << 20);
 }
 
-Tile serve_tile(const s7_server* S, int nx, int ny, int nz) {
-  const int vec = S->eng->vec;
+Tile serve_tile(const s7_server* S, int nx, int ny, int nz, int pipe) {
+  const int vec = pipe ? S->eng->vec_wide : S->eng->vec;
   const int T = S->o.threads;
   const int runs = (nx + vec - 1) / vec;
   const int cap = std::min(32, T);
@@ -159,13 +194,88 @@ void release_req(s7_server* S, Req* r) {
   r->slot = -1;
 }
 
+// Bring an nx*ny*nz array (host or device, `es`-byte elements) into the
+// padded layout `dst` (rows of nxp), staging it contiguously in `tmp`.
+cudaError_t pad_in(void* dst, const void* src, void* tmp, int nx, int nxp, long long rows, int es,
+                   double fill, cudaStream_t st) {
+  const long long n = rows * nx;
+  if (nx == nxp) return cudaMemcpyAsync(dst, src, (size_t)n * es, cudaMemcpyDefault, st);
+  cudaError_t e = cudaMemcpyAsync(tmp, src, (size_t)n * es, cudaMemcpyDefault, st);
+  if (e != cudaSuccess) return e;
+  if (es == 8)
+    k_pad<double><<<grid_of(rows * nxp), 256, 0, st>>>(rows, nx, nxp, (const double*)tmp,
+                                                      (double*)dst, fill);
+  else
+    k_pad<float><<<grid_of(rows * nxp), 256, 0, st>>>(rows, nx, nxp, (const float*)tmp,
+                                                     (float*)dst, (float)fill);
+  return cudaGetLastError();
+}
+
+// The padded array `src` back to the caller's layout `dst` (rows of nx),
+// through the contiguous device buffer `tmp`.
+cudaError_t pad_out(void* dst, const void* src, void* tmp, int nx, int nxp, long long rows,
+                    int es, cudaStream_t st) {
+  const long long n = rows * nx;
+  if (nx == nxp) return cudaMemcpyAsync(dst, src, (size_t)n * es, cudaMemcpyDefault, st);
+  if (es == 8)
+    k_unpad<double><<<grid_of(n), 256, 0, st>>>(rows, nx, nxp, (const double*)src, (double*)tmp);
+  else
+    k_unpad<float><<<grid_of(n), 256, 0, st>>>(rows, nx, nxp, (const float*)src, (float*)tmp);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return cudaMemcpyAsync(dst, tmp, (size_t)n * es, cudaMemcpyDefault, st);
+}
+
+// The request's operator with its x extent padded to r->nxp (unit diagonal,
+// zero couplings in the padding).
+int create_padded(s7_server* S, Req* r, const s7_opts* oo) {
+  const s7_coeffs& c = r->in.coeffs;
+  const int es = c.dtype == S7_F64 ? 8 : 4;
+  const size_t n = (size_t)r->n;
+  const long long rows = (long long)r->in.ny * r->in.nz;
+  cudaStream_t as = S->st_admit;
+  unsigned char* buf = nullptr;
+  if (cudaMalloc(&buf, 8 * n * es) != cudaSuccess) {
+    cudaGetLastError();
+    return set_error(S7_ENOMEM, "s7_server: staging the padded operator");
+  }
+  const void* src[7] = {c.xm, c.xp, c.ym, c.yp, c.zm, c.zp, c.diag};
+  void* dst[7];
+  void* tmp = buf + 7 * n * es;
+  cudaError_t e = cudaSuccess;
+  for (int d = 0; d < 7 && e == cudaSuccess; ++d) {
+    dst[d] = buf + d * n * es;
+    e = pad_in(dst[d], src[d], tmp, r->in.nx, r->nxp, rows, es, d == 6 ? 1.0 : 0.0, as);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(as);
+  int rc = S7_OK;
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    rc = S7_ECUDA;
+  } else {
+    s7_coeffs pc = c;
+    pc.xm = dst[0];
+    pc.xp = dst[1];
+    pc.ym = dst[2];
+    pc.yp = dst[3];
+    pc.zm = dst[4];
+    pc.zp = dst[5];
+    pc.diag = dst[6];
+    rc = stencil7_create(&r->h, r->nxp, r->in.ny, r->in.nz, &pc, oo);
+  }
+  cudaFree(buf);
+  return rc;
+}
+
 // Admit one request: operator, workspace, float64 vectors, slot.
 int admit(s7_server* S, Req* r) {
   s7_opts oo;
   memset(&oo, 0, sizeof oo);
   oo.storage = S->o.storage;
   oo.keep_true = 1;
-  int rc = stencil7_create(&r->h, r->in.nx, r->in.ny, r->in.nz, &r->in.coeffs, &oo);
+  int rc = r->nxp != r->in.nx
+               ? create_padded(S, r, &oo)
+               : stencil7_create(&r->h, r->in.nx, r->in.ny, r->in.nz, &r->in.coeffs, &oo);
   if (rc) return rc;
   if ((rc = ensure_ws(r->h, S->o.inner_maxit))) return rc;
   const size_t n = (size_t)r->n;
@@ -176,22 +286,28 @@ int admit(s7_server* S, Req* r) {
     cudaGetLastError();
     return S7_ENOMEM;
   }
-  const Tile t = serve_tile(S, r->in.nx, r->in.ny, r->in.nz);
-  const long long runs = (r->in.nx + S->eng->vec - 1) / S->eng->vec;
-  const long long nb = ((runs + t.bx - 1) / t.bx) * ((r->in.ny + t.by - 1) / t.by) *
-                       ((r->in.nz + t.zchunk - 1) / t.zchunk);
+  long long nb = 0;
+  for (int pipe = 0; pipe < 2; ++pipe) {
+    const int v = pipe ? S->eng->vec_wide : S->eng->vec;
+    const Tile t = serve_tile(S, r->nxp, r->in.ny, r->in.nz, pipe);
+    const long long runs = (r->nxp + v - 1) / v;
+    nb = std::max(nb, ((runs + t.bx - 1) / t.bx) * ((r->in.ny + t.by - 1) / t.by) *
+                          ((r->in.nz + t.zchunk - 1) / t.zchunk));
+  }
   const long long rb = S->eng->raw_resid_blocks(r->h, S7_F64);
   r->parts_n = 2 * (size_t)std::max(std::max(nb, rb), 4096LL);
   if ((e = cudaMalloc(&r->parts, r->parts_n * 8)) != cudaSuccess) {
     cudaGetLastError();
     return S7_ENOMEM;
   }
-  // b (host or device, f32/f64) -> float64; x0 = 0
+  // b (host or device, f32/f64) -> float64 (zero in the padding); x0 = 0
   cudaStream_t as = S->st_admit;
+  const long long rows = (long long)r->in.ny * r->in.nz;
   if (r->in.dt == S7_F64) {
-    e = cudaMemcpyAsync(r->br, r->in.b, n * 8, cudaMemcpyDefault, as);
+    // r->rr (unused until the first residual) stages b
+    e = pad_in(r->br, r->in.b, r->rr, r->in.nx, r->nxp, rows, 8, 0.0, as);
   } else {
-    e = cudaMemcpyAsync(r->h->ws.b, r->in.b, n * 4, cudaMemcpyDefault, as);
+    e = pad_in(r->h->ws.b, r->in.b, r->h->ws.x, r->in.nx, r->nxp, rows, 4, 0.0, as);
     if (e == cudaSuccess) {
       k_conv<float, double><<<grid_of(n), 256, 0, as>>>((long long)n, (const float*)r->h->ws.b, r->br);
       e = cudaGetLastError();
@@ -224,11 +340,12 @@ void finish(s7_server* S, Req* r, int status) {
   const size_t n = (size_t)r->n;
   if (status == S7_OK || status == S7_ENOTCONV) {
     cudaError_t e;
+    const long long rows = (long long)r->in.ny * r->in.nz;
     if (r->in.dt == S7_F64) {
-      e = cudaMemcpyAsync(r->in.x, r->xr, n * 8, cudaMemcpyDefault, S->st);
+      e = pad_out(r->in.x, r->xr, r->rr, r->in.nx, r->nxp, rows, 8, S->st);
     } else {
       k_conv<double, float><<<grid_of(n), 256, 0, S->st>>>((long long)n, r->xr, (float*)r->h->ws.x);
-      e = cudaMemcpyAsync(r->in.x, r->h->ws.x, n * 4, cudaMemcpyDefault, S->st);
+      e = pad_out(r->in.x, r->h->ws.x, r->h->ws.b, r->in.nx, r->nxp, rows, 4, S->st);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(S->st);
     if (e != cudaSuccess) {
@@ -299,7 +416,7 @@ void scheduler(s7_server* S) {
   const int K = S->o.steps_per_tick;
   std::vector<unsigned char> hd, hds;
   int sweep_blocks = 0, upd_blocks = 0;
-  size_t smem_max = 0;
+  size_t smem_max[2] = {0, 0};   // by pipelined or not
   for (;;) {
     // ---- pick up requests the admission thread has set up
     {
@@ -354,8 +471,9 @@ void scheduler(s7_server* S) {
           finish(S, r, S7_ENOTCONV);
           continue;
         }
-        // inner right-hand side r / s with unit RMS, x_inner = 0
-        r->s = rn / sqrt((double)r->n);
+        // inner right-hand side r / s with unit RMS over the request's cells,
+        // x_inner = 0
+        r->s = rn / sqrt((double)r->n_in);
         const bool f64 = S->o.storage == S7_F64;
         k_rhs_scaled<<<grid_of(r->n), 256, 0, S->st>>>(
             r->n, r->rr, 1.0 / r->s, f64 ? nullptr : (float*)r->h->ws.b,
@@ -384,21 +502,27 @@ void scheduler(s7_server* S) {
       if (r->state == INNER_START || r->state == INNER) inner.push_back(r);
     for (Req* r : inner)
       if (r->state == INNER_START) starting.push_back(r);
+    // the pipelined step sweeps when every request of the set qualifies
+    auto pipe_of = [&](const std::vector<Req*>& set) {
+      int p = 1;
+      for (Req* r : set) p &= eng->batch_pipe_ok(r->h);
+      return p;
+    };
     auto layout = [&](const std::vector<Req*>& set, std::vector<unsigned char>& host, void* dev,
-                      int* nb_total, int* ub_total, size_t* smem) {
+                      int* nb_total, int* ub_total, size_t* smem, int pipe) {
       host.resize(set.size() * eng->desc_size);
       int b0 = 0, u0 = 0;
       size_t sm = 0;
       for (size_t j = 0; j < set.size(); ++j) {
         Req* r = set[j];
-        const Tile t = serve_tile(S, r->in.nx, r->in.ny, r->in.nz);
+        const Tile t = serve_tile(S, r->nxp, r->in.ny, r->in.nz, pipe);
         int nb = 0, ub = 0;
         eng->fill_desc(r->h, host.data() + j * eng->desc_size, t, r->h->ws.b, r->parts,
                        S->d_hist + (size_t)r->slot * (S->o.inner_maxit + 1), S->d_sc + r->slot,
-                       b0, u0, &nb, &ub);
+                       b0, u0, &nb, &ub, pipe);
         b0 += nb;
         u0 += ub;
-        sm = std::max(sm, eng->batched_smem(r->h, t));
+        sm = std::max(sm, eng->batched_smem(r->h, t, pipe));
       }
       *nb_total = b0;
       *ub_total = u0;
@@ -409,32 +533,36 @@ void scheduler(s7_server* S) {
     if (!starting.empty()) {
       int nbs = 0, ubs = 0;
       size_t sms = 0;
-      if (layout(starting, hds, S->d_desc_start, &nbs, &ubs, &sms) != cudaSuccess) rc = S7_ECUDA;
-      if (!rc && sms > smem_max) {
-        smem_max = sms;
-        rc = eng->batched_prepare(smem_max);
+      const int ps = pipe_of(starting);
+      if (layout(starting, hds, S->d_desc_start, &nbs, &ubs, &sms, ps) != cudaSuccess) rc = S7_ECUDA;
+      if (!rc && sms > smem_max[ps]) {
+        smem_max[ps] = sms;
+        rc = eng->batched_prepare(smem_max[ps], ps);
       }
       if (!rc) rc = eng->launch_batched(2, S->d_desc_start, (int)starting.size(), nbs,
-                                        S->o.threads, sms, S->st);
-      if (!rc) rc = eng->launch_batched(5, S->d_desc_start, (int)starting.size(), 0, 0, 0, S->st);
+                                        S->o.threads, sms, S->st, ps);
+      if (!rc) rc = eng->launch_batched(5, S->d_desc_start, (int)starting.size(), 0, 0, 0, S->st, ps);
       for (Req* r : starting) r->state = INNER;
     }
+    const int pipe = pipe_of(inner);
     if (!rc) {
       // the membership changes as requests start and finish inner solves:
       // lay the batch out again every tick (a few hundred bytes per request)
       size_t sm = 0;
-      if (layout(inner, hd, S->d_desc, &sweep_blocks, &upd_blocks, &sm) != cudaSuccess) rc = S7_ECUDA;
-      if (!rc && sm > smem_max) {
-        smem_max = sm;
-        rc = eng->batched_prepare(smem_max);
+      if (layout(inner, hd, S->d_desc, &sweep_blocks, &upd_blocks, &sm, pipe) != cudaSuccess)
+        rc = S7_ECUDA;
+      if (!rc && sm > smem_max[pipe]) {
+        smem_max[pipe] = sm;
+        rc = eng->batched_prepare(smem_max[pipe], pipe);
       }
     }
     for (int k = 0; k < K && !rc; ++k) {
       rc = eng->launch_batched(0, S->d_desc, (int)inner.size(), sweep_blocks, S->o.threads,
-                               smem_max, S->st);
+                               smem_max[pipe], S->st, pipe);
       if (!rc) rc = eng->launch_batched(1, S->d_desc, (int)inner.size(), sweep_blocks,
-                                        S->o.threads, smem_max, S->st);
-      if (!rc) rc = eng->launch_batched(4, S->d_desc, (int)inner.size(), upd_blocks, 256, 0, S->st);
+                                        S->o.threads, smem_max[pipe], S->st, pipe);
+      if (!rc) rc = eng->launch_batched(4, S->d_desc, (int)inner.size(), upd_blocks, 256, 0, S->st,
+                                        pipe);
     }
     if (!rc && (cudaMemcpyAsync(S->h_sc, S->d_sc, (size_t)S->o.max_active * sizeof(Scalars),
                                 cudaMemcpyDeviceToHost, S->st) != cudaSuccess ||
@@ -450,7 +578,7 @@ void scheduler(s7_server* S) {
       if (r->state == INNER && S->h_sc[r->slot].done) {
         const Scalars& sc = S->h_sc[r->slot];
         r->inner_total += sc.iter;
-        S->cell_iters += (double)r->n * sc.iter;
+        S->cell_iters += (double)r->n_in * sc.iter;
         if (sc.status == S7_EBREAKDOWN && sc.iter == 0) {
           finish(S, r, S7_EBREAKDOWN);
           continue;
@@ -552,8 +680,12 @@ extern "C" int s7_server_submit(s7_server_t S, const s7_request* r, uint64_t* id
   Req* q = new (std::nothrow) Req();
   if (!q) return set_error(S7_ENOMEM, "s7_server_submit: host allocation failed");
   q->in = *r;
-  q->n = (long long)r->nx * r->ny * r->nz;
-  q->bytes = request_bytes(S, q->n);
+  // per-cell operators are held with whole wide vectors per row
+  const int vw = S->eng->vec_wide;
+  q->nxp = r->coeffs.constant ? r->nx : (r->nx + vw - 1) / vw * vw;
+  q->n_in = (long long)r->nx * r->ny * r->nz;
+  q->n = (long long)q->nxp * r->ny * r->nz;
+  q->bytes = request_bytes(S, q->n, r->coeffs.dtype == S7_F64 ? 8 : 4);
   if (q->bytes > S->o.hbm_budget_bytes) {
     delete q;
     return set_error(S7_ENOMEM, "s7_server_submit: request larger than the memory budget");

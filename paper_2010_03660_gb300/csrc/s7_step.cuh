@@ -194,12 +194,13 @@ __host__ __device__ inline size_t step_smem_bytes(int bx, int by, int stages, in
   }
 }
 
+// Block `bid` of the `nblocks` blocks of one pipelined sweep over the mesh
+// `g` (s7_smem: the dynamic shared memory; red: 128 doubles of reduction
+// scratch).  The caller has checked the stop flag.
 template <class T, class A, int VEC, int KIND, int STAGES>
-__global__ void __launch_bounds__(256) k_step(Geom g, StepArgs<T> a, Scalars* sc) {
-  extern __shared__ __align__(16) unsigned char s7_smem[];
-  __shared__ double red[32 * 4];
-  if (*((volatile int*)&sc->done)) return;
-
+__device__ __forceinline__ void step_body(const Geom& g, const StepArgs<T>& a, Scalars* sc,
+                                          int bid, int nb_total, unsigned char* s7_smem,
+                                          double* red) {
   typedef typename IterOf<T>::t X;
   const int it = sc->iter;
   const bool odd = (it & 1) != 0;
@@ -228,7 +229,6 @@ __global__ void __launch_bounds__(256) k_step(Geom g, StepArgs<T> a, Scalars* sc
   const bool has_cell = t < g.bx * g.by;
   const int tx = has_cell ? t % g.bx : 0;
   const int ty = has_cell ? t / g.bx : 0;
-  const int bid = blockIdx.x;
   const int tile_x = bid % g.tiles_x;
   const int rest = bid / g.tiles_x;
   const int tile_y = rest % g.tiles_y;
@@ -519,7 +519,6 @@ __global__ void __launch_bounds__(256) k_step(Geom g, StepArgs<T> a, Scalars* sc
   }
   cp_async_wait<0>();
   acc.fold();
-  const int nb_total = s7_nblocks(g);
   if constexpr (KIND >= 2) {
     double v[3] = {acc.tot[0], acc.tot[1], acc.tot[I2]}, tot[3];
     block_sum<3>(v, red);
@@ -560,6 +559,14 @@ __global__ void __launch_bounds__(256) k_step(Geom g, StepArgs<T> a, Scalars* sc
       }
     }
   }
+}
+
+template <class T, class A, int VEC, int KIND, int STAGES>
+__global__ void __launch_bounds__(256) k_step(Geom g, StepArgs<T> a, Scalars* sc) {
+  extern __shared__ __align__(16) unsigned char s7_smem[];
+  __shared__ double red[32 * 4];
+  if (*((volatile int*)&sc->done)) return;
+  step_body<T, A, VEC, KIND, STAGES>(g, a, sc, blockIdx.x, s7_nblocks(g), s7_smem, red);
 }
 
 }  // namespace s7

@@ -85,8 +85,9 @@ def test_alone_and_in_the_mix(s7):
 def test_admission_respects_budget(s7):
     probs = problems(700)
     sizes = [p.n for p in probs]
-    # about two average requests fit at once
-    per_cell = 6 * 2 + 4 + 28 + 7 * 2 + 8 + 24 + 28
+    # about two average requests fit at once (bytes per held cell as the
+    # server counts them: bf16 storage, float32 raw coefficients)
+    per_cell = 6 * 2 + 4 + 28 + 7 * 2 + 8 + 24 + 32
     budget = int(2.2 * np.mean(sizes) * per_cell) + (4 << 20)
     budget = max(budget, int(max(sizes) * per_cell) + (2 << 20))
     with s7.Server(storage="bf16", hbm_budget_bytes=budget) as srv:
