@@ -100,6 +100,8 @@ def parse():
                     help="speedup: storage of the served form")
     ap.add_argument("--serve-inner-tol", type=float, default=0.0,
                     help="speedup: inner tolerance of the served form (0 = server default)")
+    ap.add_argument("--serve-three-pass", action="store_true",
+                    help="speedup/serve: inner steps as Algorithm 1's three passes")
     ap.add_argument("--nx", type=int, default=600)
     ap.add_argument("--ny", type=int, default=595)
     ap.add_argument("--nz", type=int, default=1536)
@@ -764,7 +766,7 @@ def run_speedup(args):
 
     def served():
         with s7.Server(storage=args.serve_storage, hbm_budget_bytes=150 << 30,
-                       inner_tol=args.serve_inner_tol) as srv:
+                       inner_tol=args.serve_inner_tol, three_pass=args.serve_three_pass) as srv:
             xs = [torch.empty(nx * ny * nz, dtype=torch.float64).pin_memory()
                   for nx, ny, nz, _, _ in pool]
             ids = [srv.submit(nx, ny, nz, coef, b, x, 1e-8)

@@ -326,6 +326,9 @@ typedef struct {
   double inner_tol;        /* inner relative residual; 0 = 1e-2                    */
   int inner_maxit;         /* steps per inner solve; 0 = 100                       */
   int max_outer;           /* refinement steps; 0 = 60                             */
+  int three_pass;          /* 1: inner steps as Algorithm 1 prints them (three
+                              passes); 0: two reductions per step (s7_opts.variant
+                              1), the default                                      */
 } s7_server_opts;
 
 typedef struct {

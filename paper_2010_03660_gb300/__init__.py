@@ -88,7 +88,8 @@ class s7_batch_opts(C.Structure):
 class s7_server_opts(C.Structure):
     _fields_ = [("hbm_budget_bytes", C.c_size_t), ("storage", C.c_int), ("max_active", C.c_int),
                 ("steps_per_tick", C.c_int), ("threads", C.c_int), ("zchunk", C.c_int),
-                ("inner_tol", C.c_double), ("inner_maxit", C.c_int), ("max_outer", C.c_int)]
+                ("inner_tol", C.c_double), ("inner_maxit", C.c_int), ("max_outer", C.c_int),
+                ("three_pass", C.c_int)]
 
 
 class s7_request(C.Structure):
@@ -501,19 +502,23 @@ def _result_dict(r):
 
 
 def s7_server_create(hbm_budget_bytes=0, storage="bf16", max_active=0, steps_per_tick=0,
-                     threads=0, zchunk=0, inner_tol=0.0, inner_maxit=0, max_outer=0):
+                     threads=0, zchunk=0, inner_tol=0.0, inner_maxit=0, max_outer=0,
+                     three_pass=False):
     st = _STORAGE[storage] if isinstance(storage, str) else int(storage)
     o = s7_server_opts(int(hbm_budget_bytes), st, max_active, steps_per_tick, threads, zchunk,
-                       float(inner_tol), inner_maxit, max_outer)
+                       float(inner_tol), inner_maxit, max_outer, 1 if three_pass else 0)
     h = C.c_void_p()
     _check(lib().s7_server_create(C.byref(h), C.byref(o)))
     return h
 
 
 def s7_server_submit(srv, nx, ny, nz, coef, b, x, tol):
+    """Queue a request.  ``coef`` holds arrays of nx*ny*nz values, or of one
+    value each for a constant-coefficient operator."""
     names = ("diag",) + DIRS
     raw_dt = _dtype_code(coef["diag"])
-    cs = s7_coeffs(*[_ptr(coef[k]) for k in names], raw_dt, 0)
+    constant = 1 if nx * ny * nz > 1 and all(_numel(coef[k]) == 1 for k in names) else 0
+    cs = s7_coeffs(*[_ptr(coef[k]) for k in names], raw_dt, constant)
     req = s7_request(nx, ny, nz, cs, _ptr(b), _ptr(x), _dtype_code(b), float(tol))
     rid = C.c_uint64()
     _check(lib().s7_server_submit(srv, C.byref(req), C.byref(rid)))

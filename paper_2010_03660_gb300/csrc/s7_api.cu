@@ -1151,9 +1151,9 @@ struct BatchBuffers {
 static int batch_layout(int nsys, Handle* const* hs, const void* const* bdev, const Engine* eng,
                         const BatchPolicy& p, BatchBuffers& bb, const std::vector<size_t>& hist_off,
                         const std::vector<size_t>& parts_off, int* sweep_blocks, int* upd_blocks,
-                        size_t* smem, int pipe, cudaStream_t st) {
+                        size_t smem[4], int pipe, cudaStream_t st) {
   int b0 = 0, u0 = 0;
-  size_t sm = 0;
+  for (int k = 0; k < 4; ++k) smem[k] = 0;
   for (int j = 0; j < nsys; ++j) {
     const Tile t = batch_tile(hs[j], pipe ? eng->vec_wide : eng->vec, p);
     int nb = 0, ub = 0;
@@ -1162,11 +1162,10 @@ static int batch_layout(int nsys, Handle* const* hs, const void* const* bdev, co
                    pipe);
     b0 += nb;
     u0 += ub;
-    sm = std::max(sm, eng->batched_smem(hs[j], t, pipe));
+    for (int k = 0; k < 4; ++k) smem[k] = std::max(smem[k], eng->batched_smem(hs[j], t, pipe, k));
   }
   *sweep_blocks = b0;
   *upd_blocks = u0;
-  *smem = sm;
   CK(cudaMemcpyAsync(bb.desc, bb.h_desc.data(), (size_t)nsys * eng->desc_size,
                      cudaMemcpyHostToDevice, st));
   return S7_OK;
@@ -1219,7 +1218,7 @@ extern "C" int bicgstab_solve_batched(int nsys, const stencil7_t* hs_in, const v
   size_t hist_total = 0, parts_total = 0;
   long long cells = 0;
   int sweep_blocks = 0, upd_blocks = 0, threads = 128;
-  size_t smem = 0;
+  size_t smem[4] = {0, 0, 0, 0};  // by launch kind
   BatchPolicy pol{128, 16};
   const int ce = opts.check_every > 0 ? opts.check_every : 16;
   cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
@@ -1303,14 +1302,14 @@ extern "C" int bicgstab_solve_batched(int nsys, const stencil7_t* hs_in, const v
         for (int zi = 0; zi < 3; ++zi) {
           BatchPolicy c{cand_t[ti], cand_z[zi]};
           if ((rc = batch_layout(nsys, hs.data(), bdev.data(), eng, c, bb, hist_off, parts_off,
-                                 &sweep_blocks, &upd_blocks, &smem, pipe, st)))
+                                 &sweep_blocks, &upd_blocks, smem, pipe, st)))
             goto tune_out;
-          if (eng->batched_prepare(smem, pipe)) { rc = fail(S7_ECUDA, "batched kernel attributes"); goto tune_out; }
+          if (eng->batched_prepare(*std::max_element(smem, smem + 4), pipe)) { rc = fail(S7_ECUDA, "batched kernel attributes"); goto tune_out; }
           // warm, then time two probes
-          if ((rc = eng->launch_batched(3, bb.desc, nsys, sweep_blocks, c.threads, smem, st, pipe))) goto tune_out;
+          if ((rc = eng->launch_batched(3, bb.desc, nsys, sweep_blocks, c.threads, smem[3], st, pipe))) goto tune_out;
           cudaEventRecord(e0, st);
           for (int r = 0; r < 2 && rc == S7_OK; ++r)
-            rc = eng->launch_batched(3, bb.desc, nsys, sweep_blocks, c.threads, smem, st, pipe);
+            rc = eng->launch_batched(3, bb.desc, nsys, sweep_blocks, c.threads, smem[3], st, pipe);
           cudaEventRecord(e1, st);
           if (rc) goto tune_out;
           if ((e = cudaEventSynchronize(e1)) != cudaSuccess) { rc = cuda_fail(e, "autotune"); goto tune_out; }
@@ -1331,9 +1330,9 @@ extern "C" int bicgstab_solve_batched(int nsys, const stencil7_t* hs_in, const v
   }
   threads = pol.threads;
   if ((rc = batch_layout(nsys, hs.data(), bdev.data(), eng, pol, bb, hist_off, parts_off,
-                         &sweep_blocks, &upd_blocks, &smem, pipe, st)))
+                         &sweep_blocks, &upd_blocks, smem, pipe, st)))
     goto out;
-  if (eng->batched_prepare(smem, pipe)) { rc = fail(S7_ECUDA, "batched kernel attributes"); goto out; }
+  if (eng->batched_prepare(*std::max_element(smem, smem + 4), pipe)) { rc = fail(S7_ECUDA, "batched kernel attributes"); goto out; }
   // scalars: tol, maxit
   for (int j = 0; j < nsys; ++j) {
     Scalars& s = bb.h_sc[j];
@@ -1343,7 +1342,7 @@ extern "C" int bicgstab_solve_batched(int nsys, const stencil7_t* hs_in, const v
     s.status = S7_ENOTCONV;
   }
   if ((e = cudaMemcpyAsync(bb.sc, bb.h_sc, (size_t)nsys * sizeof(Scalars), cudaMemcpyHostToDevice, st)) != cudaSuccess) { rc = cuda_fail(e, "scalars"); goto out; }
-  if ((rc = eng->launch_batched(2, bb.desc, nsys, sweep_blocks, threads, smem, st, pipe)) ||
+  if ((rc = eng->launch_batched(2, bb.desc, nsys, sweep_blocks, threads, smem[2], st, pipe)) ||
       (rc = eng->launch_batched(5, bb.desc, nsys, 0, 0, 0, st, pipe))) {
     rc = fail(rc, "batched start launch failed: %s", cudaGetErrorString(cudaGetLastError()));
     goto out;
@@ -1353,8 +1352,8 @@ extern "C" int bicgstab_solve_batched(int nsys, const stencil7_t* hs_in, const v
     cudaGraph_t g = nullptr;
     if ((e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) { rc = cuda_fail(e, "capture"); goto out; }
     for (int k = 0; k < ce && rc == S7_OK; ++k) {
-      rc = eng->launch_batched(0, bb.desc, nsys, sweep_blocks, threads, smem, st, pipe);
-      if (!rc) rc = eng->launch_batched(1, bb.desc, nsys, sweep_blocks, threads, smem, st, pipe);
+      rc = eng->launch_batched(0, bb.desc, nsys, sweep_blocks, threads, smem[0], st, pipe);
+      if (!rc) rc = eng->launch_batched(1, bb.desc, nsys, sweep_blocks, threads, smem[1], st, pipe);
       if (!rc) rc = eng->launch_batched(4, bb.desc, nsys, upd_blocks, 256, 0, st, pipe);
     }
     e = cudaStreamEndCapture(st, &g);

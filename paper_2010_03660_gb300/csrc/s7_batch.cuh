@@ -32,6 +32,7 @@ struct SysDesc {
   const void* d;     // kept diagonal for b~ = D^-1 b (NULL: constant cdiv)
   double cdiv;       // constant divisor when d is NULL
   T* r;
+  T* r2;             // second r buffer (two-reduction variant) or NULL
   T* rh;
   T* p[2];
   T* s[2];
@@ -128,10 +129,10 @@ __global__ void __launch_bounds__(256) k_sweep_batched(const SysDesc<T, X>* __re
   }
 }
 
-// The pipelined sweeps (kinds 0, 1 of s7_step.cuh) over a batch whose
+// The pipelined sweeps (kinds 0-3 of s7_step.cuh) over a batch whose
 // systems all qualify (Jacobi-scaled per-cell operators, rows of whole
 // VEC-cell vectors); each system's geometry in its descriptor is for VEC
-// cells per thread.
+// cells per thread.  Kinds 2 and 3 (the two-reduction variant) need r2.
 template <class T, class X, class A, int VEC, int KIND, int STAGES>
 __global__ void __launch_bounds__(256) k_step_batched(const SysDesc<T, X>* __restrict__ sys,
                                                       int nsys) {
@@ -153,7 +154,7 @@ __global__ void __launch_bounds__(256) k_step_batched(const SysDesc<T, X>* __res
   a.y = d.y;
   a.parts = d.parts;
   a.rbuf[0] = d.r;
-  a.rbuf[1] = d.r;
+  a.rbuf[1] = d.r2;
   a.x = d.x;
   a.hist = d.hist;
   step_body<T, A, VEC, KIND, STAGES>(d.g, a, d.sc, (int)blockIdx.x - d.block0, d.nblocks, s7_smem,

@@ -819,6 +819,7 @@ struct EngineImpl {
     d.cdiv = (h->jacobi && h->constant) ? h->cconst[6] : 1.0;
     const Workspace& w = h->ws;
     d.r = (T*)w.r;
+    d.r2 = (T*)w.r2;
     d.rh = (T*)w.rh;
     d.p[0] = (T*)w.p[0];
     d.p[1] = (T*)w.p[1];
@@ -835,15 +836,18 @@ struct EngineImpl {
     *unb = d.unblocks;
   }
 
-  static size_t batched_smem(const Handle* h, const Tile& t, int pipe) {
+  static size_t batched_smem(const Handle* h, const Tile& t, int pipe, int kind) {
     const int v = pipe ? VW : VEC;
     const Geom g = geom_tile(h, t, v);
-    size_t m = (size_t)3 * (g.by + 2) * (g.bx * v + 2 * v) * sizeof(A);
-    if (pipe) {
-      m = std::max(m, step_smem_bytes<T, A, VW>(g.bx, g.by, SB, 0));
-      if (kPipeQ) m = std::max(m, step_smem_bytes<T, A, VW>(g.bx, g.by, SB, 1));
+    const size_t reg = (size_t)3 * (g.by + 2) * (g.bx * v + 2 * v) * sizeof(A);
+    if (!pipe) return reg;
+    switch (kind) {
+      case 0: return step_smem_bytes<T, A, VW>(g.bx, g.by, SB, 0);
+      case 1: return kPipeQ ? step_smem_bytes<T, A, VW>(g.bx, g.by, SB, 1) : reg;
+      case 6: return step_smem_bytes<T, A, VW>(g.bx, g.by, SB, 2);
+      case 7: return step_smem_bytes<T, A, VW>(g.bx, g.by, SB, 3);
+      default: return reg;
     }
-    return m;
   }
 
   static int batched_prepare(size_t smem, int pipe) {
@@ -852,13 +856,15 @@ struct EngineImpl {
                           (const void*)k_sweep_batched<T, X, DT, A, VEC, 1>,
                           (const void*)k_sweep_batched<T, X, DT, A, VEC, 2>,
                           (const void*)k_sweep_batched<T, X, DT, A, VEC, 3>};
-    const void* wide[5] = {(const void*)k_step_batched<T, X, A, VW, 0, SB>,
+    const void* wide[7] = {(const void*)k_step_batched<T, X, A, VW, 0, SB>,
                            (const void*)k_step_batched<T, X, A, VW, 1, SB>,
+                           (const void*)k_step_batched<T, X, A, VW, 2, SB>,
+                           (const void*)k_step_batched<T, X, A, VW, 3, SB>,
                            (const void*)k_sweep_batched<T, X, DT, A, VW, 1>,
                            (const void*)k_sweep_batched<T, X, DT, A, VW, 2>,
                            (const void*)k_sweep_batched<T, X, DT, A, VW, 3>};
     const void* const* ks = pipe ? wide : reg;
-    const int nk = pipe ? 5 : 4;
+    const int nk = pipe ? 7 : 4;
     for (int k = 0; k < nk; ++k)
       if (cudaFuncSetAttribute(ks[k], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
           cudaSuccess)
@@ -869,9 +875,12 @@ struct EngineImpl {
   static int launch_batched(int kind, const void* descs, int nsys, int blocks, int threads,
                             size_t smem, cudaStream_t st, int pipe) {
     const Desc* d = (const Desc*)descs;
-    if (pipe && kind <= 3) {
+    if (kind >= 6 && !pipe) return S7_EINVAL;
+    if (pipe && (kind <= 3 || kind >= 6)) {
       switch (kind) {
         case 0: k_step_batched<T, X, A, VW, 0, SB><<<blocks, threads, smem, st>>>(d, nsys); break;
+        case 6: k_step_batched<T, X, A, VW, 2, SB><<<blocks, threads, smem, st>>>(d, nsys); break;
+        case 7: k_step_batched<T, X, A, VW, 3, SB><<<blocks, threads, smem, st>>>(d, nsys); break;
         case 1:
           if (kPipeQ) k_step_batched<T, X, A, VW, 1, SB><<<blocks, threads, smem, st>>>(d, nsys);
           else k_sweep_batched<T, X, DT, A, VW, 1><<<blocks, threads, smem, st>>>(d, nsys);

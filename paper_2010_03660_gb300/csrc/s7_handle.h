@@ -128,8 +128,11 @@ struct Engine {
   void (*fill_desc)(Handle* h, void* desc, const Tile& t, const void* b, double* parts,
                     double* hist, Scalars* sc, int block0, int ublock0, int* nblocks,
                     int* unblocks, int pipe);
-  size_t (*batched_smem)(const Handle* h, const Tile& t, int pipe);
-  // kind 0..3: batched sweeps (see s7_batch.cuh), 4: update, 5: history start
+  // dynamic shared memory of launch kind `kind` for system h
+  size_t (*batched_smem)(const Handle* h, const Tile& t, int pipe, int kind);
+  // kind 0..3: batched sweeps (see s7_batch.cuh), 4: update, 5: history
+  // start; pipelined batches only: 6 = q/y pass and 7 = fused pass of the
+  // two-reduction variant (systems created with variant 1)
   int (*launch_batched)(int kind, const void* descs, int nsys, int blocks, int threads,
                         size_t smem, cudaStream_t st, int pipe);
   int (*batched_prepare)(size_t smem, int pipe);

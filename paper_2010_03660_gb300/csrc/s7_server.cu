@@ -21,12 +21,14 @@
 // reductions, a fixed tile policy), so its result does not depend on what
 // else was running.
 //
-// A request with per-cell coefficients is held with its x extent padded to
-// a multiple of the engine's wide vector: padding cells have a unit
-// diagonal, no couplings and a zero right-hand side, so every vector stays
-// exactly zero there and the solution on the real cells is unchanged.  With
-// all rows made of whole vectors, the batch's step sweeps run the
-// cp.async-pipelined bodies.
+// Every request is held with per-cell coefficient arrays (constants are
+// expanded) and its x extent padded to a multiple of the engine's wide
+// vector: padding cells have a unit diagonal, no couplings and a zero
+// right-hand side, so every vector stays exactly zero there and the solution
+// on the real cells is unchanged.  With all rows made of whole vectors, the
+// batch's step sweeps run the cp.async-pipelined bodies; by default the
+// inner solves take two reductions per step (a q/y pass and a fused pass,
+// s7_opts.variant 1) after a first p/s pass at their start.
 #include <math.h>
 #include <string.h>
 
@@ -76,6 +78,17 @@ __global__ void k_pad(long long rows, int nx, int nxp, const V* __restrict__ src
     const long long row = i / nxp;
     const int x = (int)(i - row * nxp);
     dst[i] = x < nx ? src[row * nx + x] : fill;
+  }
+}
+
+// dst (rows of nxp) holding `v` on the real cells and `fill` in the padding.
+template <class V>
+__global__ void k_const_pad(long long rows, int nx, int nxp, V v, V* __restrict__ dst, V fill) {
+  const long long n = rows * nxp;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long row = i / nxp;
+    dst[i] = (i - row * nxp) < nx ? v : fill;
   }
 }
 
@@ -159,11 +172,13 @@ namespace {
 
 size_t request_bytes(const s7_server* S, long long n, int raw_size) {
   // stored operator, kept diagonal, true float32 operator, seven Krylov
-  // vectors, x and b in float32, three float64 refinement vectors, and the
-  // staging of the raw coefficients (seven arrays and one more while a
-  // padded operator is formed) while the operator is created
+  // vectors (eight with the two-reduction variant's second r), x and b in
+  // float32, three float64 refinement vectors, and the staging of the raw
+  // coefficients (seven arrays and one more while a padded operator is
+  // formed) while the operator is created
   const size_t ts = S->eng->t_size;
-  return (size_t)n * (6 * ts + 4 + 28 + 7 * ts + 8 + 24 + 8 * (size_t)raw_size) + (1 << 20);
+  const size_t vecs = S->o.three_pass ? 7 : 8;
+  return (size_t)n * (6 * ts + 4 + 28 + vecs * ts + 8 + 24 + 8 * (size_t)raw_size) + (1 << 20);
 }
 
 Tile serve_tile(const s7_server* S, int nx, int ny, int nz, int pipe) {
@@ -245,7 +260,28 @@ int create_padded(s7_server* S, Req* r, const s7_opts* oo) {
   cudaError_t e = cudaSuccess;
   for (int d = 0; d < 7 && e == cudaSuccess; ++d) {
     dst[d] = buf + d * n * es;
-    e = pad_in(dst[d], src[d], tmp, r->in.nx, r->nxp, rows, es, d == 6 ? 1.0 : 0.0, as);
+    const double fill = d == 6 ? 1.0 : 0.0;
+    if (!c.constant) {
+      e = pad_in(dst[d], src[d], tmp, r->in.nx, r->nxp, rows, es, fill, as);
+      continue;
+    }
+    // a constant operator: one value per array, expanded to the cells
+    double v = 0.0;
+    if (es == 8) {
+      e = cudaMemcpy(&v, src[d], 8, cudaMemcpyDefault);
+    } else {
+      float f = 0.f;
+      e = cudaMemcpy(&f, src[d], 4, cudaMemcpyDefault);
+      v = f;
+    }
+    if (e != cudaSuccess) break;
+    if (es == 8)
+      k_const_pad<double><<<grid_of(n), 256, 0, as>>>(rows, r->in.nx, r->nxp, v, (double*)dst[d],
+                                                      fill);
+    else
+      k_const_pad<float><<<grid_of(n), 256, 0, as>>>(rows, r->in.nx, r->nxp, (float)v,
+                                                     (float*)dst[d], (float)fill);
+    e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(as);
   int rc = S7_OK;
@@ -254,6 +290,7 @@ int create_padded(s7_server* S, Req* r, const s7_opts* oo) {
     rc = S7_ECUDA;
   } else {
     s7_coeffs pc = c;
+    pc.constant = 0;
     pc.xm = dst[0];
     pc.xp = dst[1];
     pc.ym = dst[2];
@@ -273,7 +310,8 @@ int admit(s7_server* S, Req* r) {
   memset(&oo, 0, sizeof oo);
   oo.storage = S->o.storage;
   oo.keep_true = 1;
-  int rc = r->nxp != r->in.nx
+  oo.variant = S->o.three_pass ? 0 : 1;
+  int rc = (r->nxp != r->in.nx || r->in.coeffs.constant)
                ? create_padded(S, r, &oo)
                : stencil7_create(&r->h, r->in.nx, r->in.ny, r->in.nz, &r->in.coeffs, &oo);
   if (rc) return rc;
@@ -509,10 +547,10 @@ void scheduler(s7_server* S) {
       return p;
     };
     auto layout = [&](const std::vector<Req*>& set, std::vector<unsigned char>& host, void* dev,
-                      int* nb_total, int* ub_total, size_t* smem, int pipe) {
+                      int* nb_total, int* ub_total, size_t smem[8], int pipe) {
       host.resize(set.size() * eng->desc_size);
       int b0 = 0, u0 = 0;
-      size_t sm = 0;
+      for (int k = 0; k < 8; ++k) smem[k] = 0;
       for (size_t j = 0; j < set.size(); ++j) {
         Req* r = set[j];
         const Tile t = serve_tile(S, r->nxp, r->in.ny, r->in.nz, pipe);
@@ -522,47 +560,62 @@ void scheduler(s7_server* S) {
                        b0, u0, &nb, &ub, pipe);
         b0 += nb;
         u0 += ub;
-        sm = std::max(sm, eng->batched_smem(r->h, t, pipe));
+        for (int k = 0; k < 8; ++k)
+          if (k != 4 && k != 5) smem[k] = std::max(smem[k], eng->batched_smem(r->h, t, pipe, k));
       }
       *nb_total = b0;
       *ub_total = u0;
-      *smem = sm;
       return cudaMemcpyAsync(dev, host.data(), host.size(), cudaMemcpyHostToDevice, S->st);
     };
+    // kernel attributes: dynamic shared memory up to the largest seen
+    auto prepare = [&](const size_t sm[8], int pipe) {
+      const size_t m = *std::max_element(sm, sm + 8);
+      if (m <= smem_max[pipe]) return S7_OK;
+      smem_max[pipe] = m;
+      return eng->batched_prepare(m, pipe);
+    };
+    const bool merged = !S->o.three_pass;
     int rc = S7_OK;
     if (!starting.empty()) {
       int nbs = 0, ubs = 0;
-      size_t sms = 0;
+      size_t sms[8];
       const int ps = pipe_of(starting);
-      if (layout(starting, hds, S->d_desc_start, &nbs, &ubs, &sms, ps) != cudaSuccess) rc = S7_ECUDA;
-      if (!rc && sms > smem_max[ps]) {
-        smem_max[ps] = sms;
-        rc = eng->batched_prepare(smem_max[ps], ps);
-      }
+      if (merged && !ps) rc = S7_EINVAL;   // held operators always qualify
+      if (!rc && layout(starting, hds, S->d_desc_start, &nbs, &ubs, sms, ps) != cudaSuccess)
+        rc = S7_ECUDA;
+      if (!rc) rc = prepare(sms, ps);
       if (!rc) rc = eng->launch_batched(2, S->d_desc_start, (int)starting.size(), nbs,
-                                        S->o.threads, sms, S->st, ps);
+                                        S->o.threads, sms[2], S->st, ps);
       if (!rc) rc = eng->launch_batched(5, S->d_desc_start, (int)starting.size(), 0, 0, 0, S->st, ps);
+      // the two-reduction variant starts with s_0 = A p_0 and (r0, s_0)
+      if (!rc && merged)
+        rc = eng->launch_batched(0, S->d_desc_start, (int)starting.size(), nbs, S->o.threads,
+                                 sms[0], S->st, ps);
       for (Req* r : starting) r->state = INNER;
     }
     const int pipe = pipe_of(inner);
+    if (!rc && merged && !pipe) rc = S7_EINVAL;
+    size_t smi[8];
     if (!rc) {
       // the membership changes as requests start and finish inner solves:
       // lay the batch out again every tick (a few hundred bytes per request)
-      size_t sm = 0;
-      if (layout(inner, hd, S->d_desc, &sweep_blocks, &upd_blocks, &sm, pipe) != cudaSuccess)
+      if (layout(inner, hd, S->d_desc, &sweep_blocks, &upd_blocks, smi, pipe) != cudaSuccess)
         rc = S7_ECUDA;
-      if (!rc && sm > smem_max[pipe]) {
-        smem_max[pipe] = sm;
-        rc = eng->batched_prepare(smem_max[pipe], pipe);
-      }
+      if (!rc) rc = prepare(smi, pipe);
     }
     for (int k = 0; k < K && !rc; ++k) {
-      rc = eng->launch_batched(0, S->d_desc, (int)inner.size(), sweep_blocks, S->o.threads,
-                               smem_max[pipe], S->st, pipe);
-      if (!rc) rc = eng->launch_batched(1, S->d_desc, (int)inner.size(), sweep_blocks,
-                                        S->o.threads, smem_max[pipe], S->st, pipe);
-      if (!rc) rc = eng->launch_batched(4, S->d_desc, (int)inner.size(), upd_blocks, 256, 0, S->st,
-                                        pipe);
+      const int n_in = (int)inner.size();
+      if (merged) {
+        rc = eng->launch_batched(6, S->d_desc, n_in, sweep_blocks, S->o.threads, smi[6], S->st,
+                                 pipe);
+        if (!rc) rc = eng->launch_batched(7, S->d_desc, n_in, sweep_blocks, S->o.threads, smi[7],
+                                          S->st, pipe);
+        continue;
+      }
+      rc = eng->launch_batched(0, S->d_desc, n_in, sweep_blocks, S->o.threads, smi[0], S->st, pipe);
+      if (!rc) rc = eng->launch_batched(1, S->d_desc, n_in, sweep_blocks, S->o.threads, smi[1],
+                                        S->st, pipe);
+      if (!rc) rc = eng->launch_batched(4, S->d_desc, n_in, upd_blocks, 256, 0, S->st, pipe);
     }
     if (!rc && (cudaMemcpyAsync(S->h_sc, S->d_sc, (size_t)S->o.max_active * sizeof(Scalars),
                                 cudaMemcpyDeviceToHost, S->st) != cudaSuccess ||
@@ -680,9 +733,9 @@ extern "C" int s7_server_submit(s7_server_t S, const s7_request* r, uint64_t* id
   Req* q = new (std::nothrow) Req();
   if (!q) return set_error(S7_ENOMEM, "s7_server_submit: host allocation failed");
   q->in = *r;
-  // per-cell operators are held with whole wide vectors per row
+  // operators are held per cell, with whole wide vectors per row
   const int vw = S->eng->vec_wide;
-  q->nxp = r->coeffs.constant ? r->nx : (r->nx + vw - 1) / vw * vw;
+  q->nxp = (r->nx + vw - 1) / vw * vw;
   q->n_in = (long long)r->nx * r->ny * r->nz;
   q->n = (long long)q->nxp * r->ny * r->nz;
   q->bytes = request_bytes(S, q->n, r->coeffs.dtype == S7_F64 ? 8 : 4);

@@ -86,8 +86,9 @@ def test_admission_respects_budget(s7):
     probs = problems(700)
     sizes = [p.n for p in probs]
     # about two average requests fit at once (bytes per held cell as the
-    # server counts them: bf16 storage, float32 raw coefficients)
-    per_cell = 6 * 2 + 4 + 28 + 7 * 2 + 8 + 24 + 32
+    # server counts them: bf16 storage, eight Krylov vectors, float32 raw
+    # coefficients)
+    per_cell = 6 * 2 + 4 + 28 + 8 * 2 + 8 + 24 + 32
     budget = int(2.2 * np.mean(sizes) * per_cell) + (4 << 20)
     budget = max(budget, int(max(sizes) * per_cell) + (2 << 20))
     with s7.Server(storage="bf16", hbm_budget_bytes=budget) as srv:
@@ -114,3 +115,29 @@ def test_bounded_wait_and_cancel(s7):
     others = [submit(srv, p, 1e-10) for _ in range(3)]
     srv.close()                              # running and queued requests are cancelled
     assert others
+
+
+@pytest.mark.parametrize("three_pass", [False, True])
+def test_constant_and_padded_requests_both_forms(s7, three_pass):
+    """A constant-coefficient request (expanded to per-cell arrays) and
+    requests whose x extent is padded to whole vectors, with the inner steps
+    in either form: each meets its tolerance on the true operator, and the
+    padding leaves the solution on the real cells unchanged (oracle)."""
+    cases = [synth.convdiff_constant(21, 13, 17, seed=0, dtype=np.float32),
+             synth.varcoef(9, 31, 26, seed=901), synth.varcoef(35, 12, 30, seed=902)]
+    with s7.Server(storage="f16", three_pass=three_pass) as srv:
+        ids = []
+        for p in cases:
+            coef = p.coef
+            if p.constant:
+                coef = {k: np.array([v], dtype=np.float32) for k, v in p.coef.items()}
+            ids.append(srv.submit(p.nx, p.ny, p.nz, coef, p.b.astype(np.float64),
+                                  np.zeros(p.n, np.float64), 1e-8))
+        for rid, p in zip(ids, cases):
+            r = srv.wait(rid, timeout=120)
+            assert r["status"] == 0, r
+            x = srv.result(rid)
+            b = p.b.astype(np.float64)
+            assert ob.true_residual(p.nx, p.ny, p.nz, p.coef, b, x) <= 1.01e-8
+            ref = ob.bicgstab(p.nx, p.ny, p.nz, p.coef, b, tol=1e-12, maxit=3000)
+            assert np.linalg.norm(x - ref.x) / np.linalg.norm(ref.x) < 1e-5
