@@ -382,7 +382,9 @@ def run_ours(args):
         v["share"] = v["avg_ms"] * v["launches"] / tot_ms if tot_ms else None
     dom = max((k for k in kern if k in bpc),
               key=lambda k: kern[k]["avg_ms"] * kern[k]["launches"])
-    traffic = ncu_traffic(dom, n) if (args.storage == "f32" and args.variant == 0) else None
+    table = {"f32": "kernels", "bf16": "kernels_bf16"}.get(args.storage)
+    traffic = (ncu_traffic(dom, n, table) if table and args.variant == 0 and not args.stages
+               and not args.pipe_kinds and not args.step_cells else None)
     roofline = {"bound": "hbm", "kernel": dom, "achieved": kern[dom]["gbs"], "peak": peak,
                 "unit": "GB/s", "frac": kern[dom]["gbs"] / peak, "peak_kind": peak_kind,
                 "traffic": traffic}
