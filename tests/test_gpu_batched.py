@@ -12,6 +12,7 @@ import pytest
 
 import synth
 from oracle import bicgstab as ob
+from oracle import stencil
 from tests import gpu_util as gu
 
 pytestmark = pytest.mark.gpu
@@ -151,3 +152,59 @@ def test_config4_512_systems(s7):
         for op in ops:
             op.close()
         torch.cuda.empty_cache()
+
+
+def test_pipelined_batch_matches_register_batch(s7):
+    """A batch whose systems all have whole-vector rows runs the pipelined
+    step sweeps; one ragged system sends the whole batch to the register
+    sweeps.  In float32 the two give the same bits (same arithmetic and
+    order, 4 cells per thread either way)."""
+    aligned = [(16, 12, 20), (40, 31, 25), (64, 20, 12), (8, 8, 64)]
+    probs = make(aligned + [(17, 9, 33)], 500)
+    ops = [s7.stencil7_create(p.nx, p.ny, p.nz, gu.coef_on_device(p), storage="f32")
+           for p in probs]
+    try:
+        kw = dict(tol=1e-7, maxit=500, threads=128, zchunk=16)
+        piped = s7.bicgstab_solve_batched(ops[:4], [gu.to_dev(p.b) for p in probs[:4]], **kw)
+        mixed = s7.bicgstab_solve_batched(ops, [gu.to_dev(p.b) for p in probs], **kw)
+        assert all(s == 0 for s in piped.status)
+        for j in range(4):
+            assert piped.iters[j] == mixed.iters[j]
+            assert np.array_equal(piped.x[j].cpu().numpy(), mixed.x[j].cpu().numpy())
+            orc = ob.bicgstab(probs[j].nx, probs[j].ny, probs[j].nz, probs[j].coef, probs[j].b,
+                              tol=1e-7, maxit=500, storage="f32")
+            assert rel(piped.x[j].cpu().numpy(), orc.x) <= 1e-3
+    finally:
+        for op in ops:
+            op.close()
+
+
+@pytest.mark.parametrize("storage", ["bf16", "f16"])
+def test_pipelined_16bit_batch(s7, storage):
+    """16-bit batches with rows of whole 8-cell vectors run the 8-cell
+    pipelined sweeps; their results agree with the register sweeps of a
+    ragged batch to what the storage precision allows, and each system
+    meets its tolerance."""
+    aligned = [(16, 12, 20), (40, 31, 25), (64, 20, 12)]
+    probs = make(aligned + [(17, 9, 33)], 600)
+    ops = [s7.stencil7_create(p.nx, p.ny, p.nz, gu.coef_on_device(p), storage=storage)
+           for p in probs]
+    try:
+        kw = dict(tol=1e-2, maxit=300, threads=128, zchunk=16)
+        piped = s7.bicgstab_solve_batched(ops[:3], [gu.to_dev(p.b) for p in probs[:3]], **kw)
+        mixed = s7.bicgstab_solve_batched(ops, [gu.to_dev(p.b) for p in probs], **kw)
+        for j in range(3):
+            p = probs[j]
+            assert piped.status[j] == 0 and mixed.status[j] == 0
+            assert piped.resid[j] <= 1e-2
+            assert abs(piped.iters[j] - mixed.iters[j]) <= max(3, mixed.iters[j] // 4)
+            # the true residual of each x on the stored (scaled) operator
+            sc = stencil.jacobi_scale(p.nx, p.ny, p.nz, p.coef, storage)
+            bt = stencil.scale_rhs(p.nx, p.ny, p.nz, p.coef, p.b)
+            for res in (piped, mixed):
+                x = res.x[j].cpu().numpy().astype(np.float64)
+                tr = np.linalg.norm(bt - stencil.apply(p.nx, p.ny, p.nz, sc, x)) / np.linalg.norm(bt)
+                assert tr <= 3e-2, (j, tr)
+    finally:
+        for op in ops:
+            op.close()
