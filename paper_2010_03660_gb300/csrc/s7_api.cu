@@ -199,11 +199,13 @@ void default_tile9(int nx, int ny, int vec, int nsm, Tile* t) {
   const int runs = (nx + vec - 1) / vec;
   const int ntx = (runs + 127) / 128;
   const int bx = (runs + ntx - 1) / ntx;    // <= 128 runs per strip, balanced strips
-  // rows per block: about eight blocks per SM, long enough that the two
+  // rows per block: about 32 blocks per SM, so the last wave is a small
+  // fraction of the sweep (measured on 22800^2: 97.7% of the copy peak per
+  // step at ~200 rows against 92% at ~850), and at least 32 rows, so the two
   // extra rows each chunk reads stay a small fraction
-  const long long target = (long long)nsm * 8;
+  const long long target = (long long)nsm * 32;
   long long rc = ((long long)ntx * ny + target - 1) / target;
-  rc = std::max(8LL, std::min(4096LL, rc));
+  rc = std::max(32LL, std::min(4096LL, rc));
   if (rc > ny) rc = ny;
   t->bx = bx;
   t->by = 1;
