@@ -102,6 +102,8 @@ def parse():
                     help="speedup: inner tolerance of the served form (0 = server default)")
     ap.add_argument("--serve-three-pass", action="store_true",
                     help="speedup/serve: inner steps as Algorithm 1's three passes")
+    ap.add_argument("--serve-steps-per-tick", type=int, default=0,
+                    help="speedup: batched steps between the server's host checks (0 = default)")
     ap.add_argument("--nx", type=int, default=600)
     ap.add_argument("--ny", type=int, default=595)
     ap.add_argument("--nz", type=int, default=1536)
@@ -778,7 +780,8 @@ def run_speedup(args):
 
     def served():
         with s7.Server(storage=args.serve_storage, hbm_budget_bytes=150 << 30,
-                       inner_tol=args.serve_inner_tol, three_pass=args.serve_three_pass) as srv:
+                       inner_tol=args.serve_inner_tol, three_pass=args.serve_three_pass,
+                       steps_per_tick=args.serve_steps_per_tick) as srv:
             xs = [torch.empty(nx * ny * nz, dtype=torch.float64).pin_memory()
                   for nx, ny, nz, _, _ in pool]
             ids = [srv.submit(nx, ny, nz, coef, b, x, 1e-8)

@@ -20,18 +20,22 @@ typedef __half f16;
 // conversions (all rounding is round-to-nearest-even)
 // ---------------------------------------------------------------------------
 // binary32 -> binary64 is exact: for normal numbers it only re-biases the
-// exponent (127 -> 1023) and widens the significand, which integer
-// instructions do at full rate; zero, subnormals, infinities and NaN take the
-// hardware conversion.  GB300 runs float64 arithmetic (conversions included)
-// at a small fraction of its float32 rate, and the float64 residual sweeps
-// convert seven coefficients per cell.
+// exponent (127 -> 1023) and widens the significand, and a signed zero keeps
+// its sign bit alone, which integer instructions do at full rate; only
+// subnormals, infinities and NaN take the hardware conversion, on a branch
+// kept out of the common path.  GB300 runs float64 arithmetic (conversions
+// included) at a small fraction of its float32 rate, and the float64
+// residual sweeps convert seven coefficients per cell.
 __device__ __forceinline__ double f2d_exact(float v) {
   const unsigned int u = __float_as_uint(v);
   const unsigned int e = (u >> 23) & 0xffu;
-  if (e == 0u || e == 0xffu) return (double)v;
-  const unsigned long long bits = ((unsigned long long)(u >> 31) << 63) |
-                                  ((unsigned long long)(e + (1023u - 127u)) << 52) |
-                                  ((unsigned long long)(u & 0x7fffffu) << 29);
+  const unsigned int m = u & 0x7fffffu;
+  const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
+  if (__builtin_expect((e == 0u && m != 0u) || e == 0xffu, 0)) return (double)v;
+  const unsigned long long bits =
+      e == 0u ? sign
+              : sign | ((unsigned long long)(e + (1023u - 127u)) << 52) |
+                    ((unsigned long long)m << 29);
   return __longlong_as_double((long long)bits);
 }
 
