@@ -184,7 +184,10 @@ typedef struct {
 int stencil9_create(stencil7_t* out, int nx, int ny, const s9_coeffs* coeffs,
                     const s7_opts* opts);
 
-/* Release a handle and all device memory it owns.  NULL is accepted. */
+/* Release a handle and all device memory it owns (the blocks return to the
+ * library's memory pool, see s7_mem_trim).  Waits for all work queued on the
+ * handle's device first, including asynchronous stencil7_apply calls on the
+ * caller's streams.  NULL is accepted. */
 int stencil7_destroy(stencil7_t h);
 
 /* Mesh sizes, storage type and device bytes held by a handle. */
@@ -386,6 +389,30 @@ int s7_server_destroy(s7_server_t s);
  * true-residual sweep; everything else (casts, refinement kernels). */
 #define S7_PROF_NKINDS 6
 int stencil7_profile(stencil7_t h, int enable, double* ms, long long* launches);
+
+/* ---- device memory ----
+ * Handles take their device memory (operator arrays, Krylov vectors, staging
+ * buffers) from one stream-ordered CUDA memory pool per device that the
+ * library owns.  Blocks a destroyed handle gave back stay reserved in the
+ * pool, up to the cache limit, and a later handle reuses them without mapping
+ * memory again.  If the pool cannot grow, it first returns its cached blocks
+ * to the device and retries.  Other allocators (the caller's, PyTorch's)
+ * do not see the cached bytes as free: trim the pool or lower the limit when
+ * they need the memory. */
+
+/* Bytes the pool of `device` holds reserved, and of those the bytes in use
+ * by live handles (either pointer may be NULL).  S7_ECUDA for a bad device. */
+int s7_mem_stats(int device, size_t* reserved, size_t* used);
+
+/* Synchronise the current device and return the cached blocks of the pool
+ * of `device` to it, keeping at most `keep` reserved bytes (blocks in use
+ * stay).  S7_ECUDA for a bad device. */
+int s7_mem_trim(int device, size_t keep);
+
+/* Most bytes each pool keeps reserved after the synchronisation that
+ * follows a release (default 64 GiB; 0 returns every free block).  Applies
+ * to all devices' pools, present and future.  Always S7_OK. */
+int s7_mem_set_cache(size_t bytes);
 
 /* ---- thread-local error text ---- */
 const char* s7_last_error(void);

@@ -33,6 +33,7 @@ __all__ = [
     "bicgstab_solve_refined", "bicgstab_solve_batched", "stencil7_profile", "s7_last_error",
     "s7_version", "Server", "s7_server_create", "s7_server_submit", "s7_server_poll",
     "s7_server_wait", "s7_server_release", "s7_server_get_stats", "s7_server_destroy",
+    "s7_mem_stats", "s7_mem_trim", "s7_mem_set_cache",
 ]
 
 S7_F64, S7_F32, S7_BF16, S7_F16 = 0, 1, 2, 3
@@ -50,7 +51,8 @@ EXPORTS = (
     "stencil7_residual", "stencil7_residual_noalloc", "bicgstab_solve",
     "bicgstab_solve_refined", "bicgstab_solve_batched", "stencil7_profile", "s7_last_error",
     "s7_version", "s7_server_create", "s7_server_submit", "s7_server_poll", "s7_server_wait",
-    "s7_server_release", "s7_server_get_stats", "s7_server_destroy",
+    "s7_server_release", "s7_server_get_stats", "s7_server_destroy", "s7_mem_stats",
+    "s7_mem_trim", "s7_mem_set_cache",
 )
 PROF_KINDS = ("spmv_p_dot", "spmv_q_dots", "update_dots", "start_residual", "true_residual",
               "other")
@@ -148,6 +150,9 @@ def lib():
         "s7_server_release": (i, [vp, C.c_uint64]),
         "s7_server_get_stats": (i, [vp, P(s7_server_stats)]),
         "s7_server_destroy": (i, [vp]),
+        "s7_mem_stats": (i, [i, P(C.c_size_t), P(C.c_size_t)]),
+        "s7_mem_trim": (i, [i, C.c_size_t]),
+        "s7_mem_set_cache": (i, [C.c_size_t]),
         "s7_last_error": (C.c_char_p, []),
         "s7_version": (C.c_char_p, []),
     }
@@ -379,6 +384,23 @@ def stencil7_profile(op, enable):
     n = (C.c_longlong * 6)()
     _check(lib().stencil7_profile(op.handle, 1 if enable else 0, ms, n))
     return {k: (ms[j], n[j]) for j, k in enumerate(PROF_KINDS)}
+
+
+def s7_mem_stats(device=0):
+    """(reserved, used) bytes of the library's device memory pool."""
+    r, u = C.c_size_t(), C.c_size_t()
+    _check(lib().s7_mem_stats(int(device), C.byref(r), C.byref(u)))
+    return r.value, u.value
+
+
+def s7_mem_trim(device=0, keep=0):
+    """Return the pool's cached blocks to the device, keeping ``keep`` bytes."""
+    _check(lib().s7_mem_trim(int(device), int(keep)))
+
+
+def s7_mem_set_cache(nbytes):
+    """Most bytes a pool keeps reserved after a release (default 64 GiB)."""
+    _check(lib().s7_mem_set_cache(int(nbytes)))
 
 
 def stencil7_residual_noalloc(op, b, x, r=None):

@@ -90,6 +90,17 @@ static bool on_device(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// The device address of pinned (page-locked or registered) host memory that
+// kernels can read in place; NULL for pageable host memory.
+static const void* mapped_host(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 // The library carries its own CUDA runtime.  A caller (for instance PyTorch)
 // selects a device by making that device's primary context current on the
 // thread; bind this runtime to the same device before any work.
@@ -121,23 +132,153 @@ static void bind_handle_device(const Handle* h) {
   cudaGetLastError();
 }
 
-static int dmalloc(Handle* h, void** p, size_t bytes) {
-  cudaError_t e = cudaMalloc(p, bytes);
+// ---------------------------------------------------------------------------
+// device memory: one stream-ordered pool per device, owned by the library.
+// A freed block stays in the pool (up to the cache limit) and the next
+// operator of a similar size takes it without mapping memory again: mapping
+// and unmapping tens of GB costs tens of milliseconds per create/destroy,
+// as much as a few solver steps.  An allocation is synchronised on the stream
+// it was made on, so any stream may use it on return; a block goes back to
+// the pool ordered after the work already queued on the handle's stream.
+// ---------------------------------------------------------------------------
+static std::mutex g_pool_mu;
+static cudaMemPool_t g_pool[64];
+static size_t g_cache_limit = (size_t)64 << 30;
+
+static cudaError_t pool_of(int dev, cudaMemPool_t* out) {
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  if (!g_pool[dev]) {
+    cudaMemPoolProps pp;
+    memset(&pp, 0, sizeof pp);
+    pp.allocType = cudaMemAllocationTypePinned;
+    pp.handleTypes = cudaMemHandleTypeNone;
+    pp.location.type = cudaMemLocationTypeDevice;
+    pp.location.id = dev;
+    cudaMemPool_t p = nullptr;
+    cudaError_t e = cudaMemPoolCreate(&p, &pp);
+    if (e != cudaSuccess) return e;
+    unsigned long long thr = g_cache_limit;
+    cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &thr);
+    g_pool[dev] = p;
+  }
+  *out = g_pool[dev];
+  return cudaSuccess;
+}
+
+// Pool allocation on device `dev` for use from any stream.  If the pool cannot
+// grow, the blocks it caches are returned to the device and the call retried.
+static cudaError_t pool_alloc(int dev, void** p, size_t bytes, cudaStream_t st) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  cudaMemPool_t pool;
+  cudaError_t e = pool_of(dev, &pool);
+  if (e != cudaSuccess) return e;
+  e = cudaMallocFromPoolAsync(p, bytes, pool, st);
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    cudaDeviceSynchronize();
+    cudaMemPoolTrimTo(pool, 0);
+    e = cudaMallocFromPoolAsync(p, bytes, pool, st);
+  }
+  if (e == cudaErrorMemoryAllocation) {
+    // a failed attempt can leave the pool holding memory it reserved while
+    // growing: give back everything no live block uses
+    cudaGetLastError();
+    cudaMemPoolTrimTo(pool, 0);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) {
     cudaGetLastError();
     *p = nullptr;
-    return fail(S7_ENOMEM, "cudaMalloc(%zu bytes) failed: %s", bytes, cudaGetErrorString(e));
   }
+  return e;
+}
+
+cudaError_t s7::dev_alloc(int dev, void** p, size_t bytes, cudaStream_t st) {
+  return pool_alloc(dev, p, bytes, st);
+}
+
+void s7::dev_free(void* p, cudaStream_t st) {
+  if (p) cudaFreeAsync(p, st);
+}
+
+static int dmalloc(Handle* h, void** p, size_t bytes, cudaStream_t st) {
+  cudaError_t e = pool_alloc(h->device, p, bytes, st);
+  if (e != cudaSuccess)
+    return fail(S7_ENOMEM, "device allocation of %zu bytes failed: %s", bytes,
+                cudaGetErrorString(e));
   h->bytes += bytes;
   return S7_OK;
 }
 
+static int dmalloc(Handle* h, void** p, size_t bytes) { return dmalloc(h, p, bytes, h->stream); }
+
+// Return a block to the pool after the work queued on the handle's stream.
+// Work on other streams that reads it must be complete (the API calls that
+// issue such work finish it before they return; destroy synchronises the
+// device first).
 static void dfree(Handle* h, void** p, size_t bytes) {
   if (*p) {
-    cudaFree(*p);
+    cudaFreeAsync(*p, h->stream);
     h->bytes -= bytes;
   }
   *p = nullptr;
+}
+
+// Pinned host mirrors of a handle's scalars (two Scalars each), kept on a
+// free list for the next handle: freeing pinned memory synchronises the
+// whole device.
+static std::mutex g_pin_mu;
+static std::vector<Scalars*> g_pin_free;
+
+static cudaError_t pinned_scalars(Scalars** out) {
+  {
+    std::lock_guard<std::mutex> lk(g_pin_mu);
+    if (!g_pin_free.empty()) {
+      *out = g_pin_free.back();
+      g_pin_free.pop_back();
+      return cudaSuccess;
+    }
+  }
+  return cudaMallocHost((void**)out, 2 * sizeof(Scalars));
+}
+
+static void pinned_scalars_put(Scalars* p) {
+  if (!p) return;
+  std::lock_guard<std::mutex> lk(g_pin_mu);
+  g_pin_free.push_back(p);
+}
+
+extern "C" int s7_mem_stats(int device, size_t* reserved, size_t* used) {
+  cudaMemPool_t pool;
+  cudaError_t e = pool_of(device, &pool);
+  if (e != cudaSuccess) return cuda_fail(e, "s7_mem_stats");
+  unsigned long long r = 0, u = 0;
+  if ((e = cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &r)) != cudaSuccess ||
+      (e = cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &u)) != cudaSuccess)
+    return cuda_fail(e, "s7_mem_stats");
+  if (reserved) *reserved = (size_t)r;
+  if (used) *used = (size_t)u;
+  return S7_OK;
+}
+
+extern "C" int s7_mem_trim(int device, size_t keep) {
+  cudaMemPool_t pool;
+  cudaError_t e = pool_of(device, &pool);
+  if (e != cudaSuccess) return cuda_fail(e, "s7_mem_trim");
+  if ((e = cudaDeviceSynchronize()) != cudaSuccess) return cuda_fail(e, "s7_mem_trim");
+  if ((e = cudaMemPoolTrimTo(pool, keep)) != cudaSuccess) return cuda_fail(e, "s7_mem_trim");
+  return S7_OK;
+}
+
+extern "C" int s7_mem_set_cache(size_t bytes) {
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  g_cache_limit = bytes;
+  unsigned long long thr = bytes;
+  for (int d = 0; d < 64; ++d)
+    if (g_pool[d]) cudaMemPoolSetAttribute(g_pool[d], cudaMemPoolAttrReleaseThreshold, &thr);
+  return S7_OK;
 }
 
 // small kernels of the driver
@@ -241,7 +382,7 @@ static void release(Handle* h) {
   dfree(h, &w.ref_x, n * 8);
   dfree(h, &w.ref_b, n * 8);
   dfree(h, &w.ref_r, n * 8);
-  if (w.h_sc) cudaFreeHost(w.h_sc);
+  pinned_scalars_put(w.h_sc);
   w.h_sc = nullptr;
   for (int k = 0; k < 2; ++k) {
     if (w.snap[k]) cudaEventDestroy(w.snap[k]);
@@ -256,8 +397,12 @@ static void release(Handle* h) {
   prof_free(h);
   if (h->ev) cudaEventDestroy(h->ev);
   if (h->stream) cudaStreamDestroy(h->stream);
+  if (h->aux_ev) cudaEventDestroy(h->aux_ev);
+  if (h->aux) cudaStreamDestroy(h->aux);
   h->ev = nullptr;
   h->stream = nullptr;
+  h->aux_ev = nullptr;
+  h->aux = nullptr;
 }
 
 static double round_storage(double v, s7_dtype t) {
@@ -398,54 +543,59 @@ extern "C" int stencil7_create(stencil7_t* out, int nx, int ny, int nz, const s7
       for (int d = 0; d < 7; ++d)
         if ((rc = dmalloc(h, (void**)&h->tc[d], (size_t)n * 4))) goto fail_out;
   }
-  {
-    // stage raw arrays on the device (each array in turn if it is host memory)
+  if (!h->constant) {
+    // Raw arrays are read where they are when the kernels can reach them:
+    // device memory, and for the six off-diagonals (each read once, unless
+    // keep_true casts them again) pinned host memory, which the scaling
+    // kernels stream over the host link as fast as a copy engine moves it.
+    // Other host arrays are first copied to pool blocks.
     const size_t rs = dsize(c->dtype);
-    const void* raw_dev[7];
+    const void* raw_dev[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     void* stage[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-    const long long cnt = h->constant ? 1 : n;
     for (int d = 0; d < 7 && rc == S7_OK; ++d) {
-      if (!h->constant && on_device(raw_in[d])) {
+      if (on_device(raw_in[d])) {
         raw_dev[d] = raw_in[d];
-      } else {
-        void* p = nullptr;
-        if ((e = cudaMalloc(&p, (size_t)cnt * rs)) != cudaSuccess) {
-          cudaGetLastError();
-          rc = fail(S7_ENOMEM, "staging coefficients: %s", cudaGetErrorString(e));
-          break;
-        }
-        stage[d] = p;
-        if ((e = cudaMemcpyAsync(p, raw_in[d], (size_t)cnt * rs, cudaMemcpyDefault, h->stream)) !=
-            cudaSuccess) {
-          rc = cuda_fail(e, "copying coefficients");
-          break;
-        }
-        raw_dev[d] = p;
+        continue;
       }
+      const void* m = (d < 6 && !h->keep_true) ? mapped_host(raw_in[d]) : nullptr;
+      if (m) {
+        raw_dev[d] = m;
+        continue;
+      }
+      if ((e = pool_alloc(h->device, &stage[d], (size_t)n * rs, h->stream)) != cudaSuccess)
+        rc = fail(S7_ENOMEM, "staging coefficients: %s", cudaGetErrorString(e));
+      raw_dev[d] = stage[d];
     }
-    if (rc == S7_OK && !h->constant) {
+    for (int d = 0; d < 7 && rc == S7_OK; ++d)
+      if (stage[d] &&
+          (e = cudaMemcpyAsync(stage[d], raw_in[d], (size_t)n * rs, cudaMemcpyDefault,
+                               h->stream)) != cudaSuccess)
+        rc = cuda_fail(e, "copying coefficients");
+    if (rc == S7_OK) {
       int bad = 0;
       rc = eng->scale(h, raw_dev, c->dtype, h->stream, &bad);
       if (rc) rc = fail(rc, "coefficient scaling failed: %s", cudaGetErrorString(cudaGetLastError()));
       else if (bad) rc = fail(S7_EINVAL, "stencil7_create: %d zero or non-finite diagonal entries", bad);
-    } else if (rc == S7_OK && h->constant && h->keep_true) {
-      // expand the constants into arrays
-      for (int d = 0; d < 7 && rc == S7_OK; ++d) {
-        float v;
-        if (c->dtype == S7_F64) {
-          double t;
-          cudaMemcpy(&t, raw_in[d], 8, cudaMemcpyDefault);
-          v = (float)t;
-        } else {
-          cudaMemcpy(&v, raw_in[d], 4, cudaMemcpyDefault);
-        }
-        k_fill_f32<<<grid_for(n), 256, 0, h->stream>>>(n, h->tc[d], v);
-        if ((e = cudaGetLastError()) != cudaSuccess) rc = cuda_fail(e, "k_fill_f32");
-      }
     }
     cudaStreamSynchronize(h->stream);
     for (int d = 0; d < 7; ++d)
-      if (stage[d]) cudaFree(stage[d]);
+      if (stage[d]) cudaFreeAsync(stage[d], h->stream);
+    if (rc) goto fail_out;
+  } else if (h->keep_true) {
+    // expand the constants into arrays
+    for (int d = 0; d < 7 && rc == S7_OK; ++d) {
+      float v;
+      if (c->dtype == S7_F64) {
+        double t;
+        cudaMemcpy(&t, raw_in[d], 8, cudaMemcpyDefault);
+        v = (float)t;
+      } else {
+        cudaMemcpy(&v, raw_in[d], 4, cudaMemcpyDefault);
+      }
+      k_fill_f32<<<grid_for(n), 256, 0, h->stream>>>(n, h->tc[d], v);
+      if ((e = cudaGetLastError()) != cudaSuccess) rc = cuda_fail(e, "k_fill_f32");
+    }
+    cudaStreamSynchronize(h->stream);
     if (rc) goto fail_out;
   }
   *out = h;
@@ -545,8 +695,7 @@ extern "C" int stencil9_create(stencil7_t* out, int nx, int ny, const s9_coeffs*
         continue;
       }
       void* p = nullptr;
-      if ((e = cudaMalloc(&p, (size_t)n * rs)) != cudaSuccess) {
-        cudaGetLastError();
+      if ((e = pool_alloc(h->device, &p, (size_t)n * rs, h->stream)) != cudaSuccess) {
         rc = fail(S7_ENOMEM, "staging coefficients: %s", cudaGetErrorString(e));
         break;
       }
@@ -566,7 +715,7 @@ extern "C" int stencil9_create(stencil7_t* out, int nx, int ny, const s9_coeffs*
     }
     cudaStreamSynchronize(h->stream);
     for (int d = 0; d < 9; ++d)
-      if (stage[d]) cudaFree(stage[d]);
+      if (stage[d]) cudaFreeAsync(stage[d], h->stream);
     if (rc) goto fail9;
   }
   *out = h;
@@ -578,10 +727,21 @@ fail9:
   return rc;
 }
 
+void s7::destroy_idle(Handle* h) {
+  if (!h) return;
+  bind_handle_device(h);
+  cudaStreamSynchronize(h->stream);
+  release(h);
+  delete h;
+}
+
 extern "C" int stencil7_destroy(stencil7_t h) {
   if (!h) return S7_OK;
   bind_handle_device(h);
-  cudaStreamSynchronize(h->stream);
+  // work queued on the caller's streams may still read the handle's memory
+  // (stencil7_apply on device buffers returns before it runs): finish it
+  // before the blocks go back to the pool
+  cudaDeviceSynchronize();
   release(h);
   delete h;
   return S7_OK;
@@ -620,7 +780,7 @@ int s7::ensure_ws(Handle* h, int maxit) {
     if ((rc = dmalloc(h, (void**)&w.parts, w.parts_n * 8))) return rc;
     if ((rc = dmalloc(h, (void**)&w.sc, sizeof(Scalars)))) return rc;
     CK(cudaMemset(w.sc, 0, sizeof(Scalars)));
-    if (!w.h_sc) CK(cudaMallocHost((void**)&w.h_sc, 2 * sizeof(Scalars)));
+    if (!w.h_sc) CK(pinned_scalars(&w.h_sc));
     for (int k = 0; k < 2; ++k)
       if (!w.snap[k]) CK(cudaEventCreateWithFlags(&w.snap[k], cudaEventDisableTiming));
     w.ready = true;
@@ -682,6 +842,14 @@ static int stage_out(Handle* h, const void* src, s7_dtype have, void* dst, s7_dt
   if ((rc = eng->cast(src, have, h->ws.stage, dt, (long long)n, st)))
     return fail(rc, "type conversion failed");
   CK(cudaMemcpyAsync(dst, h->ws.stage, n * dsize(dt), cudaMemcpyDefault, st));
+  return S7_OK;
+}
+
+// The handle's second stream and its event, created on first use.
+static int ensure_aux(Handle* h) {
+  if (h->aux) return S7_OK;
+  CK(cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking));
+  CK(cudaEventCreateWithFlags(&h->aux_ev, cudaEventDisableTiming));
   return S7_OK;
 }
 
@@ -1020,6 +1188,17 @@ extern "C" int bicgstab_solve(stencil7_t h, const void* b, void* x, s7_dtype dt,
   SolveOut so;
   if ((rc = solve_core(h, bdev, tol, maxit, &so))) return rc;
   if (so.bnorm == 0.0) CK(cudaMemsetAsync(w.x, 0, (size_t)h->n * eng->x_size, st));
+  // The copy of x to host memory and the true residual both only read w.x,
+  // and one is bound by the host link, the other by HBM and float64
+  // arithmetic: run the copy on the second stream beside the residual.
+  cudaStream_t xs = st;
+  if (true_resid && !on_device(x)) {
+    if ((rc = ensure_aux(h))) return rc;
+    CK(cudaEventRecord(h->ev, st));
+    CK(cudaStreamWaitEvent(h->aux, h->ev, 0));
+    xs = h->aux;
+    if ((rc = stage_out(h, w.x, xt, x, dt, xs))) return rc;
+  }
   if (true_resid) {
     const int pr = prof_begin(h, PK_RES, st);
     rc = eng->true_resid(h, bdev, st);
@@ -1032,7 +1211,12 @@ extern "C" int bicgstab_solve(stencil7_t h, const void* b, void* x, s7_dtype dt,
   }
   if (resid_hist)
     CK(cudaMemcpyAsync(resid_hist, w.hist, (size_t)(so.iters + 1) * 8, cudaMemcpyDeviceToHost, st));
-  if ((rc = stage_out(h, w.x, xt, x, dt, st))) return rc;
+  if (xs == st) {
+    if ((rc = stage_out(h, w.x, xt, x, dt, st))) return rc;
+  } else {
+    CK(cudaEventRecord(h->aux_ev, xs));
+    CK(cudaStreamWaitEvent(st, h->aux_ev, 0));
+  }
   CK(cudaStreamSynchronize(st));
   if (resid_hist && so.bnorm == 0.0) resid_hist[0] = 0.0;
   if (iters) *iters = so.iters;

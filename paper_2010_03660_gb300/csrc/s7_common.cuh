@@ -39,8 +39,113 @@ __device__ __forceinline__ double f2d_exact(float v) {
   return __longlong_as_double((long long)bits);
 }
 
+// ---------------------------------------------------------------------------
+// double-word arithmetic: a value held as the unevaluated sum hi + lo of two
+// binary32 numbers with |lo| <= ulp(hi)/2 (about 48 significant bits).
+// GB300 runs float64 at a small fraction of its float32 rate, so the
+// residual sweeps that want more than float32 accuracy sum their stencil
+// terms in double words on the float32 pipes.  The building blocks are the
+// error-free transformations of Dekker and Knuth (the exact error of a sum
+// from six additions, of a product from one FMA) and the double-word
+// algorithms of Joldes, Muller and Popescu, "Tight and rigorous error bounds
+// for basic building blocks of double-word arithmetic" (ACM TOMS 44, 2017):
+// the accurate sum of two double words, the products of a double word by a
+// binary32 number and by a double word, and the quotient of two double
+// words, each with a proven relative error of a small multiple of u^2
+// (u = 2^-24).  The operations live in their own namespace and are found by
+// argument-dependent lookup, so the binary32 / binary64 overloads of fma
+// stay visible.
+// ---------------------------------------------------------------------------
+namespace dw {
+
+struct dfl {
+  float hi, lo;
+  dfl() = default;
+  __host__ __device__ constexpr dfl(int v) : hi((float)v), lo(0.f) {}
+  __host__ __device__ constexpr dfl(float v) : hi(v), lo(0.f) {}
+  __host__ __device__ constexpr dfl(float h, float l) : hi(h), lo(l) {}
+  // nearest double word of a binary64 value (exact for |v| in binary32
+  // range with at most 48 significant bits)
+  __host__ __device__ dfl(double v) : hi((float)v), lo((float)(v - (double)(float)v)) {}
+  __host__ __device__ explicit operator double() const {
+#ifdef __CUDA_ARCH__
+    return f2d_exact(hi) + f2d_exact(lo);
+#else
+    return (double)hi + (double)lo;
+#endif
+  }
+};
+
+// s + e = a + b exactly (any a, b).
+__device__ __forceinline__ dfl two_sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  return dfl(s, (a - (s - bb)) + (b - bb));
+}
+// s + e = a + b exactly, provided |a| >= |b| (or a == 0).
+__device__ __forceinline__ dfl fast_two_sum(float a, float b) {
+  const float s = a + b;
+  return dfl(s, b - (s - a));
+}
+// p + e = a * b exactly (barring underflow).
+__device__ __forceinline__ dfl two_prod(float a, float b) {
+  const float p = a * b;
+  return dfl(p, fmaf(a, b, -p));
+}
+
+__device__ __forceinline__ dfl operator-(dfl x) { return dfl(-x.hi, -x.lo); }
+
+__device__ __forceinline__ dfl operator+(dfl x, dfl y) {
+  const dfl s = two_sum(x.hi, y.hi);
+  const dfl t = two_sum(x.lo, y.lo);
+  const dfl v = fast_two_sum(s.hi, s.lo + t.hi);
+  return fast_two_sum(v.hi, t.lo + v.lo);
+}
+__device__ __forceinline__ dfl operator-(dfl x, dfl y) { return x + (-y); }
+
+__device__ __forceinline__ dfl operator*(dfl x, float y) {
+  const dfl c = two_prod(x.hi, y);
+  return fast_two_sum(c.hi, fmaf(x.lo, y, c.lo));
+}
+__device__ __forceinline__ dfl operator*(float y, dfl x) { return x * y; }
+
+__device__ __forceinline__ dfl operator*(dfl x, dfl y) {
+  const dfl c = two_prod(x.hi, y.hi);
+  const float t = fmaf(x.hi, y.lo, x.lo * y.lo);
+  return fast_two_sum(c.hi, c.lo + fmaf(x.lo, y.hi, t));
+}
+
+__device__ __forceinline__ dfl operator/(dfl x, dfl y) {
+  const float th = x.hi / y.hi;
+  const dfl r = y * th;
+  const float d = (x.hi - r.hi) + (x.lo - r.lo);
+  return fast_two_sum(th, d / y.hi);
+}
+
+__device__ __forceinline__ dfl fma(float a, dfl x, dfl acc) { return x * a + acc; }
+__device__ __forceinline__ dfl fma(dfl a, dfl x, dfl acc) { return a * x + acc; }
+
+__host__ __device__ __forceinline__ bool operator==(dfl x, dfl y) {
+  return x.hi == y.hi && x.lo == y.lo;
+}
+__host__ __device__ __forceinline__ bool operator!=(dfl x, dfl y) { return !(x == y); }
+
+// hi + lo rounded to odd in binary32: hi when hi is odd (or the pair is
+// exact), else hi's neighbour towards lo.  Rounding that value to nearest in
+// a format of at most 22 bits gives the correctly rounded hi + lo.
+__device__ __forceinline__ float round_odd(dfl x) {
+  unsigned int u = __float_as_uint(x.hi);
+  if (x.lo != 0.f && (u & 1u) == 0u && isfinite(x.hi))
+    u += ((x.lo > 0.f) == (x.hi > 0.f)) ? 1u : 0xffffffffu;
+  return __uint_as_float(u);
+}
+
+}  // namespace dw
+using dw::dfl;
+
 template <class A> __device__ __forceinline__ A to_acc(float v);
 template <> __device__ __forceinline__ float to_acc<float>(float v) { return v; }
+template <> __device__ __forceinline__ dfl to_acc<dfl>(float v) { return dfl(v); }
 template <> __device__ __forceinline__ double to_acc<double>(float v) { return f2d_exact(v); }
 
 template <class A> __device__ __forceinline__ A to_acc(double v);
@@ -61,6 +166,34 @@ template <> __device__ __forceinline__ double from_acc<double>(double v) { retur
 template <> __device__ __forceinline__ float from_acc<float>(double v) { return (float)v; }
 template <> __device__ __forceinline__ bf16 from_acc<bf16>(double v) { return __double2bfloat16(v); }
 template <> __device__ __forceinline__ f16 from_acc<f16>(double v) { return __double2half(v); }
+
+template <> __device__ __forceinline__ dfl to_acc<dfl>(double v) { return dfl(v); }
+template <class A> __device__ __forceinline__ A to_acc(dfl v);
+template <> __device__ __forceinline__ dfl to_acc<dfl>(dfl v) { return v; }
+// a double word to storage: binary32 takes hi (the pair is normalised, so hi
+// is hi + lo rounded to nearest); binary64 the exact sum; the 16-bit types
+// round the round-to-odd binary32 value, which rounds hi + lo correctly
+template <class T> __device__ __forceinline__ T from_acc(dfl v);
+template <> __device__ __forceinline__ dfl from_acc<dfl>(dfl v) { return v; }
+template <> __device__ __forceinline__ float from_acc<float>(dfl v) { return v.hi; }
+template <> __device__ __forceinline__ double from_acc<double>(dfl v) { return (double)v; }
+template <> __device__ __forceinline__ bf16 from_acc<bf16>(dfl v) {
+  return __float2bfloat16_rn(dw::round_odd(v));
+}
+template <> __device__ __forceinline__ f16 from_acc<f16>(dfl v) {
+  return __float2half_rn(dw::round_odd(v));
+}
+
+// Element type of the stored coefficients inside a sweep of arithmetic type
+// A (binary32 for double-word sweeps: coefficient times input is then a
+// double word from one product and one FMA), and the type the inner
+// products of the residual norms accumulate in (binary64 for double words:
+// squares of binary32-range values can overflow binary32).
+template <class A> struct CoefOf { typedef A t; };
+template <> struct CoefOf<dfl> { typedef float t; };
+template <class A> struct NormOf { typedef A t; };
+template <> struct NormOf<dfl> { typedef double t; };
+template <class N, class A> __device__ __forceinline__ N to_norm(A v) { return (N)v; }
 
 // ---------------------------------------------------------------------------
 // vector loads / stores of VEC consecutive elements (VEC*sizeof(T) <= 16 B,

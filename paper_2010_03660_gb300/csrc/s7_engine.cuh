@@ -5,6 +5,7 @@
 #pragma once
 
 #include <algorithm>
+#include <type_traits>
 
 #include <string.h>
 
@@ -288,20 +289,25 @@ struct EngineImpl {
   // keeps 4 cells (8-byte vectors) so per-thread state, and with it
   // occupancy, matches the float32 kernels
   static constexpr int VEC = sizeof(T) >= 4 ? 16 / (int)sizeof(T) : 4;
+  // arithmetic of the float64-accuracy residual sweeps: binary64 for float64
+  // storage; double words (binary32 pairs, about 48 bits) otherwise, since
+  // GB300's float64 rate would bound those sweeps far below HBM bandwidth
+  typedef typename std::conditional<sizeof(T) == 8, double, dfl>::type RA;
   // the other width the pipelined sweeps can take: 8 cells (16 bytes) of
   // 16-bit storage per thread, which halves their per-cell overhead
   static constexpr int VW = sizeof(T) == 2 ? 8 : VEC;
 
   template <class AA>
   static CoefView<T, AA> stored(const Handle* h) {
+    typedef typename CoefOf<AA>::t CA;
     CoefView<T, AA> cf;
     for (int d = 0; d < 6; ++d) {
       cf.c[d] = (const T*)h->c[d];
-      cf.cc[d] = (AA)h->cconst[d];
+      cf.cc[d] = (CA)h->cconst[d];
     }
     cf.constant = h->constant;
     cf.diag = h->jacobi ? nullptr : (const T*)h->diag;
-    cf.cdiag = h->jacobi ? AA(1) : (AA)h->cconst[6];
+    cf.cdiag = h->jacobi ? CA(1) : (CA)h->cconst[6];
     return cf;
   }
 
@@ -310,7 +316,7 @@ struct EngineImpl {
     CoefView9<T, AA> cf;
     for (int d = 0; d < 8; ++d) cf.c[d] = (const T*)h->c[d];
     cf.diag = h->jacobi ? nullptr : (const T*)h->diag;
-    cf.cdiag = AA(1);
+    cf.cdiag = 1;
     return cf;
   }
 
@@ -329,21 +335,21 @@ struct EngineImpl {
                             bool vl, cudaStream_t st) {
     const Geom g = make_geom(h, V);
     if (h->stencil == 9) {
-      CoefView9<float, double> cf;
+      CoefView9<float, RA> cf;
       for (int d = 0; d < 8; ++d) cf.c[d] = h->tc[d];
       cf.diag = h->tc[8];
-      cf.cdiag = 1.0;
-      return launch_sweep9<float, double, V>(g, cf, src, epi, sc, vl, st);
+      cf.cdiag = 1;
+      return launch_sweep9<float, RA, V>(g, cf, src, epi, sc, vl, st);
     }
-    CoefView<float, double> cf;
+    CoefView<float, RA> cf;
     for (int d = 0; d < 6; ++d) {
       cf.c[d] = h->tc[d];
-      cf.cc[d] = 0.0;
+      cf.cc[d] = 0;
     }
     cf.diag = h->tc[6];
-    cf.cdiag = 1.0;
+    cf.cdiag = 1;
     cf.constant = 0;
-    return launch_sweep<float, double, V>(g, cf, src, epi, sc, vl, st);
+    return launch_sweep<float, RA, V>(g, cf, src, epi, sc, vl, st);
   }
 
   static int scale(Handle* h, const void* const raw[7], s7_dtype raw_dt, cudaStream_t st, int* bad) {
@@ -634,8 +640,8 @@ struct EngineImpl {
   // ||b~ - A~ x|| and ||b~|| with float64 accumulation -> sc->res[0], res[1].
   static int true_resid(Handle* h, const void* b, cudaStream_t st) {
     Workspace& w = h->ws;
-    SrcPlain<X, double> src{(const X*)w.x};
-    EpiResid<X, T, DT, double> epi;
+    SrcPlain<X, RA> src{(const X*)w.x};
+    EpiResid<X, T, DT, RA> epi;
     epi.b = (const X*)b;
     epi.dinv = (h->jacobi && !h->constant) ? (const DT*)h->d : nullptr;
     epi.dc = (h->jacobi && h->constant) ? h->cconst[6] : 1.0;
@@ -647,7 +653,7 @@ struct EngineImpl {
     epi.counter = CNT_RES;
     epi.mode = 1;
     const bool vl = (h->nx % VEC == 0) && aligned16(b);
-    return run_sweep<double, VEC>(h, src, epi, w.sc, vl, st);
+    return run_sweep<RA, VEC>(h, src, epi, w.sc, vl, st);
   }
 
   template <class XT>
@@ -655,8 +661,8 @@ struct EngineImpl {
     Workspace& w = h->ws;
     if (h->keep_true) {
       constexpr int V = 16 / (int)sizeof(XT) < 4 ? 16 / (int)sizeof(XT) : 4;
-      SrcPlain<XT, double> src{x};
-      EpiResid<XT, XT, float, double> epi;
+      SrcPlain<XT, RA> src{x};
+      EpiResid<XT, XT, float, RA> epi;
       epi.b = b;
       epi.dinv = nullptr;
       epi.dc = 1.0;
@@ -670,8 +676,8 @@ struct EngineImpl {
       const bool vl = (h->nx % V == 0) && aligned16(b) && aligned16(x) && (!r || aligned16(r));
       return run_true_sweep<V>(h, src, epi, w.sc, vl, st);
     }
-    SrcPlain<XT, double> src{x};
-    EpiResid<XT, XT, DT, double> epi;
+    SrcPlain<XT, RA> src{x};
+    EpiResid<XT, XT, DT, RA> epi;
     epi.b = b;
     epi.dinv = nullptr;
     epi.dc = 1.0;
@@ -683,7 +689,7 @@ struct EngineImpl {
     epi.counter = CNT_RES;
     epi.mode = 1;
     const bool vl = (h->nx % VEC == 0) && aligned16(b) && aligned16(x) && (!r || aligned16(r));
-    return run_sweep<double, VEC>(h, src, epi, w.sc, vl, st);
+    return run_sweep<RA, VEC>(h, src, epi, w.sc, vl, st);
   }
 
   static int raw_resid(Handle* h, const void* b, const void* x, void* r, s7_dtype dt, cudaStream_t st) {
@@ -696,7 +702,7 @@ struct EngineImpl {
   static int raw_resid_into_t(Handle* h, const XT* b, const XT* x, XT* r, double* parts,
                               Scalars* sc, cudaStream_t st) {
     const bool al = aligned16(b) && aligned16(x) && (!r || aligned16(r));
-    EpiResid<XT, XT, DT, double> epi;
+    EpiResid<XT, XT, DT, RA> epi;
     epi.b = b;
     epi.dinv = nullptr;
     epi.dc = 1.0;
@@ -705,10 +711,10 @@ struct EngineImpl {
     epi.parts = parts;
     epi.counter = CNT_RES;
     epi.mode = 1;
-    SrcPlain<XT, double> src{x};
+    SrcPlain<XT, RA> src{x};
     if (h->keep_true) {
       constexpr int V = 16 / (int)sizeof(XT) < 4 ? 16 / (int)sizeof(XT) : 4;
-      EpiResid<XT, XT, float, double> e2;
+      EpiResid<XT, XT, float, RA> e2;
       e2.b = b;
       e2.dinv = nullptr;
       e2.dc = 1.0;
@@ -723,7 +729,7 @@ struct EngineImpl {
     }
     epi.dmul = (h->jacobi && !h->constant) ? (const DT*)h->d : nullptr;
     epi.dmc = (h->jacobi && h->constant) ? h->cconst[6] : 1.0;
-    return run_sweep<double, VEC>(h, src, epi, sc, (h->nx % VEC == 0) && al, st);
+    return run_sweep<RA, VEC>(h, src, epi, sc, (h->nx % VEC == 0) && al, st);
   }
 
   static int raw_resid_into(Handle* h, const void* b, const void* x, void* r, s7_dtype dt,

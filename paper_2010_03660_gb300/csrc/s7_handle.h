@@ -72,6 +72,8 @@ struct Handle {
   void* small = nullptr;      // 256 bytes of device scratch (flags)
   cudaStream_t stream = nullptr;   // private stream (captures, solves)
   cudaEvent_t ev = nullptr;
+  cudaStream_t aux = nullptr;      // second stream: copies that overlap the private one
+  cudaEvent_t aux_ev = nullptr;
   Workspace ws;
   // per-kernel timing (stencil7_profile)
   int prof = 0;
@@ -150,6 +152,15 @@ const Engine* engine_for(s7_dtype t);
 // Allocate (once) the solver workspace of a handle, with a history of
 // maxit+1 entries.
 int ensure_ws(Handle* h, int maxit);
+
+// A block of `bytes` from the library's memory pool of device `dev`, usable
+// from any stream on return, and its release ordered after the work queued
+// on stream `st` (work on other streams that reads it must be complete).
+cudaError_t dev_alloc(int dev, void** p, size_t bytes, cudaStream_t st);
+void dev_free(void* p, cudaStream_t st);
+// Release a handle whose memory no queued work reads any more (the caller
+// synchronised the streams that used it), without synchronising the device.
+void destroy_idle(Handle* h);
 
 // Shape of the sweep grid for a handle (same for every sweep of the handle).
 void default_tile(int nx, int ny, int nz, int vec, int nsm, Tile* t);

@@ -194,13 +194,17 @@ Tile serve_tile(const s7_server* S, int nx, int ny, int nz, int pipe) {
   return t;
 }
 
+// Retire a request whose work is complete on both server streams (the
+// scheduler synchronised its stream; admission synchronises its own before a
+// request becomes active).  Its blocks go back to the library's pool without
+// a device-wide synchronisation, which would stall the other thread's work.
 void release_req(s7_server* S, Req* r) {
-  if (r->xr) cudaFree(r->xr);
-  if (r->br) cudaFree(r->br);
-  if (r->rr) cudaFree(r->rr);
-  if (r->parts) cudaFree(r->parts);
+  dev_free(r->xr, S->st);
+  dev_free(r->br, S->st);
+  dev_free(r->rr, S->st);
+  dev_free(r->parts, S->st);
   r->xr = r->br = r->rr = r->parts = nullptr;
-  if (r->h) stencil7_destroy(r->h);
+  if (r->h) destroy_idle(r->h);
   r->h = nullptr;
   if (r->slot >= 0) {
     std::lock_guard<std::mutex> lk(S->mu);
@@ -250,10 +254,8 @@ int create_padded(s7_server* S, Req* r, const s7_opts* oo) {
   const long long rows = (long long)r->in.ny * r->in.nz;
   cudaStream_t as = S->st_admit;
   unsigned char* buf = nullptr;
-  if (cudaMalloc(&buf, 8 * n * es) != cudaSuccess) {
-    cudaGetLastError();
+  if (dev_alloc(S->device, (void**)&buf, 8 * n * es, as) != cudaSuccess)
     return set_error(S7_ENOMEM, "s7_server: staging the padded operator");
-  }
   const void* src[7] = {c.xm, c.xp, c.ym, c.yp, c.zm, c.zp, c.diag};
   void* dst[7];
   void* tmp = buf + 7 * n * es;
@@ -300,7 +302,8 @@ int create_padded(s7_server* S, Req* r, const s7_opts* oo) {
     pc.diag = dst[6];
     rc = stencil7_create(&r->h, r->nxp, r->in.ny, r->in.nz, &pc, oo);
   }
-  cudaFree(buf);
+  cudaStreamSynchronize(as);   // nothing on the admission stream reads buf now
+  dev_free(buf, as);
   return rc;
 }
 
@@ -318,12 +321,11 @@ int admit(s7_server* S, Req* r) {
   if ((rc = ensure_ws(r->h, S->o.inner_maxit))) return rc;
   const size_t n = (size_t)r->n;
   cudaError_t e = cudaSuccess;
-  if ((e = cudaMalloc(&r->xr, n * 8)) != cudaSuccess ||
-      (e = cudaMalloc(&r->br, n * 8)) != cudaSuccess ||
-      (e = cudaMalloc(&r->rr, n * 8)) != cudaSuccess) {
-    cudaGetLastError();
+  cudaStream_t as = S->st_admit;
+  if ((e = dev_alloc(S->device, (void**)&r->xr, n * 8, as)) != cudaSuccess ||
+      (e = dev_alloc(S->device, (void**)&r->br, n * 8, as)) != cudaSuccess ||
+      (e = dev_alloc(S->device, (void**)&r->rr, n * 8, as)) != cudaSuccess)
     return S7_ENOMEM;
-  }
   long long nb = 0;
   for (int pipe = 0; pipe < 2; ++pipe) {
     const int v = pipe ? S->eng->vec_wide : S->eng->vec;
@@ -334,12 +336,8 @@ int admit(s7_server* S, Req* r) {
   }
   const long long rb = S->eng->raw_resid_blocks(r->h, S7_F64);
   r->parts_n = 2 * (size_t)std::max(std::max(nb, rb), 4096LL);
-  if ((e = cudaMalloc(&r->parts, r->parts_n * 8)) != cudaSuccess) {
-    cudaGetLastError();
-    return S7_ENOMEM;
-  }
+  if ((e = dev_alloc(S->device, (void**)&r->parts, r->parts_n * 8, as)) != cudaSuccess) return S7_ENOMEM;
   // b (host or device, f32/f64) -> float64 (zero in the padding); x0 = 0
-  cudaStream_t as = S->st_admit;
   const long long rows = (long long)r->in.ny * r->in.nz;
   if (r->in.dt == S7_F64) {
     // r->rr (unused until the first residual) stages b
@@ -436,6 +434,7 @@ void admitter(s7_server* S) {
     r->t_admit = now_s();
     const int rc = admit(S, r);
     if (rc) {
+      cudaStreamSynchronize(S->st_admit);   // uploads of a failed admission
       finish(S, r, rc);
       std::lock_guard<std::mutex> lk(S->mu);
       S->admitting--;

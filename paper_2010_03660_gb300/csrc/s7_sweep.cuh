@@ -61,10 +61,11 @@ __host__ __device__ inline int s7_nblocks(const Geom& g) { return g.tiles_x * g.
 // Coefficients of the stored operator as seen by a sweep.
 template <class CT, class A>
 struct CoefView {
+  typedef typename CoefOf<A>::t CA;   // coefficient values inside the sweep
   const CT* c[6];    // xm xp ym yp zm zp; unused when constant
   const CT* diag;    // NULL: unit (or constant) diagonal
-  A cc[6];           // constant coefficients
-  A cdiag;           // constant / unit diagonal value
+  CA cc[6];          // constant coefficients
+  CA cdiag;          // constant / unit diagonal value
   int constant;
 };
 
@@ -182,8 +183,7 @@ __device__ __forceinline__ void sweep_body(const Geom& g, const CoefView<CT, A>&
   for (int z = z0, k = 0; z < z1; ++z, ++k) {
     const long long ib = (long long)z * g.plane + row;
     // coefficients of plane z (streamed: no other block reads them)
-    A c[6][VEC];
-    A dg[VEC];
+    typename CoefOf<A>::t c[6][VEC], dg[VEC];
     if (cf.constant) {
 #pragma unroll
       for (int d = 0; d < 6; ++d)
@@ -502,7 +502,8 @@ struct EpiResid {
   double* parts;
   int counter;       // which Scalars counter
   int mode;          // 0: start of a solve (sets scalars); 1: stores totals in res[0..1]
-  DotAcc<A, 2> acc;
+  typedef typename NormOf<A>::t N;
+  DotAcc<N, 2> acc;
   A bv[8];
   A dv[8];
   __device__ void setup(const Scalars*) { acc.init(); }
@@ -535,10 +536,11 @@ struct EpiResid {
       rv[k] = as_stored<T>(rk);
       // a solve's start residual enters the recurrence as stored; a reported
       // residual's norm is that of the unrounded value
-      const A rn = mode == 0 ? rv[k] : rk;
+      const N rn = to_norm<N>(mode == 0 ? rv[k] : rk);
+      const N bn = to_norm<N>(rhs);
       if (k < nv) {
         acc.part[0] = fma(rn, rn, acc.part[0]);
-        acc.part[1] = fma(rhs, rhs, acc.part[1]);
+        acc.part[1] = fma(bn, bn, acc.part[1]);
       }
     }
     if (r_out) store_run<T, VEC, VL>(r_out + i, nv, rv);

@@ -30,7 +30,7 @@ template <class CT, class A>
 struct CoefView9 {
   const CT* c[8];
   const CT* diag;    // NULL: unit diagonal
-  A cdiag;
+  typename CoefOf<A>::t cdiag;
 };
 
 template <class CT, class A, int VEC, bool VL, class Src, class Epi>
@@ -86,8 +86,7 @@ __device__ __forceinline__ void sweep9_body(const Geom& g, const CoefView9<CT, A
 
   for (int y = y0, k = 0; y < y1; ++y, ++k) {
     const long long ib = (long long)y * nx + x;
-    A c[8][VEC];
-    A dg[VEC];
+    typename CoefOf<A>::t c[8][VEC], dg[VEC];
     if (nv > 0) {
 #pragma unroll
       for (int d = 0; d < 8; ++d) load_run<CT, VEC, VL, LD_STREAM>(cf.c[d] + ib, nv, c[d]);

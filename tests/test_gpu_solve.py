@@ -291,11 +291,63 @@ def test_refined_solve_reaches_1e10(s7, storage):
     assert rel(x, orc.x) < 1e-8
 
 
+@pytest.mark.parametrize("keep_true", [True, False])
+def test_double_word_residual_under_cancellation(s7, keep_true):
+    """b = A x rounded to float32, so every residual entry b - A x is the
+    rounding error of A x: about 1e-8 of the terms that cancel.  The residual
+    sweeps sum the terms in double words (binary32 pairs); their error must
+    stay within a few u^2 (u = 2^-24) of the terms' magnitude, where a lost
+    low part anywhere would leave errors near u."""
+    nx, ny, nz = 33, 20, 18
+    p = synth.varcoef(nx, ny, nz, seed=31)
+    x = synth.random_vector(p.n, 5, 2, np.float32)
+    ax = stencil.apply(nx, ny, nz, p.coef, x.astype(np.float64))
+    b = ax.astype(np.float32)
+    ref = b.astype(np.float64) - ax
+    mag = stencil.abs_apply(nx, ny, nz, p.coef, x) + np.abs(b)
+    assert 1e-10 < np.median(np.abs(ref) / mag) < 1e-7   # cancellation, not zero
+    with s7.stencil7_create(nx, ny, nz, gu.coef_on_device(p), storage="f32",
+                            keep_true=keep_true) as op:
+        r64 = gu.to_dev(np.zeros(p.n))
+        rn, bn = s7.stencil7_residual(op, gu.to_dev(b.astype(np.float64)),
+                                      gu.to_dev(x.astype(np.float64)), r64)
+        r32 = gu.to_dev(np.zeros(p.n, np.float32))
+        rn32, _ = s7.stencil7_residual(op, gu.to_dev(b), gu.to_dev(x), r32)
+    r64 = r64.cpu().numpy()
+    if keep_true:
+        # the raw operator as given: only the summation error remains
+        assert np.max(np.abs(r64 - ref) / mag) < 2e-13
+        assert rn == pytest.approx(np.linalg.norm(ref), rel=1e-5)
+        r32 = r32.cpu().numpy().astype(np.float64)
+        assert np.max(np.abs(r32 - ref) / (np.abs(ref) * 6e-8 + mag * 2e-13)) <= 1.0
+    else:
+        # A rebuilt as d * A~ with A~ rounded to float32: entries off by ~u
+        assert np.max(np.abs(r64 - ref) / mag) < 1e-6
+    assert rn32 == pytest.approx(rn, rel=1e-5 if keep_true else 1e-2)
+
+
+def test_double_word_residual9_under_cancellation(s7):
+    from oracle import stencil9
+    nx, ny = 90, 61
+    p = synth.varcoef9(nx, ny, seed=32)
+    x = synth.random_vector(p.n, 6, 2, np.float32)
+    ax = stencil9.apply(nx, ny, p.coef, x.astype(np.float64))
+    b = ax.astype(np.float32)
+    ref = b.astype(np.float64) - ax
+    mag = stencil9.abs_apply(nx, ny, p.coef, x) + np.abs(b)
+    with s7.stencil9_create(nx, ny, {k: gu.to_dev(v) for k, v in p.coef.items()},
+                            storage="f32", keep_true=True) as op:
+        r64 = gu.to_dev(np.zeros(p.n))
+        s7.stencil7_residual(op, gu.to_dev(b.astype(np.float64)),
+                             gu.to_dev(x.astype(np.float64)), r64)
+    assert np.max(np.abs(r64.cpu().numpy() - ref) / mag) < 2e-13
+
+
 def test_float64_residual_of_float32_data_is_exact(s7):
-    """The float64 residual sweeps widen float32 values with integer
-    instructions on normal numbers (hardware path for zero, subnormal, inf);
-    the widening is exact, so the float64 residual norm of float32 data
-    matches the oracle's to float64 rounding, special values included."""
+    """The residual sweeps take float32 data exactly (double words whose low
+    part is zero; products of two float32 numbers are exact double words), so
+    the residual norm of float32 data matches the oracle's to the double-word
+    summation error, special values (zero, subnormal, large) included."""
     nx, ny, nz = 64, 48, 40
     p = synth.varcoef(nx, ny, nz, seed=9)
     x = synth.random_vector(p.n, 3, 3, np.float32)
