@@ -274,6 +274,22 @@ def test_residual_entry_point(s7):
         assert bn == pytest.approx(np.linalg.norm(p.b.astype(np.float64)), rel=1e-12)
 
 
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+def test_refined_solve_reaches_1e12(s7, storage):
+    """The outer residual in double words (about 48 bits) still carries the
+    refinement to 1e-12 relative, checked by the oracle's float64 residual."""
+    nx, ny, nz = 40, 33, 29
+    p = synth.varcoef(nx, ny, nz, seed=6)
+    b64 = p.b.astype(np.float64)
+    with s7.stencil7_create(nx, ny, nz, gu.coef_on_device(p), storage=storage,
+                            keep_true=True) as op:
+        res = s7.bicgstab_solve_refined(op, gu.to_dev(b64), tol=1e-12, max_outer=60,
+                                        inner_maxit=100, inner_tol=1e-2)
+        x = res.x.cpu().numpy()
+    assert res.status == 0 and res.hist[-1] <= 1e-12
+    assert ob.true_residual(nx, ny, nz, p.coef, b64, x) <= 1.5e-12
+
+
 @pytest.mark.parametrize("storage", ["bf16", "f16", "f32"])
 def test_refined_solve_reaches_1e10(s7, storage):
     nx, ny, nz = 48, 40, 36
