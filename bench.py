@@ -125,6 +125,8 @@ def parse():
                     help="cells per thread in the pipelined sweeps (0 = tuned; 8 for 16-bit)")
     ap.add_argument("--pipe-kinds", type=int, default=0,
                     help="sweeps using the pipeline: bit 0 p/s sweep, bit 1 q/y sweep (0 = tuned)")
+    ap.add_argument("--residual-f64", action="store_true",
+                    help="float64-accuracy residual sweeps in binary64 (default: double words)")
     ap.add_argument("--ref-sample-nz", type=int, default=8)
     ap.add_argument("--ref-sample-iters", type=int, default=5)
     return ap.parse_args()
@@ -303,6 +305,7 @@ def config_of(args):
             "iters_per_step": args.iters, "storage": args.storage,
             "coefficients": "per-cell off-diagonals -U[0.5,1.5], diag = sum|off| + U[0.01,0.1]",
             "rhs": "N(0,1)", "x0": "0", "stop": "iteration-bounded (tol 0)",
+            "true_residual": "binary64" if args.residual_f64 else "double words (binary32 pairs)",
             "l2": "inputs larger than L2 (working set ~%d GB), no flush" %
                   round(args.nx * args.ny * args.nz * 60 / 1e9),
             "parallelism": "replicas" if args.gpus > 1 else "single GPU"}
@@ -336,7 +339,8 @@ def run_ours(args):
     coef_d = {k: torch.from_numpy(v).to(dev) for k, v in prob.coef.items()}
     op = s7.stencil7_create(nx, ny, nz, coef_d, storage=args.storage, bx=args.bx, by=args.by,
                             zchunk=args.zchunk, variant=args.variant, stages=args.stages,
-                            pipe_kinds=args.pipe_kinds, step_cells=args.step_cells)
+                            pipe_kinds=args.pipe_kinds, step_cells=args.step_cells,
+                            residual_f64=args.residual_f64)
     del coef_d
     torch.cuda.empty_cache()
     b = torch.from_numpy(prob.b).to(dev)
@@ -551,7 +555,8 @@ def run_e2e(args, s7, prob, dev):
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
         ev0.record()
-        op = s7.stencil7_create(prob.nx, prob.ny, prob.nz, pin, storage=args.storage)
+        op = s7.stencil7_create(prob.nx, prob.ny, prob.nz, pin, storage=args.storage,
+                                residual_f64=args.residual_f64)
         r = s7.bicgstab_solve(op, bh, xh, tol=0.0, maxit=args.iters, history=True)
         op.close()
         ev1.record()
@@ -608,7 +613,7 @@ def run_refined(args):
     for storage, inner_tol in (("bf16", 1e-2), ("f16", 1e-2), ("f16", 1e-3), ("f32", 1e-5),
                                ("f32", 1e-2)):
         op = s7.stencil7_create(e, e, e, coef, storage=storage, keep_true=True,
-                                variant=args.variant)
+                                variant=args.variant, residual_f64=args.residual_f64)
         for tol in (1e-8, 1e-10):
             def fn():
                 return s7.bicgstab_solve_refined(op, b, tol=tol, max_outer=80, inner_maxit=200,

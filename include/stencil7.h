@@ -126,6 +126,14 @@ typedef struct {
                         of the other sweeps (4; 2 for float64), or for 16-bit
                         storage 8 (one 16-byte copy per array and thread);
                         0 = default (8 for 16-bit storage)                    */
+  int residual_f64;  /* arithmetic of the float64-accuracy residual sweeps (the
+                        true residual of bicgstab_solve, stencil7_residual and
+                        the refinement's outer residual): 0 = double words
+                        (unevaluated sums of two binary32 numbers, about 48
+                        significant bits; error a few 1e-14 of the terms'
+                        magnitude; squared norms in binary64), several times
+                        faster on GB300; 1 = binary64 throughout.  float64
+                        storage always uses binary64.                          */
 } s7_opts;
 
 /* Create an operator handle.  Copies the coefficients to library-owned device
@@ -332,6 +340,8 @@ typedef struct {
   int three_pass;          /* 1: inner steps as Algorithm 1 prints them (three
                               passes); 0: two reductions per step (s7_opts.variant
                               1), the default                                      */
+  int residual_f64;        /* 1: outer residuals in binary64; 0: double words (see
+                              s7_opts.residual_f64), the default                   */
 } s7_server_opts;
 
 typedef struct {

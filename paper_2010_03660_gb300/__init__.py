@@ -79,7 +79,7 @@ class s7_opts(C.Structure):
     _fields_ = [("storage", C.c_int), ("no_jacobi", C.c_int), ("keep_true", C.c_int),
                 ("bx", C.c_int), ("by", C.c_int), ("zchunk", C.c_int),
                 ("check_every", C.c_int), ("stages", C.c_int), ("pipe_kinds", C.c_int),
-                ("variant", C.c_int), ("step_cells", C.c_int)]
+                ("variant", C.c_int), ("step_cells", C.c_int), ("residual_f64", C.c_int)]
 
 
 class s7_batch_opts(C.Structure):
@@ -91,7 +91,7 @@ class s7_server_opts(C.Structure):
     _fields_ = [("hbm_budget_bytes", C.c_size_t), ("storage", C.c_int), ("max_active", C.c_int),
                 ("steps_per_tick", C.c_int), ("threads", C.c_int), ("zchunk", C.c_int),
                 ("inner_tol", C.c_double), ("inner_maxit", C.c_int), ("max_outer", C.c_int),
-                ("three_pass", C.c_int)]
+                ("three_pass", C.c_int), ("residual_f64", C.c_int)]
 
 
 class s7_request(C.Structure):
@@ -275,12 +275,14 @@ class Operator:
 
 def stencil7_create(nx, ny, nz, coef, storage="f32", jacobi=True, keep_true=False,
                     bx=0, by=0, zchunk=0, check_every=0, constant=None, stages=0,
-                    pipe_kinds=0, variant=0, step_cells=0):
+                    pipe_kinds=0, variant=0, step_cells=0, residual_f64=False):
     """Create an operator from raw coefficients.
 
     ``coef`` maps ``diag, xm, xp, ym, yp, zm, zp`` to arrays/tensors of
     ``nx*ny*nz`` float32 or float64 values (all the same type), or all to
-    Python floats for a constant-coefficient operator.
+    Python floats for a constant-coefficient operator.  ``residual_f64``
+    runs the float64-accuracy residual sweeps in binary64 instead of double
+    words.
     """
     names = ("diag",) + DIRS
     if constant is None:
@@ -308,7 +310,7 @@ def stencil7_create(nx, ny, nz, coef, storage="f32", jacobi=True, keep_true=Fals
                    ptrs["zm"], ptrs["zp"], raw_dt, 1 if constant else 0)
     st = _STORAGE[storage] if isinstance(storage, str) else int(storage)
     op = s7_opts(st, 0 if jacobi else 1, 1 if keep_true else 0, bx, by, zchunk, check_every,
-                 stages, pipe_kinds, variant, step_cells)
+                 stages, pipe_kinds, variant, step_cells, 1 if residual_f64 else 0)
     h = C.c_void_p()
     _check(lib().stencil7_create(C.byref(h), nx, ny, nz, C.byref(cs), C.byref(op)))
     del keep
@@ -316,7 +318,7 @@ def stencil7_create(nx, ny, nz, coef, storage="f32", jacobi=True, keep_true=Fals
 
 
 def stencil9_create(nx, ny, coef, storage="f32", jacobi=True, keep_true=False, bx=0,
-                    zchunk=0, check_every=0, variant=0, layout="rows"):
+                    zchunk=0, check_every=0, variant=0, layout="rows", residual_f64=False):
     """Create a 2D 9-point operator from raw coefficients.
 
     ``coef`` maps ``diag`` and the eight directions of ``DIRS9`` to
@@ -341,7 +343,7 @@ def stencil9_create(nx, ny, coef, storage="f32", jacobi=True, keep_true=False, b
     cs = s9_coeffs(ptrs["diag"], *[ptrs[k] for k in DIRS9], raw_dt, lay)
     st = _STORAGE[storage] if isinstance(storage, str) else int(storage)
     op = s7_opts(st, 0 if jacobi else 1, 1 if keep_true else 0, bx, 0, zchunk, check_every,
-                 0, 0, variant)
+                 0, 0, variant, 0, 1 if residual_f64 else 0)
     h = C.c_void_p()
     _check(lib().stencil9_create(C.byref(h), nx, ny, C.byref(cs), C.byref(op)))
     del keep
@@ -525,10 +527,11 @@ def _result_dict(r):
 
 def s7_server_create(hbm_budget_bytes=0, storage="bf16", max_active=0, steps_per_tick=0,
                      threads=0, zchunk=0, inner_tol=0.0, inner_maxit=0, max_outer=0,
-                     three_pass=False):
+                     three_pass=False, residual_f64=False):
     st = _STORAGE[storage] if isinstance(storage, str) else int(storage)
     o = s7_server_opts(int(hbm_budget_bytes), st, max_active, steps_per_tick, threads, zchunk,
-                       float(inner_tol), inner_maxit, max_outer, 1 if three_pass else 0)
+                       float(inner_tol), inner_maxit, max_outer, 1 if three_pass else 0,
+                       1 if residual_f64 else 0)
     h = C.c_void_p()
     _check(lib().s7_server_create(C.byref(h), C.byref(o)))
     return h

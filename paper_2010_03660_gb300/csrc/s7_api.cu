@@ -486,6 +486,7 @@ extern "C" int stencil7_create(stencil7_t* out, int nx, int ny, int nz, const s7
   }
   h->step_vec = opts.step_cells > 0 ? opts.step_cells : (half ? 8 : eng->vec);
   h->variant = opts.variant;
+  h->resid_f64 = opts.residual_f64 ? 1 : 0;
   if (!eng->smem_ok(h)) {
     delete h;
     return fail(S7_EINVAL, "stencil7_create: tile too large for shared memory");
@@ -661,6 +662,7 @@ extern "C" int stencil9_create(stencil7_t* out, int nx, int ny, const s9_coeffs*
   h->pipe_kinds = 0;
   h->step_vec = eng->vec;
   h->variant = opts.variant;
+  h->resid_f64 = opts.residual_f64 ? 1 : 0;
   if (!eng->smem_ok(h)) {
     delete h;
     return fail(S7_EINVAL, "stencil9_create: tile too large for shared memory");

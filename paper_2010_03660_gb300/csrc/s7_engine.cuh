@@ -329,19 +329,20 @@ struct EngineImpl {
     return launch_sweep<T, AA, V>(g, stored<AA>(h), src, epi, sc, vl, st);
   }
 
-  // One float64 sweep of the raw float32 operator kept by keep_true.
-  template <int V, class Src, class Epi>
+  // One float64-accuracy sweep (arithmetic R) of the raw float32 operator kept
+  // by keep_true.
+  template <int V, class R, class Src, class Epi>
   static int run_true_sweep(const Handle* h, const Src& src, const Epi& epi, Scalars* sc,
                             bool vl, cudaStream_t st) {
     const Geom g = make_geom(h, V);
     if (h->stencil == 9) {
-      CoefView9<float, RA> cf;
+      CoefView9<float, R> cf;
       for (int d = 0; d < 8; ++d) cf.c[d] = h->tc[d];
       cf.diag = h->tc[8];
       cf.cdiag = 1;
-      return launch_sweep9<float, RA, V>(g, cf, src, epi, sc, vl, st);
+      return launch_sweep9<float, R, V>(g, cf, src, epi, sc, vl, st);
     }
-    CoefView<float, RA> cf;
+    CoefView<float, R> cf;
     for (int d = 0; d < 6; ++d) {
       cf.c[d] = h->tc[d];
       cf.cc[d] = 0;
@@ -349,7 +350,7 @@ struct EngineImpl {
     cf.diag = h->tc[6];
     cf.cdiag = 1;
     cf.constant = 0;
-    return launch_sweep<float, RA, V>(g, cf, src, epi, sc, vl, st);
+    return launch_sweep<float, R, V>(g, cf, src, epi, sc, vl, st);
   }
 
   static int scale(Handle* h, const void* const raw[7], s7_dtype raw_dt, cudaStream_t st, int* bad) {
@@ -637,11 +638,20 @@ struct EngineImpl {
     return launch_sweep1<T, A, VEC>(g, stored<A>(h), m, w.sc, vl, st);
   }
 
-  // ||b~ - A~ x|| and ||b~|| with float64 accumulation -> sc->res[0], res[1].
+  // The float64-accuracy residual sweeps run in binary64 when the handle asks
+  // for it (and always for float64 storage), else in double words.
+  static bool resid_f64(const Handle* h) { return h->resid_f64 != 0; }
+
+  // ||b~ - A~ x|| and ||b~|| with float64 accuracy -> sc->res[0], res[1].
   static int true_resid(Handle* h, const void* b, cudaStream_t st) {
+    return resid_f64(h) ? true_resid_r<double>(h, b, st) : true_resid_r<RA>(h, b, st);
+  }
+
+  template <class R>
+  static int true_resid_r(Handle* h, const void* b, cudaStream_t st) {
     Workspace& w = h->ws;
-    SrcPlain<X, RA> src{(const X*)w.x};
-    EpiResid<X, T, DT, RA> epi;
+    SrcPlain<X, R> src{(const X*)w.x};
+    EpiResid<X, T, DT, R> epi;
     epi.b = (const X*)b;
     epi.dinv = (h->jacobi && !h->constant) ? (const DT*)h->d : nullptr;
     epi.dc = (h->jacobi && h->constant) ? h->cconst[6] : 1.0;
@@ -653,16 +663,16 @@ struct EngineImpl {
     epi.counter = CNT_RES;
     epi.mode = 1;
     const bool vl = (h->nx % VEC == 0) && aligned16(b);
-    return run_sweep<RA, VEC>(h, src, epi, w.sc, vl, st);
+    return run_sweep<R, VEC>(h, src, epi, w.sc, vl, st);
   }
 
-  template <class XT>
+  template <class R, class XT>
   static int raw_resid_t(Handle* h, const XT* b, const XT* x, XT* r, cudaStream_t st) {
     Workspace& w = h->ws;
     if (h->keep_true) {
       constexpr int V = 16 / (int)sizeof(XT) < 4 ? 16 / (int)sizeof(XT) : 4;
-      SrcPlain<XT, RA> src{x};
-      EpiResid<XT, XT, float, RA> epi;
+      SrcPlain<XT, R> src{x};
+      EpiResid<XT, XT, float, R> epi;
       epi.b = b;
       epi.dinv = nullptr;
       epi.dc = 1.0;
@@ -674,10 +684,10 @@ struct EngineImpl {
       epi.counter = CNT_RES;
       epi.mode = 1;
       const bool vl = (h->nx % V == 0) && aligned16(b) && aligned16(x) && (!r || aligned16(r));
-      return run_true_sweep<V>(h, src, epi, w.sc, vl, st);
+      return run_true_sweep<V, R>(h, src, epi, w.sc, vl, st);
     }
-    SrcPlain<XT, RA> src{x};
-    EpiResid<XT, XT, DT, RA> epi;
+    SrcPlain<XT, R> src{x};
+    EpiResid<XT, XT, DT, R> epi;
     epi.b = b;
     epi.dinv = nullptr;
     epi.dc = 1.0;
@@ -689,20 +699,28 @@ struct EngineImpl {
     epi.counter = CNT_RES;
     epi.mode = 1;
     const bool vl = (h->nx % VEC == 0) && aligned16(b) && aligned16(x) && (!r || aligned16(r));
-    return run_sweep<RA, VEC>(h, src, epi, w.sc, vl, st);
+    return run_sweep<R, VEC>(h, src, epi, w.sc, vl, st);
+  }
+
+  template <class R>
+  static int raw_resid_r(Handle* h, const void* b, const void* x, void* r, s7_dtype dt,
+                         cudaStream_t st) {
+    if (dt == S7_F64)
+      return raw_resid_t<R, double>(h, (const double*)b, (const double*)x, (double*)r, st);
+    return raw_resid_t<R, float>(h, (const float*)b, (const float*)x, (float*)r, st);
   }
 
   static int raw_resid(Handle* h, const void* b, const void* x, void* r, s7_dtype dt, cudaStream_t st) {
-    if (dt == S7_F64) return raw_resid_t<double>(h, (const double*)b, (const double*)x, (double*)r, st);
-    return raw_resid_t<float>(h, (const float*)b, (const float*)x, (float*)r, st);
+    return resid_f64(h) ? raw_resid_r<double>(h, b, x, r, dt, st)
+                        : raw_resid_r<RA>(h, b, x, r, dt, st);
   }
 
   // The raw-system residual sweep with caller-supplied combine scratch.
-  template <class XT>
+  template <class R, class XT>
   static int raw_resid_into_t(Handle* h, const XT* b, const XT* x, XT* r, double* parts,
                               Scalars* sc, cudaStream_t st) {
     const bool al = aligned16(b) && aligned16(x) && (!r || aligned16(r));
-    EpiResid<XT, XT, DT, RA> epi;
+    EpiResid<XT, XT, DT, R> epi;
     epi.b = b;
     epi.dinv = nullptr;
     epi.dc = 1.0;
@@ -711,10 +729,10 @@ struct EngineImpl {
     epi.parts = parts;
     epi.counter = CNT_RES;
     epi.mode = 1;
-    SrcPlain<XT, RA> src{x};
+    SrcPlain<XT, R> src{x};
     if (h->keep_true) {
       constexpr int V = 16 / (int)sizeof(XT) < 4 ? 16 / (int)sizeof(XT) : 4;
-      EpiResid<XT, XT, float, RA> e2;
+      EpiResid<XT, XT, float, R> e2;
       e2.b = b;
       e2.dinv = nullptr;
       e2.dc = 1.0;
@@ -725,19 +743,27 @@ struct EngineImpl {
       e2.parts = parts;
       e2.counter = CNT_RES;
       e2.mode = 1;
-      return run_true_sweep<V>(h, src, e2, sc, (h->nx % V == 0) && al, st);
+      return run_true_sweep<V, R>(h, src, e2, sc, (h->nx % V == 0) && al, st);
     }
     epi.dmul = (h->jacobi && !h->constant) ? (const DT*)h->d : nullptr;
     epi.dmc = (h->jacobi && h->constant) ? h->cconst[6] : 1.0;
-    return run_sweep<RA, VEC>(h, src, epi, sc, (h->nx % VEC == 0) && al, st);
+    return run_sweep<R, VEC>(h, src, epi, sc, (h->nx % VEC == 0) && al, st);
+  }
+
+  template <class R>
+  static int raw_resid_into_r(Handle* h, const void* b, const void* x, void* r, s7_dtype dt,
+                              double* parts, Scalars* sc, cudaStream_t st) {
+    if (dt == S7_F64)
+      return raw_resid_into_t<R, double>(h, (const double*)b, (const double*)x, (double*)r,
+                                         parts, sc, st);
+    return raw_resid_into_t<R, float>(h, (const float*)b, (const float*)x, (float*)r, parts, sc,
+                                      st);
   }
 
   static int raw_resid_into(Handle* h, const void* b, const void* x, void* r, s7_dtype dt,
                             double* parts, Scalars* sc, cudaStream_t st) {
-    if (dt == S7_F64)
-      return raw_resid_into_t<double>(h, (const double*)b, (const double*)x, (double*)r, parts,
-                                      sc, st);
-    return raw_resid_into_t<float>(h, (const float*)b, (const float*)x, (float*)r, parts, sc, st);
+    return resid_f64(h) ? raw_resid_into_r<double>(h, b, x, r, dt, parts, sc, st)
+                        : raw_resid_into_r<RA>(h, b, x, r, dt, parts, sc, st);
   }
 
   static long long raw_resid_blocks(const Handle* h, s7_dtype dt) {

@@ -68,6 +68,7 @@ struct Handle {
   int pipe_kinds;             // bit k: sweep k of a step uses the pipeline
   int variant;                // 0: three reductions per step; 1: two (merged passes)
   int step_vec = 0;           // cells per thread in the pipelined sweeps
+  int resid_f64 = 0;          // 1: float64-accuracy residual sweeps in binary64
   size_t bytes = 0;           // device bytes held
   void* small = nullptr;      // 256 bytes of device scratch (flags)
   cudaStream_t stream = nullptr;   // private stream (captures, solves)

@@ -314,6 +314,7 @@ int admit(s7_server* S, Req* r) {
   oo.storage = S->o.storage;
   oo.keep_true = 1;
   oo.variant = S->o.three_pass ? 0 : 1;
+  oo.residual_f64 = S->o.residual_f64;
   int rc = (r->nxp != r->in.nx || r->in.coeffs.constant)
                ? create_padded(S, r, &oo)
                : stencil7_create(&r->h, r->in.nx, r->in.ny, r->in.nz, &r->in.coeffs, &oo);

@@ -117,15 +117,16 @@ def test_bounded_wait_and_cancel(s7):
     assert others
 
 
-@pytest.mark.parametrize("three_pass", [False, True])
-def test_constant_and_padded_requests_both_forms(s7, three_pass):
+@pytest.mark.parametrize("three_pass,f64", [(False, False), (True, False), (False, True)])
+def test_constant_and_padded_requests_both_forms(s7, three_pass, f64):
     """A constant-coefficient request (expanded to per-cell arrays) and
     requests whose x extent is padded to whole vectors, with the inner steps
-    in either form: each meets its tolerance on the true operator, and the
-    padding leaves the solution on the real cells unchanged (oracle)."""
+    in either form and the outer residuals in double words or binary64: each
+    meets its tolerance on the true operator, and the padding leaves the
+    solution on the real cells unchanged (oracle)."""
     cases = [synth.convdiff_constant(21, 13, 17, seed=0, dtype=np.float32),
              synth.varcoef(9, 31, 26, seed=901), synth.varcoef(35, 12, 30, seed=902)]
-    with s7.Server(storage="f16", three_pass=three_pass) as srv:
+    with s7.Server(storage="f16", three_pass=three_pass, residual_f64=f64) as srv:
         ids = []
         for p in cases:
             coef = p.coef

@@ -342,6 +342,54 @@ def test_double_word_residual_under_cancellation(s7, keep_true):
     assert rn32 == pytest.approx(rn, rel=1e-5 if keep_true else 1e-2)
 
 
+def test_binary64_residual_option_under_cancellation(s7):
+    """residual_f64 = 1 runs the same sweeps in binary64: the cancellation case
+    then resolves to binary64 rounding of the terms (about 1e-16)."""
+    nx, ny, nz = 33, 20, 18
+    p = synth.varcoef(nx, ny, nz, seed=31)
+    x = synth.random_vector(p.n, 5, 2, np.float32)
+    ax = stencil.apply(nx, ny, nz, p.coef, x.astype(np.float64))
+    b = ax.astype(np.float32)
+    ref = b.astype(np.float64) - ax
+    mag = stencil.abs_apply(nx, ny, nz, p.coef, x) + np.abs(b)
+    with s7.stencil7_create(nx, ny, nz, gu.coef_on_device(p), storage="f32", keep_true=True,
+                            residual_f64=True) as op:
+        r64 = gu.to_dev(np.zeros(p.n))
+        rn, _ = s7.stencil7_residual(op, gu.to_dev(b.astype(np.float64)),
+                                     gu.to_dev(x.astype(np.float64)), r64)
+    assert np.max(np.abs(r64.cpu().numpy() - ref) / mag) < 2e-15
+    assert rn == pytest.approx(np.linalg.norm(ref), rel=1e-9)
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+def test_true_residual_modes_agree(s7, storage):
+    """The true residual a solve reports is the same quantity in both modes:
+    double words and binary64 agree far below the solve's tolerance."""
+    nx, ny, nz = 48, 36, 30
+    p = synth.varcoef(nx, ny, nz, seed=13)
+    out = []
+    for f64 in (False, True):
+        with s7.stencil7_create(nx, ny, nz, gu.coef_on_device(p), storage=storage,
+                                residual_f64=f64) as op:
+            out.append(s7.bicgstab_solve(op, gu.to_dev(p.b), tol=1e-5, maxit=400))
+    assert out[0].iters == out[1].iters
+    assert np.array_equal(out[0].x.cpu().numpy(), out[1].x.cpu().numpy())
+    assert out[0].true_resid == pytest.approx(out[1].true_resid, rel=1e-6)
+
+
+def test_refined_solve_binary64_residuals(s7):
+    nx, ny, nz = 40, 33, 29
+    p = synth.varcoef(nx, ny, nz, seed=6)
+    b64 = p.b.astype(np.float64)
+    with s7.stencil7_create(nx, ny, nz, gu.coef_on_device(p), storage="f16", keep_true=True,
+                            residual_f64=True) as op:
+        res = s7.bicgstab_solve_refined(op, gu.to_dev(b64), tol=1e-12, max_outer=60,
+                                        inner_maxit=100, inner_tol=1e-2)
+        x = res.x.cpu().numpy()
+    assert res.status == 0 and res.hist[-1] <= 1e-12
+    assert ob.true_residual(nx, ny, nz, p.coef, b64, x) <= 1.5e-12
+
+
 def test_double_word_residual9_under_cancellation(s7):
     from oracle import stencil9
     nx, ny = 90, 61
@@ -359,7 +407,8 @@ def test_double_word_residual9_under_cancellation(s7):
     assert np.max(np.abs(r64.cpu().numpy() - ref) / mag) < 2e-13
 
 
-def test_float64_residual_of_float32_data_is_exact(s7):
+@pytest.mark.parametrize("f64", [False, True])
+def test_float64_residual_of_float32_data_is_exact(s7, f64):
     """The residual sweeps take float32 data exactly (double words whose low
     part is zero; products of two float32 numbers are exact double words), so
     the residual norm of float32 data matches the oracle's to the double-word
@@ -374,7 +423,7 @@ def test_float64_residual_of_float32_data_is_exact(s7):
     ref = p.b.astype(np.float64) - stencil.apply(nx, ny, nz, p.coef, x.astype(np.float64))
     for keep in (True, False):
         with s7.stencil7_create(nx, ny, nz, gu.coef_on_device(p), storage="f32",
-                                keep_true=keep) as op:
+                                keep_true=keep, residual_f64=f64) as op:
             r = gu.to_dev(np.zeros(p.n, np.float32))
             rn, bn = s7.stencil7_residual(op, gu.to_dev(p.b), gu.to_dev(x), r)
         if keep:
