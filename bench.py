@@ -661,7 +661,8 @@ def run_batched(args):
     for j, e in enumerate(edges):
         p = synth.varcoef(e, e, e, seed=synth.system_seed(1, j))
         ops.append(s7.stencil7_create(e, e, e, {k: torch.from_numpy(v).to(dev)
-                                                for k, v in p.coef.items()}, storage="f32"))
+                                                for k, v in p.coef.items()}, storage="f32",
+                                      variant=args.variant))
         bs.append(torch.from_numpy(p.b).to(dev))
     cells = [e ** 3 for e in edges]
     xs = [torch.zeros_like(b) for b in bs]
@@ -685,7 +686,9 @@ def run_batched(args):
     seq_s = time.perf_counter() - t0
     out = {"metric": "batched cell-iters/s (512 systems, edges 16..128, FP32, tol 1e-6)",
            "value": ci / (ms / 1e3), "unit": "cell-iters/s", "higher_is_better": True,
-           "workload": "batched_%d" % args.systems, "dtype": "f32", "data": "synthetic (seed 1)",
+           "workload": "batched_%d%s" % (args.systems, "_merged" if args.variant else ""),
+           "variant": "two reductions per step" if args.variant else "Algorithm 1",
+           "dtype": "f32", "data": "synthetic (seed 1)",
            "ms_per_batch_solve": ms, "systems": len(ops), "total_cells": int(sum(cells)),
            "iters_min_max": [min(r.iters), max(r.iters)], "all_converged": r.rc == 0,
            "hbm_gbs": 116 * ci / (ms / 1e3) / 1e9,

@@ -121,7 +121,10 @@ typedef struct {
                         r_{i+1}) directly, which the next step starts from
                         (two passes, 104 instead of 116 bytes per cell in
                         float32; same iterates in exact arithmetic).
-                        Single solves only; batched and served solves use 0. */
+                        bicgstab_solve_batched runs it when every system
+                        of the batch was created with it (a batch mixing
+                        variants is S7_EINVAL); the server has its own
+                        option (s7_server_opts.three_pass). */
   int step_cells;    /* cells per thread in the pipelined sweeps: the width
                         of the other sweeps (4; 2 for float64), or for 16-bit
                         storage 8 (one 16-byte copy per array and thread);
@@ -291,7 +294,9 @@ typedef struct {
   int no_autotune;  /* 1: skip the autotuner (use threads/zchunk or 128/16)  */
 } s7_batch_opts;
 
-/* Solve nsys independent systems together (BiCGStab, Algorithm 1, on each).
+/* Solve nsys independent systems together (BiCGStab, Algorithm 1, on each;
+ * or the two-reduction variant when every handle was created with
+ * s7_opts.variant = 1).
  * One launch per kernel of a step covers every system: each system owns a
  * range of the launch's blocks and its own grid combine, scalars and stop
  * flag, so systems of different sizes and tolerances share the launches and

@@ -226,29 +226,46 @@ static void dfree(Handle* h, void** p, size_t bytes) {
   *p = nullptr;
 }
 
-// Pinned host mirrors of a handle's scalars (two Scalars each), kept on a
-// free list for the next handle: freeing pinned memory synchronises the
-// whole device.
+// Pinned host buffers (scalar mirrors of handles and batches), kept on a free
+// list for reuse: freeing pinned memory synchronises the whole device.
 static std::mutex g_pin_mu;
-static std::vector<Scalars*> g_pin_free;
+static std::vector<std::pair<void*, size_t>> g_pin_free;
+static std::map<void*, size_t> g_pin_size;   // capacity of every buffer made here
 
-static cudaError_t pinned_scalars(Scalars** out) {
+static cudaError_t pinned_get(void** out, size_t bytes) {
   {
     std::lock_guard<std::mutex> lk(g_pin_mu);
-    if (!g_pin_free.empty()) {
-      *out = g_pin_free.back();
-      g_pin_free.pop_back();
+    size_t best = g_pin_free.size();
+    for (size_t i = 0; i < g_pin_free.size(); ++i)
+      if (g_pin_free[i].second >= bytes &&
+          (best == g_pin_free.size() || g_pin_free[i].second < g_pin_free[best].second))
+        best = i;
+    if (best < g_pin_free.size()) {
+      *out = g_pin_free[best].first;
+      g_pin_free.erase(g_pin_free.begin() + best);
       return cudaSuccess;
     }
   }
-  return cudaMallocHost((void**)out, 2 * sizeof(Scalars));
+  const size_t cap = std::max(bytes, (size_t)4096);
+  cudaError_t e = cudaMallocHost(out, cap);
+  if (e == cudaSuccess) {
+    std::lock_guard<std::mutex> lk(g_pin_mu);
+    g_pin_size[*out] = cap;
+  }
+  return e;
 }
 
-static void pinned_scalars_put(Scalars* p) {
+static void pinned_put(void* p) {
   if (!p) return;
   std::lock_guard<std::mutex> lk(g_pin_mu);
-  g_pin_free.push_back(p);
+  g_pin_free.emplace_back(p, g_pin_size[p]);
 }
+
+static cudaError_t pinned_scalars(Scalars** out) {
+  return pinned_get((void**)out, 2 * sizeof(Scalars));
+}
+
+static void pinned_scalars_put(Scalars* p) { pinned_put(p); }
 
 extern "C" int s7_mem_stats(int device, size_t* reserved, size_t* used) {
   cudaMemPool_t pool;
@@ -1315,6 +1332,8 @@ Tile batch_tile(const Handle* h, int vec, const BatchPolicy& p) {
   return t;
 }
 
+// Buffers of one batched solve, from the library's pools; released when the
+// solve returns, after its stream has synchronised.
 struct BatchBuffers {
   Scalars* sc = nullptr;
   Scalars* h_sc = nullptr;
@@ -1323,11 +1342,11 @@ struct BatchBuffers {
   void* desc = nullptr;
   std::vector<unsigned char> h_desc;
   ~BatchBuffers() {
-    if (sc) cudaFree(sc);
-    if (h_sc) cudaFreeHost(h_sc);
-    if (hist) cudaFree(hist);
-    if (parts) cudaFree(parts);
-    if (desc) cudaFree(desc);
+    dev_free(sc, nullptr);
+    pinned_put(h_sc);
+    dev_free(hist, nullptr);
+    dev_free(parts, nullptr);
+    dev_free(desc, nullptr);
   }
 };
 
@@ -1339,9 +1358,9 @@ struct BatchBuffers {
 static int batch_layout(int nsys, Handle* const* hs, const void* const* bdev, const Engine* eng,
                         const BatchPolicy& p, BatchBuffers& bb, const std::vector<size_t>& hist_off,
                         const std::vector<size_t>& parts_off, int* sweep_blocks, int* upd_blocks,
-                        size_t smem[4], int pipe, cudaStream_t st) {
+                        size_t smem[8], int pipe, cudaStream_t st) {
   int b0 = 0, u0 = 0;
-  for (int k = 0; k < 4; ++k) smem[k] = 0;
+  for (int k = 0; k < 8; ++k) smem[k] = 0;
   for (int j = 0; j < nsys; ++j) {
     const Tile t = batch_tile(hs[j], pipe ? eng->vec_wide : eng->vec, p);
     int nb = 0, ub = 0;
@@ -1350,7 +1369,8 @@ static int batch_layout(int nsys, Handle* const* hs, const void* const* bdev, co
                    pipe);
     b0 += nb;
     u0 += ub;
-    for (int k = 0; k < 4; ++k) smem[k] = std::max(smem[k], eng->batched_smem(hs[j], t, pipe, k));
+    for (int k = 0; k < 8; ++k)
+      if (k != 4 && k != 5) smem[k] = std::max(smem[k], eng->batched_smem(hs[j], t, pipe, k));
   }
   *sweep_blocks = b0;
   *upd_blocks = u0;
@@ -1387,6 +1407,11 @@ extern "C" int bicgstab_solve_batched(int nsys, const stencil7_t* hs_in, const v
     if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end())
       return fail(S7_EINVAL, "bicgstab_solve_batched: a handle appears twice");
   }
+  // the two-reduction variant when the handles were created with it
+  const int merged = hs[0]->variant;
+  for (int j = 1; j < nsys; ++j)
+    if (hs[j]->variant != merged)
+      return fail(S7_EINVAL, "bicgstab_solve_batched: systems created with different variants");
   bind_handle_device(hs[0]);
   const Engine* eng = engine_for(hs[0]->storage);
   const s7_dtype xt = xtype(hs[0]);
@@ -1406,7 +1431,7 @@ extern "C" int bicgstab_solve_batched(int nsys, const stencil7_t* hs_in, const v
   size_t hist_total = 0, parts_total = 0;
   long long cells = 0;
   int sweep_blocks = 0, upd_blocks = 0, threads = 128;
-  size_t smem[4] = {0, 0, 0, 0};  // by launch kind
+  size_t smem[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // by launch kind
   BatchPolicy pol{128, 16};
   const int ce = opts.check_every > 0 ? opts.check_every : 16;
   cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
@@ -1450,15 +1475,16 @@ extern "C" int bicgstab_solve_batched(int nsys, const stencil7_t* hs_in, const v
     }
     bb.h_desc.resize((size_t)nsys * eng->desc_size);
     void* p = nullptr;
-    if ((e = cudaMalloc(&p, (size_t)nsys * sizeof(Scalars))) != cudaSuccess) { rc = cuda_fail(e, "batch scalars"); goto out; }
+    const int dev = hs[0]->device;
+    if ((e = dev_alloc(dev, &p, (size_t)nsys * sizeof(Scalars), st)) != cudaSuccess) { rc = cuda_fail(e, "batch scalars"); goto out; }
     bb.sc = (Scalars*)p;
-    if ((e = cudaMallocHost(&p, (size_t)nsys * sizeof(Scalars))) != cudaSuccess) { rc = cuda_fail(e, "batch scalars (host)"); goto out; }
+    if ((e = pinned_get(&p, (size_t)nsys * sizeof(Scalars))) != cudaSuccess) { rc = cuda_fail(e, "batch scalars (host)"); goto out; }
     bb.h_sc = (Scalars*)p;
-    if ((e = cudaMalloc(&p, hist_total * 8)) != cudaSuccess) { rc = cuda_fail(e, "batch history"); goto out; }
+    if ((e = dev_alloc(dev, &p, hist_total * 8, st)) != cudaSuccess) { rc = cuda_fail(e, "batch history"); goto out; }
     bb.hist = (double*)p;
-    if ((e = cudaMalloc(&p, parts_total * 8)) != cudaSuccess) { rc = cuda_fail(e, "batch partials"); goto out; }
+    if ((e = dev_alloc(dev, &p, parts_total * 8, st)) != cudaSuccess) { rc = cuda_fail(e, "batch partials"); goto out; }
     bb.parts = (double*)p;
-    if ((e = cudaMalloc(&p, (size_t)nsys * eng->desc_size)) != cudaSuccess) { rc = cuda_fail(e, "batch descriptors"); goto out; }
+    if ((e = dev_alloc(dev, &p, (size_t)nsys * eng->desc_size, st)) != cudaSuccess) { rc = cuda_fail(e, "batch descriptors"); goto out; }
     bb.desc = p;
   }
   // policy: explicit, cached, or autotuned with a batched SpMV probe
@@ -1492,7 +1518,7 @@ extern "C" int bicgstab_solve_batched(int nsys, const stencil7_t* hs_in, const v
           if ((rc = batch_layout(nsys, hs.data(), bdev.data(), eng, c, bb, hist_off, parts_off,
                                  &sweep_blocks, &upd_blocks, smem, pipe, st)))
             goto tune_out;
-          if (eng->batched_prepare(*std::max_element(smem, smem + 4), pipe)) { rc = fail(S7_ECUDA, "batched kernel attributes"); goto tune_out; }
+          if (eng->batched_prepare(*std::max_element(smem, smem + 8), pipe)) { rc = fail(S7_ECUDA, "batched kernel attributes"); goto tune_out; }
           // warm, then time two probes
           if ((rc = eng->launch_batched(3, bb.desc, nsys, sweep_blocks, c.threads, smem[3], st, pipe))) goto tune_out;
           cudaEventRecord(e0, st);
@@ -1520,7 +1546,7 @@ extern "C" int bicgstab_solve_batched(int nsys, const stencil7_t* hs_in, const v
   if ((rc = batch_layout(nsys, hs.data(), bdev.data(), eng, pol, bb, hist_off, parts_off,
                          &sweep_blocks, &upd_blocks, smem, pipe, st)))
     goto out;
-  if (eng->batched_prepare(*std::max_element(smem, smem + 4), pipe)) { rc = fail(S7_ECUDA, "batched kernel attributes"); goto out; }
+  if (eng->batched_prepare(*std::max_element(smem, smem + 8), pipe)) { rc = fail(S7_ECUDA, "batched kernel attributes"); goto out; }
   // scalars: tol, maxit
   for (int j = 0; j < nsys; ++j) {
     Scalars& s = bb.h_sc[j];
@@ -1531,7 +1557,10 @@ extern "C" int bicgstab_solve_batched(int nsys, const stencil7_t* hs_in, const v
   }
   if ((e = cudaMemcpyAsync(bb.sc, bb.h_sc, (size_t)nsys * sizeof(Scalars), cudaMemcpyHostToDevice, st)) != cudaSuccess) { rc = cuda_fail(e, "scalars"); goto out; }
   if ((rc = eng->launch_batched(2, bb.desc, nsys, sweep_blocks, threads, smem[2], st, pipe)) ||
-      (rc = eng->launch_batched(5, bb.desc, nsys, 0, 0, 0, st, pipe))) {
+      (rc = eng->launch_batched(5, bb.desc, nsys, 0, 0, 0, st, pipe)) ||
+      // the two-reduction variant starts with s_0 = A p_0 and (r0, s_0)
+      (merged && (rc = eng->launch_batched(0, bb.desc, nsys, sweep_blocks, threads, smem[0], st,
+                                           pipe)))) {
     rc = fail(rc, "batched start launch failed: %s", cudaGetErrorString(cudaGetLastError()));
     goto out;
   }
@@ -1540,6 +1569,12 @@ extern "C" int bicgstab_solve_batched(int nsys, const stencil7_t* hs_in, const v
     cudaGraph_t g = nullptr;
     if ((e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) { rc = cuda_fail(e, "capture"); goto out; }
     for (int k = 0; k < ce && rc == S7_OK; ++k) {
+      if (merged) {
+        // q/y pass, then the x, r updates fused with the next step's p/s pass
+        rc = eng->launch_batched(6, bb.desc, nsys, sweep_blocks, threads, smem[6], st, pipe);
+        if (!rc) rc = eng->launch_batched(7, bb.desc, nsys, sweep_blocks, threads, smem[7], st, pipe);
+        continue;
+      }
       rc = eng->launch_batched(0, bb.desc, nsys, sweep_blocks, threads, smem[0], st, pipe);
       if (!rc) rc = eng->launch_batched(1, bb.desc, nsys, sweep_blocks, threads, smem[1], st, pipe);
       if (!rc) rc = eng->launch_batched(4, bb.desc, nsys, upd_blocks, 256, 0, st, pipe);

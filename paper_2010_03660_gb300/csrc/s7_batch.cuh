@@ -59,7 +59,11 @@ __device__ __forceinline__ int find_system(const D* sys, int nsys, int blk, bool
 
 // KIND 0: p update + s = A p + (r0,s) -> alpha.  KIND 1: q + y = A q +
 // (q,y),(y,y) -> omega.  KIND 2: start residual r0 = D^-1 b - A x0.
-// KIND 3: y = A r (timing probe of the autotuner; no reductions).
+// KIND 3: y = A r (timing probe of the autotuner; no reductions).  The two
+// passes of the two-reduction variant (systems created with variant 1):
+// KIND 4: q + y = A q + (q,y),(y,y),(r0,y) -> omega, beta from the rho
+// recurrence; KIND 5: x, r updates fused with p + s = A p of the next step
+// + (r0,s),(r,r),(r0,r) -> alpha, history, stop test.
 template <class T, class X, class DT, class A, int VEC, int KIND>
 __global__ void __launch_bounds__(256) k_sweep_batched(const SysDesc<T, X>* __restrict__ sys,
                                                        int nsys) {
@@ -70,7 +74,7 @@ __global__ void __launch_bounds__(256) k_sweep_batched(const SysDesc<T, X>* __re
   __syncthreads();
   const SysDesc<T, X>& d = sys[s_sys];
   Scalars* sc = d.sc;
-  if ((KIND == 0 || KIND == 1) && *((volatile int*)&sc->done)) return;
+  if ((KIND == 0 || KIND == 1 || KIND == 4 || KIND == 5) && *((volatile int*)&sc->done)) return;
   const int bid = (int)blockIdx.x - d.block0;
   const Geom g = d.g;
   CoefView<T, A> cf;
@@ -121,11 +125,38 @@ __global__ void __launch_bounds__(256) k_sweep_batched(const SysDesc<T, X>* __re
     epi.mode = 0;
     if (d.vl) sweep_body<T, A, VEC, true>(g, cf, src, epi, sc, bid, d.nblocks, sm, red);
     else sweep_body<T, A, VEC, false>(g, cf, src, epi, sc, bid, d.nblocks, sm, red);
-  } else {
+  } else if (KIND == 3) {
     SrcPlain<T, A> src{d.r};
     EpiStore<T, A> epi{d.y};
     if (d.vl) sweep_body<T, A, VEC, true>(g, cf, src, epi, nullptr, bid, d.nblocks, sm, red);
     else sweep_body<T, A, VEC, false>(g, cf, src, epi, nullptr, bid, d.nblocks, sm, red);
+  } else if (KIND == 4) {
+    SrcQ2<T, A> src;
+    src.rbuf[0] = d.r;
+    src.rbuf[1] = d.r2;
+    src.sbuf[0] = d.s[0];
+    src.sbuf[1] = d.s[1];
+    EpiYMerged<T, A> epi;
+    epi.y_out = d.y;
+    epi.rh = d.rh;
+    epi.parts = d.parts;
+    if (d.vl) sweep_body<T, A, VEC, true>(g, cf, src, epi, sc, bid, d.nblocks, sm, red);
+    else sweep_body<T, A, VEC, false>(g, cf, src, epi, sc, bid, d.nblocks, sm, red);
+  } else {
+    MergedPass<T, X, A> m;
+    m.rbuf[0] = d.r;
+    m.rbuf[1] = d.r2;
+    m.pbuf[0] = d.p[0];
+    m.pbuf[1] = d.p[1];
+    m.sbuf[0] = d.s[0];
+    m.sbuf[1] = d.s[1];
+    m.y = d.y;
+    m.rh = d.rh;
+    m.x = d.x;
+    m.parts = d.parts;
+    m.hist = d.hist;
+    if (d.vl) sweep_body<T, A, VEC, true>(g, cf, m, m, sc, bid, d.nblocks, sm, red);
+    else sweep_body<T, A, VEC, false>(g, cf, m, m, sc, bid, d.nblocks, sm, red);
   }
 }
 

@@ -884,10 +884,12 @@ struct EngineImpl {
 
   static int batched_prepare(size_t smem, int pipe) {
     if (smem <= kSmemNoOptIn) return S7_OK;
-    const void* reg[4] = {(const void*)k_sweep_batched<T, X, DT, A, VEC, 0>,
+    const void* reg[6] = {(const void*)k_sweep_batched<T, X, DT, A, VEC, 0>,
                           (const void*)k_sweep_batched<T, X, DT, A, VEC, 1>,
                           (const void*)k_sweep_batched<T, X, DT, A, VEC, 2>,
-                          (const void*)k_sweep_batched<T, X, DT, A, VEC, 3>};
+                          (const void*)k_sweep_batched<T, X, DT, A, VEC, 3>,
+                          (const void*)k_sweep_batched<T, X, DT, A, VEC, 4>,
+                          (const void*)k_sweep_batched<T, X, DT, A, VEC, 5>};
     const void* wide[7] = {(const void*)k_step_batched<T, X, A, VW, 0, SB>,
                            (const void*)k_step_batched<T, X, A, VW, 1, SB>,
                            (const void*)k_step_batched<T, X, A, VW, 2, SB>,
@@ -896,7 +898,7 @@ struct EngineImpl {
                            (const void*)k_sweep_batched<T, X, DT, A, VW, 2>,
                            (const void*)k_sweep_batched<T, X, DT, A, VW, 3>};
     const void* const* ks = pipe ? wide : reg;
-    const int nk = pipe ? 7 : 4;
+    const int nk = pipe ? 7 : 6;
     for (int k = 0; k < nk; ++k)
       if (cudaFuncSetAttribute(ks[k], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
           cudaSuccess)
@@ -907,7 +909,6 @@ struct EngineImpl {
   static int launch_batched(int kind, const void* descs, int nsys, int blocks, int threads,
                             size_t smem, cudaStream_t st, int pipe) {
     const Desc* d = (const Desc*)descs;
-    if (kind >= 6 && !pipe) return S7_EINVAL;
     if (pipe && (kind <= 3 || kind >= 6)) {
       switch (kind) {
         case 0: k_step_batched<T, X, A, VW, 0, SB><<<blocks, threads, smem, st>>>(d, nsys); break;
@@ -929,6 +930,8 @@ struct EngineImpl {
       case 3: k_sweep_batched<T, X, DT, A, VEC, 3><<<blocks, threads, smem, st>>>(d, nsys); break;
       case 4: k_update_batched<T, X, A, VEC><<<blocks, 256, 0, st>>>(d, nsys); break;
       case 5: k_hist0_batched<T, X><<<(nsys + 127) / 128, 128, 0, st>>>(d, nsys); break;
+      case 6: k_sweep_batched<T, X, DT, A, VEC, 4><<<blocks, threads, smem, st>>>(d, nsys); break;
+      case 7: k_sweep_batched<T, X, DT, A, VEC, 5><<<blocks, threads, smem, st>>>(d, nsys); break;
       default: return S7_EINVAL;
     }
     return cudaGetLastError() == cudaSuccess ? S7_OK : S7_ECUDA;

@@ -208,3 +208,51 @@ def test_pipelined_16bit_batch(s7, storage):
     finally:
         for op in ops:
             op.close()
+
+
+@pytest.mark.parametrize("storage,shapes", [
+    ("f32", SHAPES),                                              # ragged: register sweeps
+    ("f32", [(16, 16, 16), (24, 20, 12), (32, 9, 30), (8, 8, 64)]),   # whole rows: pipelined
+    ("bf16", [(16, 16, 16), (24, 20, 12), (32, 9, 30), (8, 8, 64)]),
+])
+def test_batched_two_reduction_variant(s7, storage, shapes):
+    """Handles created with variant 1 run the two-reduction form in the batch:
+    every system matches the oracle's form of that variant at its tolerance,
+    and alone or in the mix it gives the same bits (fixed launch policy)."""
+    probs = make(shapes, 300)
+    tol = 1e-6 if storage == "f32" else 1e-2
+    ops = [s7.stencil7_create(p.nx, p.ny, p.nz, gu.coef_on_device(p), storage=storage,
+                              variant=1) for p in probs]
+    try:
+        kw = dict(tol=tol, maxit=1000, threads=128, zchunk=16)
+        res = s7.bicgstab_solve_batched(ops, [gu.to_dev(p.b) for p in probs], **kw)
+        assert all(st == 0 for st in res.status), res.status
+        for j, p in enumerate(probs):
+            orc = ob.bicgstab_merged(p.nx, p.ny, p.nz, p.coef, p.b, tol=tol, maxit=1000,
+                                     storage=storage)
+            x = res.x[j].cpu().numpy()
+            assert res.resid[j] <= tol
+            win = max(6, orc.iters // 4) if storage == "f32" else max(10, orc.iters // 2)
+            assert abs(res.iters[j] - orc.iters) <= win, j
+            if storage == "f32":
+                assert rel(x, orc.x) <= 100 * tol, (j, rel(x, orc.x))
+                assert ob.true_residual(p.nx, p.ny, p.nz, p.coef, p.b, x) <= 10 * tol
+        alone = s7.bicgstab_solve_batched([ops[1]], [gu.to_dev(probs[1].b)], **kw)
+        assert alone.iters[0] == res.iters[1]
+        assert np.array_equal(alone.x[0].cpu().numpy(), res.x[1].cpu().numpy())
+    finally:
+        for op in ops:
+            op.close()
+
+
+def test_batched_variants_must_agree(s7):
+    probs = make([(12, 10, 8), (9, 9, 9)], 400)
+    ops = [s7.stencil7_create(p.nx, p.ny, p.nz, gu.coef_on_device(p), storage="f32",
+                              variant=j) for j, p in enumerate(probs)]
+    try:
+        with pytest.raises(s7.S7Error) as e:
+            s7.bicgstab_solve_batched(ops, [gu.to_dev(p.b) for p in probs], tol=1e-6, maxit=100)
+        assert e.value.code == s7.EINVAL
+    finally:
+        for op in ops:
+            op.close()
