@@ -229,7 +229,7 @@ __device__ __forceinline__ void sweep_body(const Geom& g, const CoefView<CT, A>&
         acc = fma(c[3][j], dn[j], acc);
         acc = fma(c[4][j], vm[j], acc);
         acc = fma(c[5][j], vp[j], acc);
-        out[j] = acc;
+        out[j] = settle(acc);
       }
       epi.template consume<VEC, VL>(ib, nv, out, vc);
     }
@@ -502,8 +502,7 @@ struct EpiResid {
   double* parts;
   int counter;       // which Scalars counter
   int mode;          // 0: start of a solve (sets scalars); 1: stores totals in res[0..1]
-  typedef typename NormOf<A>::t N;
-  DotAcc<N, 2> acc;
+  SqAcc<A, 2> acc;
   A bv[8];
   A dv[8];
   __device__ void setup(const Scalars*) { acc.init(); }
@@ -536,11 +535,9 @@ struct EpiResid {
       rv[k] = as_stored<T>(rk);
       // a solve's start residual enters the recurrence as stored; a reported
       // residual's norm is that of the unrounded value
-      const N rn = to_norm<N>(mode == 0 ? rv[k] : rk);
-      const N bn = to_norm<N>(rhs);
       if (k < nv) {
-        acc.part[0] = fma(rn, rn, acc.part[0]);
-        acc.part[1] = fma(bn, bn, acc.part[1]);
+        acc.add_sq(0, mode == 0 ? rv[k] : rk);
+        acc.add_sq(1, rhs);
       }
     }
     if (r_out) store_run<T, VEC, VL>(r_out + i, nv, rv);

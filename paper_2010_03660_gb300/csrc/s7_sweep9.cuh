@@ -133,7 +133,7 @@ __device__ __forceinline__ void sweep9_body(const Geom& g, const CoefView9<CT, A
         acc = fma(c[5][j], r_m, acc);
         acc = fma(c[6][j], l_p, acc);
         acc = fma(c[7][j], r_p, acc);
-        out[j] = acc;
+        out[j] = settle(acc);
       }
       epi.template consume<VEC, VL>(ib, nv, out, vc);
     }
