@@ -419,9 +419,9 @@ int stencil7_profile(stencil7_t h, int enable, double* ms, long long* launches);
  * by live handles (either pointer may be NULL).  S7_ECUDA for a bad device. */
 int s7_mem_stats(int device, size_t* reserved, size_t* used);
 
-/* Synchronise the current device and return the cached blocks of the pool
- * of `device` to it, keeping at most `keep` reserved bytes (blocks in use
- * stay).  S7_ECUDA for a bad device. */
+/* Synchronise `device` and return the cached blocks of its pool to it,
+ * keeping at most `keep` reserved bytes (blocks in use stay).  The calling
+ * thread's current device is left as it was.  S7_ECUDA for a bad device. */
 int s7_mem_trim(int device, size_t keep);
 
 /* Most bytes each pool keeps reserved after the synchronisation that

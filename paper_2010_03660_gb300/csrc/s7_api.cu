@@ -284,8 +284,13 @@ extern "C" int s7_mem_trim(int device, size_t keep) {
   cudaMemPool_t pool;
   cudaError_t e = pool_of(device, &pool);
   if (e != cudaSuccess) return cuda_fail(e, "s7_mem_trim");
-  if ((e = cudaDeviceSynchronize()) != cudaSuccess) return cuda_fail(e, "s7_mem_trim");
-  if ((e = cudaMemPoolTrimTo(pool, keep)) != cudaSuccess) return cuda_fail(e, "s7_mem_trim");
+  int cur = -1;
+  cudaGetDevice(&cur);
+  if (cur != device && (e = cudaSetDevice(device)) != cudaSuccess) return cuda_fail(e, "s7_mem_trim");
+  e = cudaDeviceSynchronize();   // frees still queued on the device's streams
+  if (e == cudaSuccess) e = cudaMemPoolTrimTo(pool, keep);
+  if (cur >= 0 && cur != device) cudaSetDevice(cur);
+  if (e != cudaSuccess) return cuda_fail(e, "s7_mem_trim");
   return S7_OK;
 }
 

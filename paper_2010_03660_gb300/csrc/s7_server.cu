@@ -194,11 +194,14 @@ Tile serve_tile(const s7_server* S, int nx, int ny, int nz, int pipe) {
   return t;
 }
 
-// Retire a request whose work is complete on both server streams (the
-// scheduler synchronised its stream; admission synchronises its own before a
-// request becomes active).  Its blocks go back to the library's pool without
-// a device-wide synchronisation, which would stall the other thread's work.
+// Retire a request.  Its work on the scheduler's stream is finished first
+// (a no-op after a normal completion, which synchronised it; needed when a
+// failure or cancellation retires a request with launches still queued);
+// admission synchronises its own stream before a request becomes active.  The
+// blocks then go back to the library's pool without a device-wide
+// synchronisation, which would stall the other thread's work.
 void release_req(s7_server* S, Req* r) {
+  if (S->st) cudaStreamSynchronize(S->st);
   dev_free(r->xr, S->st);
   dev_free(r->br, S->st);
   dev_free(r->rr, S->st);
