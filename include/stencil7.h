@@ -18,8 +18,8 @@
  *   the six off-diagonals named by axis and sign as in Sec. IV-A; a
  *   neighbour outside the mesh contributes zero (homogeneous Dirichlet).
  * Diagonal preconditioning.  By default the library stores the operator with
- *   a unit main diagonal, A~ = D^-1 A (Sec. IV: "with diagonal preconditioning
- *   the main diagonal is all ones", so six diagonals are stored); each
+ *   a unit main diagonal, A~ = D^-1 A (Sec. IV scales the operator by its
+ *   diagonal, which leaves ones there, and stores the six others); each
  *   off-diagonal is divided by its row's diagonal in float64 and rounded once
  *   (round to nearest even) to the storage type.  Solves then run on
  *   A~ x = D^-1 b, which has the same solution; tolerances and residual
@@ -212,15 +212,16 @@ int stencil7_info(stencil7_t h, int* nx, int* ny, int* nz, s7_dtype* storage,
  * buffers the call is asynchronous on `stream`. */
 int stencil7_apply(stencil7_t h, const void* x, void* y, s7_dtype dt, void* stream);
 
-/* True residual of the raw system, r = b - A x, accumulated in float64 from
- * the raw float32 coefficients when the handle keeps them (keep_true), else
- * from the stored operator times the kept diagonal.  b and x hold nx*ny*nz
+/* True residual of the raw system, r = b - A x, with float64 accuracy (double
+ * words by default, binary64 with opts.residual_f64) from the raw float32
+ * coefficients when the handle keeps them (keep_true), else from the stored
+ * operator times the kept diagonal.  b and x hold nx*ny*nz
  * elements of `dt` (S7_F64 or S7_F32).  r (same type) may be NULL.  Returns
  * ||r||_2 in *rnorm and ||b||_2 in *bnorm (either may be NULL); synchronous. */
 int stencil7_residual(stencil7_t h, const void* b, const void* x, void* r,
                       s7_dtype dt, double* rnorm, double* bnorm, void* stream);
 
-/* The same residual as stencil7_residual (same float64 sweep, same results),
+/* The same residual as stencil7_residual (same sweep, same results),
  * for callers that must not allocate device memory when they call: services
  * that reserve their whole device-memory budget at start-up (a pool that owns
  * the memory, where a cudaMalloc would fail or fragment it), latency-bound
@@ -258,7 +259,7 @@ int stencil7_residual_noalloc(stencil7_t h, const void* b, const void* x, void* 
  *   resid_hist  out (host, may be NULL): *iters+1 values, resid_hist[k] =
  *          ||r_k|| / ||b~|| (caller provides maxit+1 doubles).
  *   true_resid  out (may be NULL): ||b~ - A~ x|| / ||b~|| recomputed from x at
- *          the end with float64 accumulation.
+ *          the end with float64 accuracy (see opts.residual_f64).
  * Every step runs as three fused sweeps (p update + SpMV + (r0,s); q + SpMV +
  * (q,y),(y,y); x and r updates + (r0,r),(r,r)), each ending in a
  * deterministic grid-level combine of per-block partial sums in float64; the
@@ -271,8 +272,8 @@ int bicgstab_solve(stencil7_t h, const void* b, void* x, s7_dtype dt,
 /* Mixed-precision solve with float64 iterative refinement.  The paper notes
  * that 16-bit solves plateau near a relative residual of 1e-2 (Sec. VI-B) and
  * that they may need a correction scheme such as iterative refinement.  Outer
- * loop: r = b - A x in float64 on the true operator (keep_true, float32
- * coefficients); stop when ||r|| / ||b|| <= tol; else solve A~ d = D^-1 r / s
+ * loop: r = b - A x with float64 accuracy (see opts.residual_f64) on the true
+ * operator (keep_true, float32 coefficients); stop when ||r|| / ||b|| <= tol; else solve A~ d = D^-1 r / s
  * with the handle's storage precision (s = ||r||_2 / sqrt(N), so the inner
  * right-hand side has unit RMS and stays inside binary16's normal range) to
  * inner_tol or inner_maxit steps, and update x += s d in float64.

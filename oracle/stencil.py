@@ -13,8 +13,8 @@ off-diagonal vectors are named by axis and sign (Sec. IV-A, "SpMV (3D)":
 with a neighbour outside the mesh contributing zero (homogeneous Dirichlet
 boundary).  Storage is x-fastest: ``i = x + nx*(y + ny*z)``.
 
-With diagonal preconditioning the main diagonal is all ones and only the six
-off-diagonals are stored (Sec. IV); :func:`jacobi_scale` forms that operator
+Sec. IV keeps the operator scaled by its diagonal, so the diagonal is one
+everywhere and only the six off-diagonals need storing; :func:`jacobi_scale` forms that operator
 as ``D^-1 A`` (left scaling) and rounds the scaled values once to the storage
 type.
 """

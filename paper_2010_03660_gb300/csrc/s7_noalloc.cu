@@ -1,4 +1,4 @@
-// stencil7_residual_noalloc: the float64 residual sweep of stencil7_residual
+// stencil7_residual_noalloc: the float64-accuracy residual sweep of stencil7_residual
 // for callers that cannot allocate device memory at call time.  Its scratch
 // (the per-block partial sums of the grid combine and the solver-scalar
 // block with the arrival counter and the totals) lives in a file-scope

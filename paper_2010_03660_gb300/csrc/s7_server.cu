@@ -6,7 +6,7 @@
 // runs mixed-precision BiCGStab with float64 iterative refinement as a small
 // state machine:
 //
-//   RESIDUAL  r = b - A x in float64 on the true float32 operator; stop if
+//   RESIDUAL  r = b - A x with float64 accuracy on the true float32 operator; stop if
 //             ||r||/||b|| <= tol; else start an inner solve of
 //             A~ d = D^-1 r / s (s = ||r||/sqrt(N)) in the storage precision
 //   INNER     BiCGStab steps; every request in this state shares the same

@@ -7,7 +7,7 @@ oracle cannot solve these on the host, so:
 * SpMV: sampled rows (random, mesh faces and edges, tile and chunk seams) are
   recomputed by the oracle one by one (``stencil.apply_at``) from the
   generator's values at those cells, bit-identical to the GPU's inputs.
-* Solves: the GPU's float64 residual vector r = b - A x is checked row by
+* Solves: the GPU's float64-accuracy residual vector r = b - A x is checked row by
   row against the oracle's recomputation from the GPU's x (so the residual
   norm that certifies convergence is itself verified), and the certified
   norms must meet the tolerance.
@@ -96,7 +96,7 @@ def test_config2_fullsize_solve_to_1e6(s7, config2):
     assert res.status == 0, res.status
     assert res.hist[-1] <= 1e-6 and res.hist[0] == pytest.approx(1.0, rel=1e-6)
     assert res.true_resid <= 2e-6
-    # the float64 residual of the raw system, verified row by row
+    # the float64-accuracy residual of the raw system, verified row by row
     r = torch.empty_like(b)
     rn, bn = s7.stencil7_residual(op, b, res.x, r)
     assert rn / bn <= 1e-5
