@@ -219,6 +219,25 @@ def test_bicgstab_symmetric_case_equals_cg():
     assert np.linalg.norm(res.x - xc) / np.linalg.norm(xc) < 1e-11
 
 
+def test_direct_helpers_against_lapack():
+    """The helpers that serve as pins are pinned themselves: Thomas against a
+    dense LAPACK solve of the same tridiagonal matrix (lower[i] couples row i
+    to i-1, upper[i] to i+1), CG against a dense solve of the SPD Laplacian."""
+    n = 37
+    lower = synth.random_vector(n, 41, 1, np.float64, "uniform")
+    upper = synth.random_vector(n, 41, 2, np.float64, "uniform")
+    diag = 2.5 + synth.random_vector(n, 41, 3, np.float64, "uniform")
+    rhs = synth.random_vector(n, 41, 4, np.float64, "uniform")
+    t = np.diag(diag) + np.diag(lower[1:], -1) + np.diag(upper[:-1], 1)
+    assert np.allclose(direct.thomas(lower, diag, upper, rhs), np.linalg.solve(t, rhs),
+                       rtol=1e-12, atol=1e-13)
+    nx, ny, nz = 5, 4, 6
+    lap = {"diag": 6.0, **{d: -1.0 for d in stencil.DIRS}}
+    b = synth.random_vector(nx * ny * nz, 42, 1, np.float64, "uniform")
+    xd = np.linalg.solve(stencil.assemble_dense(nx, ny, nz, lap), b)
+    assert np.linalg.norm(direct.cg(nx, ny, nz, lap, b) - xd) / np.linalg.norm(xd) < 1e-11
+
+
 def test_bicgstab_1d_equals_thomas():
     nz = 40
     coef, b = rand_coef(1, 1, nz, seed=31)
