@@ -37,6 +37,8 @@
  *   non-zero return, s7_last_error() gives a one-line description (per host
  *   thread).  A handle stays usable after S7_EBREAKDOWN / S7_ENOTCONV.
  * Threads.  A handle must not be used by two host threads at once.
+ * Devices.  An entry point that takes a handle runs on the handle's device
+ *   and leaves the calling thread's current device as it found it.
  */
 #ifndef STENCIL7_H
 #define STENCIL7_H
@@ -239,7 +241,9 @@ int stencil7_residual(stencil7_t h, const void* b, const void* x, void* r,
  *   rejected with S7_EINVAL (a larger opts.zchunk lowers the count).
  * Set-up: the first call on each device looks up the device address of the
  * scratch array (once per device, under a lock); make that first call
- * before any stream capture.  All calls share the one array, which keeps
+ * before any stream capture.  The address is kept for the rest of the
+ * process: do not use the library across a reset of the device or of its
+ * primary context (cudaDeviceReset), after which it would be stale.  All calls share the one array, which keeps
  * the last call's contents; each call clears the part that must start at
  * zero.  Calls whose work overlaps on the GPU (unordered streams or host
  * threads) race on the array: order them.  Runs on `stream`; returns after

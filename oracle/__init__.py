@@ -19,10 +19,13 @@ Modules
               closed-form Dirichlet-Laplacian eigenpairs.
 ``counts``    the paper's operation count per mesh point (Table I) and the
               byte model of one fused iteration.
+``fp32model`` Algorithm 1 under a float32 rounding model with a chosen
+              summation order: bounds the step count of a float32 solve
+              (a model of rounding, not a reference for values).
 
 Parity status: every function here is pinned by a ``-m "not gpu"`` test
 against closed forms, brute force or a library routine (see ``tests/``),
 except where a function's docstring says "parity unpinned".
 """
 
-from . import counts, direct, stencil, bicgstab  # noqa: F401
+from . import counts, direct, stencil, bicgstab, fp32model  # noqa: F401

@@ -126,11 +126,6 @@ static void bind_caller_device() {
   cudaGetLastError();
 }
 
-static void bind_handle_device(const Handle* h) {
-  int cur = -1;
-  if (cudaGetDevice(&cur) != cudaSuccess || cur != h->device) cudaSetDevice(h->device);
-  cudaGetLastError();
-}
 
 // ---------------------------------------------------------------------------
 // device memory: one stream-ordered pool per device, owned by the library.
@@ -753,7 +748,7 @@ fail9:
 
 void s7::destroy_idle(Handle* h) {
   if (!h) return;
-  bind_handle_device(h);
+  DeviceScope dev_scope(h->device);
   cudaStreamSynchronize(h->stream);
   release(h);
   delete h;
@@ -761,7 +756,7 @@ void s7::destroy_idle(Handle* h) {
 
 extern "C" int stencil7_destroy(stencil7_t h) {
   if (!h) return S7_OK;
-  bind_handle_device(h);
+  DeviceScope dev_scope(h->device);
   // work queued on the caller's streams may still read the handle's memory
   // (stencil7_apply on device buffers returns before it runs): finish it
   // before the blocks go back to the pool
@@ -894,7 +889,7 @@ extern "C" int stencil7_apply(stencil7_t h, const void* x, void* y, s7_dtype dt,
     return fail(S7_EINVAL, "stencil7_apply: dt (%d) must equal the storage type (%d)", (int)dt,
                 (int)h->storage);
   if (x == y) return fail(S7_EINVAL, "stencil7_apply: x and y must not overlap");
-  bind_handle_device(h);
+  DeviceScope dev_scope(h->device);
   const Engine* eng = engine_for(h->storage);
   cudaStream_t st = (cudaStream_t)stream;
   const bool dx = on_device(x), dy = on_device(y);
@@ -940,7 +935,7 @@ extern "C" int stencil7_residual(stencil7_t h, const void* b, const void* x, voi
                                  double* rnorm, double* bnorm, void* stream) {
   if (!h || !b || !x) return fail(S7_EINVAL, "stencil7_residual: NULL argument");
   if (dt != S7_F64 && dt != S7_F32) return fail(S7_EINVAL, "stencil7_residual: dt must be F64 or F32");
-  bind_handle_device(h);
+  DeviceScope dev_scope(h->device);
   int rc;
   if ((rc = ensure_ws(h, 0))) return rc;
   cudaStream_t us = (cudaStream_t)stream, st = h->stream;
@@ -1042,7 +1037,7 @@ static void prof_free(Handle* h) {
 
 extern "C" int stencil7_profile(stencil7_t h, int enable, double* ms, long long* launches) {
   if (!h) return fail(S7_EINVAL, "stencil7_profile: NULL handle");
-  bind_handle_device(h);
+  DeviceScope dev_scope(h->device);
   cudaStreamSynchronize(h->stream);
   prof_collect(h);
   for (int k = 0; k < S7_PROF_NKINDS; ++k) {
@@ -1196,7 +1191,7 @@ extern "C" int bicgstab_solve(stencil7_t h, const void* b, void* x, s7_dtype dt,
   if (!h || !b || !x) return fail(S7_EINVAL, "bicgstab_solve: NULL argument");
   if (dt != S7_F64 && dt != S7_F32) return fail(S7_EINVAL, "bicgstab_solve: dt must be F64 or F32");
   if (maxit < 0 || !(tol >= 0.0)) return fail(S7_EINVAL, "bicgstab_solve: bad tol or maxit");
-  bind_handle_device(h);
+  DeviceScope dev_scope(h->device);
   int rc;
   if ((rc = ensure_ws(h, maxit))) return rc;
   Workspace& w = h->ws;
@@ -1261,7 +1256,7 @@ extern "C" int bicgstab_solve_refined(stencil7_t h, const double* b, double* x, 
     return fail(S7_EINVAL, "bicgstab_solve_refined: bad tolerances or limits");
   if ((h->storage == S7_BF16 || h->storage == S7_F16) && !h->keep_true)
     return fail(S7_EINVAL, "bicgstab_solve_refined: 16-bit storage needs keep_true");
-  bind_handle_device(h);
+  DeviceScope dev_scope(h->device);
   int rc;
   if ((rc = ensure_ws(h, inner_maxit))) return rc;
   Workspace& w = h->ws;
@@ -1417,7 +1412,7 @@ extern "C" int bicgstab_solve_batched(int nsys, const stencil7_t* hs_in, const v
   for (int j = 1; j < nsys; ++j)
     if (hs[j]->variant != merged)
       return fail(S7_EINVAL, "bicgstab_solve_batched: systems created with different variants");
-  bind_handle_device(hs[0]);
+  DeviceScope dev_scope(hs[0]->device);
   const Engine* eng = engine_for(hs[0]->storage);
   const s7_dtype xt = xtype(hs[0]);
   // the pipelined step sweeps when every system qualifies

@@ -12,6 +12,28 @@ namespace s7 {
 
 struct Scalars;
 
+// Makes `dev` the calling thread's current device for the scope of an entry
+// point and gives the caller's current device back when the scope ends, so
+// a caller that works on several devices keeps the device it selected.
+class DeviceScope {
+ public:
+  explicit DeviceScope(int dev) {
+    if (cudaGetDevice(&prev_) != cudaSuccess) prev_ = -1;
+    if (prev_ != dev) changed_ = cudaSetDevice(dev) == cudaSuccess;
+    cudaGetLastError();
+  }
+  ~DeviceScope() {
+    if (changed_ && prev_ >= 0) cudaSetDevice(prev_);
+    cudaGetLastError();
+  }
+  DeviceScope(const DeviceScope&) = delete;
+  DeviceScope& operator=(const DeviceScope&) = delete;
+
+ private:
+  int prev_ = -1;
+  bool changed_ = false;
+};
+
 // Krylov workspace of one handle (allocated on first solve, reused).
 struct Workspace {
   void* r = nullptr;

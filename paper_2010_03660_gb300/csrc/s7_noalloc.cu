@@ -76,9 +76,7 @@ extern "C" int stencil7_residual_noalloc(stencil7_t h, const void* b, const void
   if (!h || !b || !x) return set_error(S7_EINVAL, "stencil7_residual_noalloc: NULL argument");
   if (dt != S7_F64 && dt != S7_F32)
     return set_error(S7_EINVAL, "stencil7_residual_noalloc: dt must be S7_F64 or S7_F32");
-  int cur = -1;
-  if (cudaGetDevice(&cur) != cudaSuccess || cur != h->device) cudaSetDevice(h->device);
-  cudaGetLastError();
+  DeviceScope dev_scope(h->device);
   if (!device_memory(b) || !device_memory(x) || (r && !device_memory(r)))
     return set_error(S7_EINVAL,
                      "stencil7_residual_noalloc: b, x and r must be device memory (host buffers "

@@ -56,3 +56,15 @@ def problem(kind, nx, ny, nz, seed, dtype=np.float32):
     if kind == "const":
         return synth.convdiff_constant(nx, ny, nz, seed=seed, dtype=dtype)
     raise ValueError(kind)
+
+
+def fp32_step_window(nx, ny, nz, coef, b, tol, maxit, oracle_iters, orders=6):
+    """Step-count window of a float32 solve: the range of the float32 rounding
+    model's step counts over `orders` summation orders, joined with the
+    float64 oracle's count, widened by max(2, 10%) (a handful of orders
+    samples, not bounds, the orders a float32 implementation may take)."""
+    from oracle import fp32model
+    lo, hi = fp32model.step_range(nx, ny, nz, coef, b, tol, maxit=maxit, orders=orders)
+    lo, hi = min(lo, oracle_iters), max(hi, oracle_iters)
+    m = max(2, lo // 10)
+    return lo - m, hi + m

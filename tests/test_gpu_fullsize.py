@@ -17,6 +17,7 @@ import numpy as np
 import pytest
 
 import synth
+from oracle import bicgstab as ob
 from oracle import stencil
 from tests import gpu_util as gu
 
@@ -107,6 +108,34 @@ def test_config2_fullsize_solve_to_1e6(s7, config2):
     # statistical: 3000 of 548M rows)
     ms = float(np.mean(gpu_at(r)(idx) ** 2))
     assert 0.2 < ms * p.n / rn ** 2 < 5.0
+
+
+def test_config2_slab_solve_matches_oracle(s7):
+    """A 600 x 595 x 64 slab of the 600 x 595 x 1536 recipe (seed 0): the full
+    xy plane, so every x/y tile, seam and face of the full-size sweeps runs,
+    and 64 planes.  FP32 solve to 1e-6 against the oracle's Algorithm 1 on
+    the same stored operator, element by element (about 150 s of oracle
+    time on one host core)."""
+    nx, ny, nz = 600, 595, 64
+    p = synth.varcoef(nx, ny, nz, seed=0)
+    with s7.stencil7_create(nx, ny, nz, gu.coef_on_device(p), storage="f32") as op:
+        res = s7.bicgstab_solve(op, gu.to_dev(p.b), tol=1e-6, maxit=1000)
+        x = res.x.cpu().numpy().astype(np.float64)
+    orc = ob.bicgstab(nx, ny, nz, p.coef, p.b, tol=1e-6, maxit=1000, storage="f32")
+    assert res.status == 0 and orc.status == 0
+    # float32 step counts of this recipe lie within [0.75, 1.1] of the float64
+    # count (float32 rounding model, tests/test_oracle.py); the mesh is too
+    # large to run the model itself
+    assert 0.75 * orc.iters <= res.iters <= 1.1 * orc.iters, (res.iters, orc.iters)
+    assert np.max(np.abs(res.hist[:6] - orc.hist[:6]) / orc.hist[:6]) < 1e-4
+    err = np.linalg.norm(x - orc.x) / np.linalg.norm(orc.x)
+    assert err <= 1e-4, err
+    # element by element, against the largest solution entry
+    assert np.max(np.abs(x - orc.x)) <= 1e-3 * np.max(np.abs(orc.x))
+    sc = stencil.jacobi_scale(nx, ny, nz, p.coef, "f32")
+    bt = stencil.scale_rhs(nx, ny, nz, p.coef, p.b)
+    tr = np.linalg.norm(bt - stencil.apply(nx, ny, nz, sc, x)) / np.linalg.norm(bt)
+    assert tr <= 2e-6 and abs(tr - res.true_resid) <= 1e-3 * tr, (tr, res.true_resid)
 
 
 @pytest.mark.parametrize("storage", ["bf16", "f16"])

@@ -429,3 +429,75 @@ def test_planted_wrong_omega_sign_is_caught(monkeypatch):
     xd = direct.dense_solve(6, 5, 4, coef, b)
     assert not (res.status == ob.OK and
                 np.linalg.norm(res.x - xd) / np.linalg.norm(xd) < 1e-8)
+
+
+# ---------------------------------------------------------------------------
+# the float32 rounding model of Algorithm 1 (oracle.fp32model)
+# ---------------------------------------------------------------------------
+
+def test_fp32_model_tracks_float64_early_and_holds_float32():
+    """Before rounding has been amplified, the float32 model follows the float64
+    oracle step for step (a dropped term, a wrong sign or a transposed operand
+    in the model would separate them at the first steps); its iterate holds
+    float32 values."""
+    from oracle import fp32model as fm
+    for shape, seed in (((20, 13, 11), 7), ((16, 16, 16), 100), ((1, 1, 40), 3)):
+        p = synth.varcoef(*shape, seed=seed)
+        o = ob.bicgstab(*shape, p.coef, p.b, tol=1e-6, maxit=300, storage="f32")
+        for order in (0, 1):
+            m = fm.bicgstab_f32(*shape, p.coef, p.b, tol=1e-6, maxit=300, order=order)
+            k = min(8, len(o.hist), len(m.hist))
+            assert np.max(np.abs(m.hist[:k] - o.hist[:k]) / o.hist[:k]) < 1e-5
+            assert np.array_equal(m.x.astype(np.float32).astype(np.float64), m.x)
+            assert m.status == ob.OK
+
+
+def test_fp32_model_tolerance_one_step_equals_float64():
+    """At a loose tolerance rounding cannot change the outcome: same steps."""
+    from oracle import fp32model as fm
+    p = synth.varcoef(12, 10, 9, seed=5)
+    o = ob.bicgstab(12, 10, 9, p.coef, p.b, tol=1e-2, storage="f32")
+    for order in range(3):
+        m = fm.bicgstab_f32(12, 10, 9, p.coef, p.b, tol=1e-2, order=order)
+        assert m.iters == o.iters
+        assert np.linalg.norm(m.x - o.x) / np.linalg.norm(o.x) < 1e-5
+
+
+def test_fp32_step_counts_spread_and_true_residual_holds():
+    """Reading for the float32 parity bars: with float32 vectors and sums,
+    Algorithm 1's step count to 1e-6 moves by several steps when only the
+    summation order changes, and on these systems it is mostly *below* the
+    float64 count; yet the true residual at the stop stays within 1.5 tol,
+    so the earlier stop is real convergence, not a recurrence that drifted
+    below the true residual."""
+    from oracle import fp32model as fm
+    spreads = []
+    for shape, seed in (((20, 13, 11), 7), ((33, 33, 8), 107), ((28, 19, 22), 110)):
+        p = synth.varcoef(*shape, seed=seed)
+        o = ob.bicgstab(*shape, p.coef, p.b, tol=1e-6, maxit=300, storage="f32")
+        its = []
+        for order in range(6):
+            m = fm.bicgstab_f32(*shape, p.coef, p.b, tol=1e-6, maxit=300, order=order)
+            assert m.status == ob.OK and m.true_resid <= 1.5e-6
+            assert np.linalg.norm(m.x - o.x) / np.linalg.norm(o.x) <= 1e-4
+            its.append(m.iters)
+        spreads.append((min(its), max(its), o.iters))
+    assert max(hi - lo for lo, hi, _ in spreads) >= 2
+    assert all(lo <= orc for lo, _, orc in spreads)
+
+
+def test_fp32_to_float64_step_ratio():
+    """The float32 step counts of the model stay within [0.75, 1.1] of the
+    float64 count on systems of the variable-coefficient recipe at tol 1e-6
+    (the window given to float32 solves too large to run the model on)."""
+    from oracle import fp32model as fm
+    ratios = []
+    for shape, seed in (((20, 13, 11), 7), ((16, 16, 16), 100), ((17, 9, 33), 101),
+                        ((40, 31, 25), 102), ((24, 24, 24), 104), ((64, 20, 12), 106),
+                        ((33, 33, 8), 107), ((28, 19, 22), 110)):
+        p = synth.varcoef(*shape, seed=seed)
+        o = ob.bicgstab(*shape, p.coef, p.b, tol=1e-6, maxit=500, storage="f32")
+        for order in range(4):
+            m = fm.bicgstab_f32(*shape, p.coef, p.b, tol=1e-6, maxit=500, order=order)
+            ratios.append(m.iters / o.iters)
+    assert 0.75 <= min(ratios) and max(ratios) <= 1.1, (min(ratios), max(ratios))
