@@ -93,9 +93,19 @@ def parse():
     ap.add_argument("--edge2d", type=int, default=22800,
                     help="solve9: edge of the square 2D mesh (Sec. IV-A's largest: 22800)")
     ap.add_argument("--systems", type=int, default=512, help="batched: number of systems")
-    ap.add_argument("--requests", type=int, default=300, help="serve: requests")
-    ap.add_argument("--rate", type=float, default=30.0, help="serve: arrivals per second")
-    ap.add_argument("--pool", type=int, default=24, help="serve: distinct problems drawn")
+    ap.add_argument("--requests", type=int, default=20000, help="serve: requests in the stream")
+    ap.add_argument("--rate", type=float, default=40.0, help="serve: arrivals per second")
+    ap.add_argument("--serve-deadline", type=float, default=540.0,
+                    help="serve: stop submitting after this many seconds")
+    ap.add_argument("--serve-held-gb", type=float, default=60.0,
+                    help="serve: most input bytes held for unfinished requests")
+    ap.add_argument("--pool", type=int, default=48, help="speedup: requests solved both ways")
+    ap.add_argument("--no-serve", action="store_true", help="default line without the stream")
+    ap.add_argument("--no-speedup", action="store_true", help="default line without the speedup")
+    ap.add_argument("--no-refined", action="store_true",
+                    help="default line without the 512^3 refined solves")
+    ap.add_argument("--cpu-all-nz", type=int, default=12,
+                    help="z planes of each slab of the all-core oracle baseline")
     ap.add_argument("--serve-storage", default="bf16", choices=["bf16", "f16"],
                     help="speedup: storage of the served form")
     ap.add_argument("--serve-inner-tol", type=float, default=0.0,
@@ -250,18 +260,70 @@ class ClockSampler:
 # CPU oracle
 # ---------------------------------------------------------------------------
 
-def oracle_sample(nx, ny, nz_sample, iters, seed=0):
-    """The FP64 oracle on a slab of the same recipe; returns (cell-iters/s, desc)."""
+def oracle_sample(nx, ny, nz_sample, iters, seed=0, window=False):
+    """The FP64 oracle on a slab of the same recipe; returns (cell-iters/s, desc,
+    seconds) and, with `window`, also the wall-clock start and end of the solve."""
     import synth
     from oracle import bicgstab as ob
     p = synth.varcoef(nx, ny, nz_sample, seed=seed)
+    w0 = time.time()
     t0 = time.perf_counter()
     r = ob.bicgstab(nx, ny, nz_sample, p.coef, p.b, tol=0.0, maxit=iters, storage="f32")
     dt = time.perf_counter() - t0
+    w1 = time.time()
     desc = ("%dx%dx%d slab of the same coefficient recipe (seed %d), FP64 NumPy oracle "
             "(Algorithm 1), %d iterations incl. Jacobi scaling" % (nx, ny, nz_sample, seed,
                                                                  r.iters))
+    if window:
+        return p.n * r.iters, desc, dt, w0, w1
     return p.n * r.iters / dt, desc, dt
+
+
+def _oracle_job(a):
+    """One oracle solve in a worker process (spawned: no CUDA state)."""
+    nx, ny, nz, iters, seed = a
+    return oracle_sample(nx, ny, nz, iters, seed, window=True)
+
+
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.machine()
+
+
+def oracle_baseline(nx, ny, nz_sample, iters, procs):
+    """The FP64 oracle, as it stands, on `procs` host cores: one independent
+    slab solve per worker process (seeds 0..procs-1), each process limited
+    to one thread (BLAS included), started with spawn.  Returns cell-iters/s
+    over the common wall-clock window (first start to last end) and the
+    sample description."""
+    import multiprocessing as mp
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
+    ctx = mp.get_context("spawn")
+    jobs = [(nx, ny, nz_sample, iters, seed) for seed in range(procs)]
+    with ctx.Pool(procs) as pool:
+        res = pool.map(_oracle_job, jobs)
+    work = sum(r[0] for r in res)
+    t0 = min(r[3] for r in res)
+    t1 = max(r[4] for r in res)
+    desc = ("%d independent %dx%dx%d slabs of the same coefficient recipe (seeds 0..%d), "
+            "FP64 NumPy oracle (Algorithm 1), %d iterations each, one process per core, "
+            "one thread per process" % (procs, nx, ny, nz_sample, procs - 1, iters))
+    return work / (t1 - t0), desc, t1 - t0
 
 
 def run_reference(args):
@@ -405,17 +467,32 @@ def run_ours(args):
     launches = int(sum(c for _, c in prof.values()))
 
     # end to end through the C ABI with pinned host buffers (rank-local)
+    op.close()
+    del b, x
+    torch.cuda.empty_cache()
     e2e = None
     if not args.no_e2e:
-        op.close()
-        del b, x
-        torch.cuda.empty_cache()
         e2e = run_e2e(args, s7, prob, dev)
 
-    cpu = None
+    extras = {}
+    if rank == 0 and world == 1:
+        del prob
+        extras = run_extras(args)
+
+    cpu = cpu_all = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, desc, _ = oracle_sample(nx, ny, min(args.cpu_sample_nz, nz), args.cpu_sample_iters)
-        cpu = {"value": v, "unit": "cell-iters/s", "cores": 1, "kind": "oracle", "sample": desc}
+        try:
+            v, desc, _ = oracle_baseline(nx, ny, min(args.cpu_sample_nz, nz),
+                                         args.cpu_sample_iters, 1)
+            cpu = {"value": v, "unit": "cell-iters/s", "cores": 1, "kind": "oracle",
+                   "sample": desc, "cpu_model": cpu_model()}
+            ncores = os.cpu_count() or 1
+            v, desc, _ = oracle_baseline(nx, ny, min(args.cpu_all_nz, nz), args.cpu_sample_iters,
+                                         ncores)
+            cpu_all = {"value": v, "unit": "cell-iters/s", "cores": ncores, "kind": "oracle",
+                       "sample": desc, "cpu_model": cpu_model()}
+        except Exception as e:          # reported, the GPU line stands
+            cpu = cpu or {"error": repr(e)}
 
     if rank == 0:
         out = {
@@ -429,15 +506,44 @@ def run_ours(args):
             "gflops": FLOPS_PER_CELL * value / 1e9,
             "ms_per_iter": iter_ms,
             "roofline": roofline, "kernels": kern,
-            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-            "clocks": clocks,
+            "cpu_baseline": cpu, "cpu_baseline_all_cores": cpu_all, "e2e": e2e,
+            "gpu_launches": launches, "clocks": clocks,
             "context": {"paper_cs1_cell_iters_per_s": PAPER_CS1_CELL_ITERS,
                         "final_rel_resid": float(res.hist[-1]) if res.hist is not None else None,
                         "input_gen_s": gen_s},
         }
+        out.update(extras)
         print(json.dumps(out))
     if pg:
         pg.destroy_process_group()
+
+
+def run_extras(args):
+    """The rest of the headline metric, measured after the main line in the
+    same run: the served request stream (p50/p99 latency), the served
+    mixed-precision form against the plain FP32 form to 1e-8, and 512^3
+    refined solves with their solution error.  A failure in one of them is
+    reported in its object; the main line stands."""
+    import torch
+    out = {}
+    blocks = []
+    if not args.no_serve:
+        blocks.append(("serve", lambda: serve_block(args)))
+    if not args.no_speedup:
+        blocks.append(("speedup", lambda: {s: speedup_block(args, s) for s in ("bf16", "f16")}))
+    if not args.no_refined:
+        blocks.append(("refined", lambda: refined_block(args)))
+    for name, fn in blocks:
+        t0 = time.perf_counter()
+        try:
+            out[name] = fn()
+        except Exception as e:
+            out[name] = {"error": repr(e)}
+        if isinstance(out[name], dict):
+            out[name]["bench_s"] = time.perf_counter() - t0
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+    return out
 
 
 def kernel_table(prof, bpc, n, peak):
@@ -594,6 +700,339 @@ def _timed(fn, steps, warmup):
     return ev0.elapsed_time(ev1) / steps, outs
 
 
+def run_batched(args):
+    """512 systems, cube edges log-uniform in [16,128] (seed 1), FP32, tol 1e-6."""
+    import torch
+    import synth
+    import paper_2010_03660_gb300 as s7
+    s7.lib()
+    dev = torch.device("cuda:0")
+    edges = synth.batched_edges(args.systems, seed=1)
+    ops, bs = [], []
+    for j, e in enumerate(edges):
+        p = synth.varcoef(e, e, e, seed=synth.system_seed(1, j))
+        ops.append(s7.stencil7_create(e, e, e, {k: torch.from_numpy(v).to(dev)
+                                                for k, v in p.coef.items()}, storage="f32",
+                                      variant=args.variant))
+        bs.append(torch.from_numpy(p.b).to(dev))
+    cells = [e ** 3 for e in edges]
+    xs = [torch.zeros_like(b) for b in bs]
+
+    def fn():
+        for x in xs:
+            x.zero_()
+        return s7.bicgstab_solve_batched(ops, bs, xs, tol=1e-6, maxit=2000)
+    ms, outs = _timed(fn, args.steps, max(1, args.warmup))
+    r = outs[-1]
+    ci = sum(c * it for c, it in zip(cells, r.iters))
+    # the same systems one after another through bicgstab_solve
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    seq_ci = 0
+    for op, b, x, c in zip(ops, bs, xs, cells):
+        x.zero_()
+        rs = s7.bicgstab_solve(op, b, x, tol=1e-6, maxit=2000, history=False, true_resid=False)
+        seq_ci += c * rs.iters
+    torch.cuda.synchronize()
+    seq_s = time.perf_counter() - t0
+    out = {"metric": "batched cell-iters/s (512 systems, edges 16..128, FP32, tol 1e-6)",
+           "value": ci / (ms / 1e3), "unit": "cell-iters/s", "higher_is_better": True,
+           "workload": "batched_%d%s" % (args.systems, "_merged" if args.variant else ""),
+           "variant": "two reductions per step" if args.variant else "Algorithm 1",
+           "dtype": "f32", "data": "synthetic (seed 1)",
+           "ms_per_batch_solve": ms, "systems": len(ops), "total_cells": int(sum(cells)),
+           "iters_min_max": [min(r.iters), max(r.iters)], "all_converged": r.rc == 0,
+           "hbm_gbs": 116 * ci / (ms / 1e3) / 1e9,
+           "sequential_single_solves": {"s": seq_s, "cell_iters_per_s": seq_ci / seq_s},
+           "speedup_vs_sequential": (seq_s * 1e3) / ms, "steps": args.steps}
+    for op in ops:
+        op.close()
+    print(json.dumps(out))
+
+
+def _quantiles(v):
+    v = np.asarray(v, dtype=np.float64)
+    return {"min": float(v.min()), "median": float(np.median(v)), "max": float(v.max()),
+            "iqr": float(np.percentile(v, 75) - np.percentile(v, 25))}
+
+
+def serve_block(args, requests=None, rate=None, deadline_s=None, storage=None):
+    """The served request stream: Poisson arrivals of solve requests, mesh
+    edges log-uniform in [32,384] with aspect ratios log-uniform in [0.5,2],
+    tolerances drawn from {1e-4,1e-6,1e-8}, BF16 storage + float64-accuracy
+    refinement, 150 GB admission budget.  Every request is its own system
+    (its own seed), generated on the device at its arrival time and submitted
+    from device memory.  Latency = completion - submission (the server's host
+    monotonic clock); p50/p99 over the requests after the warm-up ones.
+    Submission stops at `deadline_s`; the requests submitted until then are
+    all waited for and reported."""
+    import threading
+    import torch
+    import synth
+    from synth import device as sd
+    import paper_2010_03660_gb300 as s7
+    requests = args.requests if requests is None else requests
+    rate = args.rate if rate is None else rate
+    deadline_s = args.serve_deadline if deadline_s is None else deadline_s
+    storage = args.serve_storage if storage is None else storage
+    dev = torch.device("cuda", torch.cuda.current_device())
+    reqs = synth.request_stream(requests, rate=rate, seed=3)
+    srv = s7.Server(storage=storage, hbm_budget_bytes=150 << 30)
+    ids = [None] * len(reqs)
+    lag = [0.0] * len(reqs)
+    state = {"submitted": 0, "done": False, "error": None, "inflight": 0, "held": 0}
+    lock = threading.Lock()
+    # inputs held for submitted, unfinished requests (7 float32 arrays, b and
+    # x in float64): past the limit the producer waits for completions, so
+    # an overloaded stream shows up as arrival lag instead of running the
+    # device out of memory
+    held_limit = int(args.serve_held_gb * 1e9)
+    arr0 = reqs[0].arrival
+    t_start = time.perf_counter()
+
+    def producer():
+        try:
+            torch.cuda.set_device(dev)
+            gs = torch.cuda.Stream(dev)
+            with torch.cuda.stream(gs):
+                for j, q in enumerate(reqs):
+                    if time.perf_counter() - t_start > deadline_s:
+                        break
+                    delay = (q.arrival - arr0) - (time.perf_counter() - t_start)
+                    if delay > 0:
+                        time.sleep(delay)
+                    need = 44 * q.nx * q.ny * q.nz
+                    while state["inflight"] and state["inflight"] + need > held_limit:
+                        time.sleep(0.001)
+                    with lock:
+                        state["inflight"] += need
+                        state["held"] = max(state["held"], state["inflight"])
+                    coef, b = sd.varcoef(q.nx, q.ny, q.nz, q.seed, dev)
+                    x = torch.empty_like(b)
+                    gs.synchronize()
+                    lag[j] = time.perf_counter() - t_start - (q.arrival - arr0)
+                    ids[j] = srv.submit(q.nx, q.ny, q.nz, coef, b, x, q.tol)
+                    state["submitted"] = j + 1
+        except Exception as e:      # reported in the output, the stream stops
+            state["error"] = repr(e)
+        finally:
+            state["done"] = True
+
+    th = threading.Thread(target=producer, daemon=True)
+    th.start()
+    lat, statuses, over, cells, tols = [], [], [], [], []
+    for j in range(len(reqs)):
+        while ids[j] is None and not (state["done"] and state["submitted"] <= j):
+            time.sleep(0.0005)
+        if ids[j] is None:
+            break
+        r = srv.wait(ids[j], timeout=900)
+        q = reqs[j]
+        lat.append(r["latency"])
+        statuses.append(r["status"])
+        over.append(r["resid"] / q.tol)
+        cells.append(q.nx * q.ny * q.nz)
+        tols.append(q.tol)
+        srv.release(ids[j])
+        with lock:
+            state["inflight"] -= 44 * q.nx * q.ny * q.nz
+    th.join()
+    wall = time.perf_counter() - t_start
+    st = srv.stats()
+    srv.close()
+    torch.cuda.empty_cache()
+    n = len(lat)
+    warm = min(500, n // 10)
+    lw = np.array(lat[warm:]) if n > warm else np.array(lat)
+    out = {"workload": "serve_%d_requests_at_%g_per_s" % (n, rate),
+           "requests_in_stream": requests, "requests_run": n, "warmup_requests": warm,
+           "rate_per_s": rate, "storage": storage, "budget_gb": 150 * 2 ** 30 / 1e9,
+           "p50_s": float(np.percentile(lw, 50)), "p99_s": float(np.percentile(lw, 99)),
+           "mean_s": float(lw.mean()), "max_s": float(lw.max()),
+           "completed": int(st["completed"]), "failed": int(st["failed"]),
+           "statuses_ok": int(sum(1 for s_ in statuses if s_ == 0)),
+           "max_resid_over_tol": float(max(over)) if over else None,
+           "wall_s": wall, "cell_iters_per_s": st["cell_iters"] / wall,
+           "mean_cells": float(np.mean(cells)) if cells else 0.0,
+           "mem_peak_gb": st["mem_peak"] / 1e9,
+           "arrival_lag_p99_s": float(np.percentile(lag[:n], 99)) if n else None,
+           "arrival_lag_max_s": float(np.max(lag[:n])) if n else None,
+           "inputs_held_peak_gb": state["held"] / 1e9,
+           "stopped_by_deadline": n < requests,
+           "inputs": "each request its own seeded system (SplitMix64, seed 3 stream), generated "
+                     "on the device at arrival and submitted from device memory",
+           "latency": "completion - submission, host monotonic clock"}
+    if state["error"]:
+        out["error"] = state["error"]
+    return out
+
+
+def run_serve(args):
+    import torch
+    import paper_2010_03660_gb300 as s7
+    s7.lib()
+    torch.cuda.set_device(0)
+    out = serve_block(args)
+    out.update({"metric": "p99 solve latency (serving, %s + FP64 refinement)"
+                % args.serve_storage.upper(), "value": out["p99_s"], "unit": "s",
+                "higher_is_better": False, "data": "synthetic (seed 3)"})
+    print(json.dumps(out))
+
+
+def speedup_block(args, storage, requests=None, reps=None):
+    """The same requests to relative residual 1e-8 two ways: one after another
+    with FP32 storage + float64-accuracy refinement (the plain form, at the
+    faster of two inner tolerances), and all at once through the server
+    (`storage` + refinement, continuous batching).  Inputs are device-resident
+    for both forms (generated on the device, each request its own seed);
+    both include operator creation.  The plain and served forms alternate
+    `reps` times; the ratio is of the medians, with every sample reported."""
+    import torch
+    import synth
+    from synth import device as sd
+    import paper_2010_03660_gb300 as s7
+    requests = args.pool if requests is None else requests
+    reps = max(5, args.steps if reps is None else reps)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    reqs = synth.request_stream(requests, rate=1.0, seed=3)
+    pool = []
+    for q in reqs:
+        coef, b = sd.varcoef(q.nx, q.ny, q.nz, q.seed, dev)
+        pool.append((q.nx, q.ny, q.nz, coef, b))
+    torch.cuda.synchronize()
+    cells = sum(nx * ny * nz for nx, ny, nz, _, _ in pool)
+
+    def plain(inner_tol):
+        its = 0
+        for nx, ny, nz, coef, b in pool:
+            op = s7.stencil7_create(nx, ny, nz, coef, storage="f32", keep_true=True)
+            x = torch.zeros_like(b)
+            r = s7.bicgstab_solve_refined(op, b, x, tol=1e-8, max_outer=60, inner_maxit=400,
+                                          inner_tol=inner_tol)
+            its += r.inner_total
+            op.close()
+        torch.cuda.synchronize()
+        return its
+
+    def served():
+        with s7.Server(storage=storage, hbm_budget_bytes=150 << 30,
+                       inner_tol=args.serve_inner_tol, three_pass=args.serve_three_pass,
+                       steps_per_tick=args.serve_steps_per_tick) as srv:
+            xs = [torch.empty_like(b) for _, _, _, _, b in pool]
+            ids = [srv.submit(nx, ny, nz, coef, b, x, 1e-8)
+                   for (nx, ny, nz, coef, b), x in zip(pool, xs)]
+            return [srv.wait(i, timeout=600) for i in ids]
+
+    plain(1e-2)                   # warm-up (module loading, pool)
+    served()
+    t_inner = {}
+    for inner_tol in (1e-2, 1e-5):
+        t0 = time.perf_counter()
+        its_k = plain(inner_tol)
+        t_inner[inner_tol] = (time.perf_counter() - t0, its_k)
+    best = min(t_inner, key=lambda k: t_inner[k][0])
+    its = t_inner[best][1]
+    tp, ts = [], []
+    res = None
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        plain(best)
+        tp.append(time.perf_counter() - t0)
+        t0 = time.perf_counter()
+        res = served()
+        ts.append(time.perf_counter() - t0)
+    ratios = [a / b for a, b in zip(tp, ts)]
+    t_plain, t_served = statistics.median(tp), statistics.median(ts)
+    value = t_plain / t_served
+    lo = float(np.percentile(ratios, 25))
+    return {"workload": "speedup_%d_requests_to_1e-8" % len(pool), "served_storage": storage,
+            "value": value, "unit": "x", "requests": len(pool), "total_cells": cells,
+            "plain_fp32_s": t_plain, "served_s": t_served,
+            "plain_fp32_samples_s": tp, "served_samples_s": ts,
+            "ratio_per_pair": ratios, "ratio_spread": _quantiles(ratios),
+            "clears_1_5x_by_more_than_spread": bool(lo > 1.5 and min(ratios) > 1.5),
+            "plain_fp32_inner_tol": best,
+            "plain_fp32_s_by_inner_tol": {str(k): v[0] for k, v in t_inner.items()},
+            "plain_inner_iters": its,
+            "served_inner_iters": int(sum(r["inner_iters"] for r in res)),
+            "served_all_ok": all(r["status"] == 0 for r in res),
+            "served_max_resid": max(r["resid"] for r in res),
+            "reps": reps, "inputs": "device-resident, each request its own seeded system"}
+
+
+def run_speedup(args):
+    import torch
+    import paper_2010_03660_gb300 as s7
+    s7.lib()
+    torch.cuda.set_device(0)
+    out = speedup_block(args, args.serve_storage)
+    out.update({"metric": "speedup to relative residual 1e-8: served %s + FP64 refinement vs "
+                          "sequential FP32 + FP64 refinement" % args.serve_storage.upper(),
+                "higher_is_better": True, "data": "synthetic (seed 3)"})
+    print(json.dumps(out))
+
+
+def refined_block(args, edge=None, storages=("bf16", "f16"), reps=3):
+    """512^3 (seed 2) refined to relative residual 1e-10 with 16-bit storage:
+    the time of the solve on b ~ N(0,1) (median of `reps`), its steps and
+    certified float64-accuracy residual, and the solution error against the
+    exact solution of a manufactured system: x* ~ N(0,1) (seeded), b* = A x*
+    computed by the FP64 oracle on the host from the same raw float32
+    coefficients, so x* solves A x = b* to float64 rounding."""
+    import torch
+    import synth
+    from synth import device as sd
+    import paper_2010_03660_gb300 as s7
+    from oracle import stencil
+    e = args.edge if edge is None else edge
+    n = e ** 3
+    dev = torch.device("cuda", torch.cuda.current_device())
+    coef, b = sd.varcoef(e, e, e, 2, dev)
+    # the manufactured system, on the host, by the oracle
+    t0 = time.perf_counter()
+    ph = synth.varcoef(e, e, e, seed=2)
+    xs = synth.random_vector(n, 2, 9, np.float64)
+    bs = stencil.apply(e, e, e, ph.coef, xs)
+    del ph
+    oracle_s = time.perf_counter() - t0
+    bs_d = torch.from_numpy(bs).to(dev)
+    del bs
+    out = {"workload": "refined_%d^3_to_1e-10" % e, "cells": n,
+           "error_reference": "x* ~ N(0,1) seeded, b* = A x* by the FP64 oracle on the host "
+                              "(raw float32 coefficients, float64 arithmetic)",
+           "oracle_host_s": oracle_s, "runs": {}}
+    for storage in storages:
+        op = s7.stencil7_create(e, e, e, coef, storage=storage, keep_true=True)
+        times, r = [], None
+        for k in range(reps + 1):
+            x = torch.zeros_like(b)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            r = s7.bicgstab_solve_refined(op, b, x, tol=1e-10, max_outer=60, inner_maxit=200,
+                                          inner_tol=1e-2)
+            torch.cuda.synchronize()
+            if k:
+                times.append(time.perf_counter() - t1)
+        rn, bn = s7.stencil7_residual(op, b, r.x)
+        xm = torch.zeros_like(bs_d)
+        rm = s7.bicgstab_solve_refined(op, bs_d, xm, tol=1e-10, max_outer=60, inner_maxit=200,
+                                       inner_tol=1e-2)
+        xsd = torch.from_numpy(xs).to(dev)
+        err = float(torch.linalg.norm(rm.x - xsd) / torch.linalg.norm(xsd))
+        err_inf = float((rm.x - xsd).abs().max() / xsd.abs().max())
+        del xsd
+        out["runs"][storage] = {
+            "s": statistics.median(times), "samples_s": times, "status": r.status,
+            "outer": r.outer, "inner_iters": r.inner_total, "true_resid": rn / bn,
+            "manufactured": {"status": rm.status, "outer": rm.outer,
+                             "inner_iters": rm.inner_total, "resid": float(rm.hist[-1]),
+                             "rel_error_2norm": err, "rel_error_max": err_inf}}
+        op.close()
+    del coef, b, bs_d
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_refined(args):
     """512^3, seed 2: refined solves to 1e-8 and 1e-10 with BF16, FP16 and FP32
     storage (FP32 arithmetic, FP64 outer residual on the true operator)."""
@@ -645,198 +1084,8 @@ def run_refined(args):
            "speedup_vs_best_fp32_storage_to_1e-8": {
                k: base / runs["%s_tol1e-08" % k]["ms"] for k in ("bf16_in0.01", "f16_in0.01",
                                                                  "f16_in0.001")},
+           "manufactured_solution_error": refined_block(args, edge=e)["runs"],
            "steps": args.steps}
-    print(json.dumps(out))
-
-
-def run_batched(args):
-    """512 systems, cube edges log-uniform in [16,128] (seed 1), FP32, tol 1e-6."""
-    import torch
-    import synth
-    import paper_2010_03660_gb300 as s7
-    s7.lib()
-    dev = torch.device("cuda:0")
-    edges = synth.batched_edges(args.systems, seed=1)
-    ops, bs = [], []
-    for j, e in enumerate(edges):
-        p = synth.varcoef(e, e, e, seed=synth.system_seed(1, j))
-        ops.append(s7.stencil7_create(e, e, e, {k: torch.from_numpy(v).to(dev)
-                                                for k, v in p.coef.items()}, storage="f32",
-                                      variant=args.variant))
-        bs.append(torch.from_numpy(p.b).to(dev))
-    cells = [e ** 3 for e in edges]
-    xs = [torch.zeros_like(b) for b in bs]
-
-    def fn():
-        for x in xs:
-            x.zero_()
-        return s7.bicgstab_solve_batched(ops, bs, xs, tol=1e-6, maxit=2000)
-    ms, outs = _timed(fn, args.steps, max(1, args.warmup))
-    r = outs[-1]
-    ci = sum(c * it for c, it in zip(cells, r.iters))
-    # the same systems one after another through bicgstab_solve
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    seq_ci = 0
-    for op, b, x, c in zip(ops, bs, xs, cells):
-        x.zero_()
-        rs = s7.bicgstab_solve(op, b, x, tol=1e-6, maxit=2000, history=False, true_resid=False)
-        seq_ci += c * rs.iters
-    torch.cuda.synchronize()
-    seq_s = time.perf_counter() - t0
-    out = {"metric": "batched cell-iters/s (512 systems, edges 16..128, FP32, tol 1e-6)",
-           "value": ci / (ms / 1e3), "unit": "cell-iters/s", "higher_is_better": True,
-           "workload": "batched_%d%s" % (args.systems, "_merged" if args.variant else ""),
-           "variant": "two reductions per step" if args.variant else "Algorithm 1",
-           "dtype": "f32", "data": "synthetic (seed 1)",
-           "ms_per_batch_solve": ms, "systems": len(ops), "total_cells": int(sum(cells)),
-           "iters_min_max": [min(r.iters), max(r.iters)], "all_converged": r.rc == 0,
-           "hbm_gbs": 116 * ci / (ms / 1e3) / 1e9,
-           "sequential_single_solves": {"s": seq_s, "cell_iters_per_s": seq_ci / seq_s},
-           "speedup_vs_sequential": (seq_s * 1e3) / ms, "steps": args.steps}
-    for op in ops:
-        op.close()
-    print(json.dumps(out))
-
-
-def run_serve(args):
-    """Poisson stream of solve requests (config: edges log-uniform in
-    [32,384], aspect [0.5,2], tol in {1e-4,1e-6,1e-8}, BF16 + FP64
-    refinement, 150 GB budget).  Inputs of `--pool` distinct requests are
-    generated up front and reused by the stream (each request keeps its own
-    arrival time and tolerance)."""
-    import threading
-    import torch
-    import synth
-    import paper_2010_03660_gb300 as s7
-    s7.lib()
-    reqs = synth.request_stream(args.requests, rate=args.rate, seed=3)
-    pool = []
-    for q in reqs[:args.pool]:
-        p = synth.varcoef(q.nx, q.ny, q.nz, seed=q.seed)
-        pin = {k: torch.from_numpy(v).pin_memory() for k, v in p.coef.items()}
-        pool.append((q.nx, q.ny, q.nz, pin, torch.from_numpy(p.b.astype(np.float64)).pin_memory()))
-    srv = s7.Server(storage="bf16", hbm_budget_bytes=150 << 30)
-    ids = [None] * len(reqs)
-    t_start = time.perf_counter()
-    arr0 = reqs[0].arrival
-
-    def producer():
-        for j, q in enumerate(reqs):
-            delay = (q.arrival - arr0) - (time.perf_counter() - t_start)
-            if delay > 0:
-                time.sleep(delay)
-            nx, ny, nz, coef, b = pool[j % len(pool)]
-            x = torch.empty(nx * ny * nz, dtype=torch.float64).pin_memory()
-            ids[j] = srv.submit(nx, ny, nz, coef, b, x, q.tol)
-
-    th = threading.Thread(target=producer)
-    th.start()
-    lat, cells_done, statuses = [], 0, []
-    for j in range(len(reqs)):
-        while ids[j] is None:
-            time.sleep(0.0005)
-        r = srv.wait(ids[j], timeout=600)
-        statuses.append(r["status"])
-        lat.append(r["latency"])
-        srv.release(ids[j])
-    th.join()
-    wall = time.perf_counter() - t_start
-    st = srv.stats()
-    srv.close()
-    warm = min(20, len(lat) // 10)
-    l = np.array(lat[warm:])
-    out = {"metric": "p99 solve latency (serving, BF16 + FP64 refinement)",
-           "value": float(np.percentile(l, 99)), "unit": "s", "higher_is_better": False,
-           "p50_s": float(np.percentile(l, 50)), "p99_s": float(np.percentile(l, 99)),
-           "mean_s": float(l.mean()), "requests": len(reqs), "warmup_requests": warm,
-           "rate_per_s": args.rate, "pool": len(pool), "completed": int(st["completed"]),
-           "failed": int(st["failed"]), "statuses_ok": int(sum(1 for s_ in statuses if s_ == 0)),
-           "wall_s": wall, "cell_iters_per_s": st["cell_iters"] / wall,
-           "mem_peak_gb": st["mem_peak"] / 1e9, "workload": "serve_%d_at_%g" % (len(reqs), args.rate),
-           "data": "synthetic (seed 3)"}
-    print(json.dumps(out))
-
-
-def run_speedup(args):
-    """The same requests to relative residual 1e-8 two ways: one after another
-    with FP32 storage + FP64 refinement (the plain form), and all at once
-    through the server (BF16 storage + FP64 refinement, continuous batching).
-    Both include operator creation from host memory."""
-    import torch
-    import synth
-    import paper_2010_03660_gb300 as s7
-    s7.lib()
-    reqs = synth.request_stream(args.pool, rate=1.0, seed=3)
-    pool = []
-    for q in reqs:
-        p = synth.varcoef(q.nx, q.ny, q.nz, seed=q.seed)
-        pin = {k: torch.from_numpy(v).pin_memory() for k, v in p.coef.items()}
-        pool.append((q.nx, q.ny, q.nz, pin, torch.from_numpy(p.b.astype(np.float64)).pin_memory()))
-    cells = sum(nx * ny * nz for nx, ny, nz, _, _ in pool)
-
-    def plain(inner_tol):
-        its = 0
-        for nx, ny, nz, coef, b in pool:
-            op = s7.stencil7_create(nx, ny, nz, coef, storage="f32", keep_true=True)
-            x = torch.zeros(nx * ny * nz, dtype=torch.float64).pin_memory()
-            r = s7.bicgstab_solve_refined(op, b, x, tol=1e-8, max_outer=60, inner_maxit=400,
-                                          inner_tol=inner_tol)
-            its += r.inner_total
-            op.close()
-        return its
-
-    def served():
-        with s7.Server(storage=args.serve_storage, hbm_budget_bytes=150 << 30,
-                       inner_tol=args.serve_inner_tol, three_pass=args.serve_three_pass,
-                       steps_per_tick=args.serve_steps_per_tick) as srv:
-            xs = [torch.empty(nx * ny * nz, dtype=torch.float64).pin_memory()
-                  for nx, ny, nz, _, _ in pool]
-            ids = [srv.submit(nx, ny, nz, coef, b, x, 1e-8)
-                   for (nx, ny, nz, coef, b), x in zip(pool, xs)]
-            res = [srv.wait(i, timeout=600) for i in ids]
-            return res
-
-    # the plain form at the faster of two inner tolerances; then the plain
-    # and served forms alternately, `reps` times each (medians reported)
-    plain(1e-2)                   # warm-up (module loading, allocator)
-    served()
-    t_inner = {}
-    for inner_tol in (1e-2, 1e-5):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        its_k = plain(inner_tol)
-        torch.cuda.synchronize()
-        t_inner[inner_tol] = (time.perf_counter() - t0, its_k)
-    best = min(t_inner, key=lambda k: t_inner[k][0])
-    its = t_inner[best][1]
-    reps = max(1, args.steps)
-    tp, ts = [t_inner[best][0]], []
-    res = None
-    for k in range(reps):
-        if k > 0:
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            plain(best)
-            torch.cuda.synchronize()
-            tp.append(time.perf_counter() - t0)
-        t0 = time.perf_counter()
-        res = served()
-        ts.append(time.perf_counter() - t0)
-    t_plain, t_served = statistics.median(tp), statistics.median(ts)
-    out = {"metric": "speedup to relative residual 1e-8: served %s + FP64 refinement vs "
-                     "sequential FP32 + FP64 refinement" % args.serve_storage.upper(),
-           "value": t_plain / t_served, "unit": "x", "higher_is_better": True,
-           "requests": len(pool), "total_cells": cells, "plain_fp32_s": t_plain,
-           "plain_fp32_samples_s": tp, "served_samples_s": ts,
-           "plain_fp32_inner_tol": best,
-           "plain_fp32_s_by_inner_tol": {str(k): v[0] for k, v in t_inner.items()},
-           "served_s": t_served, "served_storage": args.serve_storage,
-           "plain_inner_iters": its,
-           "served_inner_iters": int(sum(r["inner_iters"] for r in res)),
-           "served_all_ok": all(r["status"] == 0 for r in res),
-           "served_max_resid": max(r["resid"] for r in res),
-           "workload": "speedup_%d_requests" % len(pool), "data": "synthetic (seed 3)"}
     print(json.dumps(out))
 
 
