@@ -435,23 +435,35 @@ def test_float64_residual_of_float32_data_is_exact(s7, f64):
 
 
 def test_mixed_precision_plateau_and_refinement(s7):
-    """Sec. VI-B analogue: plain BiCGStab with 16-bit storage first tracks the
-    float32 history, then stalls at a plateau set by the storage precision;
-    float64 refinement on the true operator still reaches 1e-10."""
+    """Sec. VI-B analogue, against the FP64 oracle: plain BiCGStab with 16-bit
+    storage first follows the oracle's history on the same stored operator,
+    then stalls at a plateau set by the storage precision, and its solution
+    error against the oracle's float64 solution of the true system is set by
+    that precision; float64 refinement on the true operator reaches 1e-10 and
+    the oracle's solution to 1e-8."""
     nx, ny, nz = 50, 100, 25
     p = synth.varcoef(nx, ny, nz, seed=4)
+    b64 = p.b.astype(np.float64)
+    # the true (float32-coefficient) system solved in float64 by the oracle
+    x_ref = ob.bicgstab(nx, ny, nz, p.coef, b64, tol=1e-13, maxit=3000, storage="f64").x
     coef = gu.coef_on_device(p)
     b = gu.to_dev(p.b)
-    h = {}
+    h, err = {}, {}
     for storage in ("f32", "bf16", "f16"):
         with s7.stencil7_create(nx, ny, nz, coef, storage=storage, keep_true=True) as op:
             r = s7.bicgstab_solve(op, b, tol=1e-12, maxit=80)
             rn, bn = s7.stencil7_residual(op, b, r.x)
             h[storage] = (np.asarray(r.hist), rn / bn)
+            err[storage] = rel(r.x.cpu().numpy(), x_ref)
+            # the oracle's Algorithm 1 on the same stored operator: early steps
+            orc = ob.bicgstab(nx, ny, nz, p.coef, p.b, tol=1e-12, maxit=6, storage=storage)
+            assert np.max(np.abs(r.hist[:6] - orc.hist[:6]) / orc.hist[:6]) < 1e-3
             if storage != "f32":
                 rr = s7.bicgstab_solve_refined(op, b.double(), tol=1e-10, max_outer=40,
                                                inner_maxit=100, inner_tol=1e-2)
                 assert rr.status == 0 and rr.hist[-1] <= 1e-10
+                assert ob.true_residual(nx, ny, nz, p.coef, b64, rr.x.cpu().numpy()) <= 1.5e-10
+                assert rel(rr.x.cpu().numpy(), x_ref) < 1e-8
     f32 = h["f32"][0]
     for storage, floor in (("bf16", 1e-4), ("f16", 1e-6)):
         hist, true_raw = h[storage]
@@ -460,6 +472,8 @@ def test_mixed_precision_plateau_and_refinement(s7):
         # the true residual stalls far above what float32 reaches
         assert true_raw > floor
         assert true_raw > 100 * h["f32"][1]
+    # the solution error follows the storage precision
+    assert err["f32"] <= 1e-4 and err["f32"] < err["f16"] < err["bf16"], err
 
 
 def test_two_reduction_variant_fp64_matches_its_oracle(s7):
