@@ -135,6 +135,8 @@ def parse():
                     help="cells per thread in the pipelined sweeps (0 = tuned; 8 for 16-bit)")
     ap.add_argument("--pipe-kinds", type=int, default=0,
                     help="sweeps using the pipeline: bit 0 p/s sweep, bit 1 q/y sweep (0 = tuned)")
+    ap.add_argument("--tma", action="store_true",
+                    help="pipelined sweeps stage with TMA tensor copies instead of cp.async")
     ap.add_argument("--residual-f64", action="store_true",
                     help="float64-accuracy residual sweeps in binary64 (default: double words)")
     ap.add_argument("--ref-sample-nz", type=int, default=8)
@@ -402,7 +404,7 @@ def run_ours(args):
     op = s7.stencil7_create(nx, ny, nz, coef_d, storage=args.storage, bx=args.bx, by=args.by,
                             zchunk=args.zchunk, variant=args.variant, stages=args.stages,
                             pipe_kinds=args.pipe_kinds, step_cells=args.step_cells,
-                            residual_f64=args.residual_f64)
+                            residual_f64=args.residual_f64, tma=args.tma)
     del coef_d
     torch.cuda.empty_cache()
     b = torch.from_numpy(prob.b).to(dev)

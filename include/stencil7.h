@@ -139,6 +139,13 @@ typedef struct {
                         magnitude; squared norms in binary64), several times
                         faster on GB300; 1 = binary64 throughout.  float64
                         storage always uses binary64.                          */
+  int tma;           /* 1: the pipelined sweeps of single solves stage their
+                        tiles with TMA tensor copies issued by the first warp
+                        of a block, where the tile allows (16-byte cell runs,
+                        a halo'd tile at most 256 cells wide); 0 (default):
+                        with per-thread cp.async copies, which measured as
+                        fast or faster on GB300 for these tiles.  Same
+                        results either way.                                   */
 } s7_opts;
 
 /* Create an operator handle.  Copies the coefficients to library-owned device

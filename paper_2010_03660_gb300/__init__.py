@@ -79,7 +79,8 @@ class s7_opts(C.Structure):
     _fields_ = [("storage", C.c_int), ("no_jacobi", C.c_int), ("keep_true", C.c_int),
                 ("bx", C.c_int), ("by", C.c_int), ("zchunk", C.c_int),
                 ("check_every", C.c_int), ("stages", C.c_int), ("pipe_kinds", C.c_int),
-                ("variant", C.c_int), ("step_cells", C.c_int), ("residual_f64", C.c_int)]
+                ("variant", C.c_int), ("step_cells", C.c_int), ("residual_f64", C.c_int),
+                ("tma", C.c_int)]
 
 
 class s7_batch_opts(C.Structure):
@@ -275,7 +276,7 @@ class Operator:
 
 def stencil7_create(nx, ny, nz, coef, storage="f32", jacobi=True, keep_true=False,
                     bx=0, by=0, zchunk=0, check_every=0, constant=None, stages=0,
-                    pipe_kinds=0, variant=0, step_cells=0, residual_f64=False):
+                    pipe_kinds=0, variant=0, step_cells=0, residual_f64=False, tma=False):
     """Create an operator from raw coefficients.
 
     ``coef`` maps ``diag, xm, xp, ym, yp, zm, zp`` to arrays/tensors of
@@ -310,7 +311,8 @@ def stencil7_create(nx, ny, nz, coef, storage="f32", jacobi=True, keep_true=Fals
                    ptrs["zm"], ptrs["zp"], raw_dt, 1 if constant else 0)
     st = _STORAGE[storage] if isinstance(storage, str) else int(storage)
     op = s7_opts(st, 0 if jacobi else 1, 1 if keep_true else 0, bx, by, zchunk, check_every,
-                 stages, pipe_kinds, variant, step_cells, 1 if residual_f64 else 0)
+                 stages, pipe_kinds, variant, step_cells, 1 if residual_f64 else 0,
+                 1 if tma else 0)
     h = C.c_void_p()
     _check(lib().stencil7_create(C.byref(h), nx, ny, nz, C.byref(cs), C.byref(op)))
     del keep

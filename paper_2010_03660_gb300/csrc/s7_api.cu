@@ -399,6 +399,7 @@ static void release(Handle* h) {
   dfree(h, &w.ref_x, n * 8);
   dfree(h, &w.ref_b, n * 8);
   dfree(h, &w.ref_r, n * 8);
+  w.maps_key[0] = 0;
   pinned_scalars_put(w.h_sc);
   w.h_sc = nullptr;
   for (int k = 0; k < 2; ++k) {
@@ -504,6 +505,7 @@ extern "C" int stencil7_create(stencil7_t* out, int nx, int ny, int nz, const s7
   h->step_vec = opts.step_cells > 0 ? opts.step_cells : (half ? 8 : eng->vec);
   h->variant = opts.variant;
   h->resid_f64 = opts.residual_f64 ? 1 : 0;
+  h->tma = opts.tma ? 1 : 0;
   if (!eng->smem_ok(h)) {
     delete h;
     return fail(S7_EINVAL, "stencil7_create: tile too large for shared memory");
@@ -680,6 +682,7 @@ extern "C" int stencil9_create(stencil7_t* out, int nx, int ny, const s9_coeffs*
   h->step_vec = eng->vec;
   h->variant = opts.variant;
   h->resid_f64 = opts.residual_f64 ? 1 : 0;
+  h->tma = opts.tma ? 1 : 0;
   if (!eng->smem_ok(h)) {
     delete h;
     return fail(S7_EINVAL, "stencil9_create: tile too large for shared memory");
@@ -799,6 +802,7 @@ int s7::ensure_ws(Handle* h, int maxit) {
     if ((rc = dmalloc(h, (void**)&w.parts, w.parts_n * 8))) return rc;
     if ((rc = dmalloc(h, (void**)&w.sc, sizeof(Scalars)))) return rc;
     CK(cudaMemset(w.sc, 0, sizeof(Scalars)));
+
     if (!w.h_sc) CK(pinned_scalars(&w.h_sc));
     for (int k = 0; k < 2; ++k)
       if (!w.snap[k]) CK(cudaEventCreateWithFlags(&w.snap[k], cudaEventDisableTiming));

@@ -169,6 +169,7 @@ __global__ void __launch_bounds__(256) k_step_batched(const SysDesc<T, X>* __res
                                                       int nsys) {
   extern __shared__ __align__(16) unsigned char s7_smem[];
   __shared__ double red[32 * 4];
+  __shared__ __align__(8) unsigned long long bars[STAGES];
   __shared__ int s_sys;
   if (threadIdx.x == 0) s_sys = find_system(sys, nsys, (int)blockIdx.x, false);
   __syncthreads();
@@ -188,8 +189,9 @@ __global__ void __launch_bounds__(256) k_step_batched(const SysDesc<T, X>* __res
   a.rbuf[1] = d.r2;
   a.x = d.x;
   a.hist = d.hist;
+  a.maps = nullptr;   // batches stage with cp.async
   step_body<T, A, VEC, KIND, STAGES>(d.g, a, d.sc, (int)blockIdx.x - d.block0, d.nblocks, s7_smem,
-                                     red);
+                                     red, bars);
 }
 
 template <class T, class X, class A, int VEC>

@@ -73,7 +73,7 @@ __device__ __forceinline__ void update_body(long long n, const T* p0, const T* p
     ldv<X, VEC, LD_STREAM>(x + i, xv);
 #pragma unroll
     for (int k = 0; k < VEC; ++k) {
-      const A q = q_of(rv[k], sv[k], alpha);
+      const A q = q_of<T>(rv[k], sv[k], alpha);
       xv[k] = fma(omega, q, fma(alpha, pv[k], xv[k]));
       const A rn = as_stored<T>(fma(-omega, yv[k], q));
       rv[k] = rn;
@@ -90,7 +90,7 @@ __device__ __forceinline__ void update_body(long long n, const T* p0, const T* p
   if (bid == 0) {
     for (long long i = nvec * VEC + threadIdx.x; i < n; i += blockDim.x) {
       const A rv = to_acc<A>(r[i]), sv = to_acc<A>(s[i]);
-      const A q = q_of(rv, sv, alpha);
+      const A q = q_of<T>(rv, sv, alpha);
       x[i] = from_acc<X>(fma(omega, q, fma(alpha, to_acc<A>(p[i]), to_acc<A>(x[i]))));
       const A rn = as_stored<T>(fma(-omega, to_acc<A>(y[i]), q));
       r[i] = from_acc<T>(rn);
@@ -279,6 +279,54 @@ int launch_sweep9_1(const Geom& g, const CoefView9<CT, A>& cf, const P& pol, Sca
   return cudaGetLastError() == cudaSuccess ? S7_OK : S7_ECUDA;
 }
 
+// ---- TMA tensor maps (host side) ----
+static_assert(sizeof(StepMaps) <= kMapsBytes, "tensor maps do not fit their slot");
+
+typedef CUresult (*TensorMapEncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                           const cuuint64_t*, const cuuint64_t*,
+                                           const cuuint32_t*, const cuuint32_t*,
+                                           CUtensorMapInterleave, CUtensorMapSwizzle,
+                                           CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// The driver's tensor-map encoder, looked up once (NULL if unavailable).
+inline TensorMapEncodeTiledFn tensor_map_encoder() {
+  static TensorMapEncodeTiledFn fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      f = nullptr;
+    cudaGetLastError();
+    return (TensorMapEncodeTiledFn)f;
+  }();
+  return fn;
+}
+
+template <class E> struct TmaType;
+template <> struct TmaType<double> { static constexpr CUtensorMapDataType v = CU_TENSOR_MAP_DATA_TYPE_FLOAT64; };
+template <> struct TmaType<float> { static constexpr CUtensorMapDataType v = CU_TENSOR_MAP_DATA_TYPE_FLOAT32; };
+template <> struct TmaType<__nv_bfloat16> { static constexpr CUtensorMapDataType v = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16; };
+template <> struct TmaType<__half> { static constexpr CUtensorMapDataType v = CU_TENSOR_MAP_DATA_TYPE_FLOAT16; };
+
+// Map of an nx*ny*nz array of E (x fastest) read in boxes of bw x bh x 1;
+// cells outside the array read as zero.
+template <class E>
+inline bool encode_box(CUtensorMap* m, const void* base, int nx, int ny, int nz, int bw, int bh) {
+  TensorMapEncodeTiledFn fn = tensor_map_encoder();
+  if (!fn || !base || ((uintptr_t)base & 15u) || bw > 256 || bh > 256 ||
+      ((size_t)bw * sizeof(E)) % 16)
+    return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
+  const cuuint64_t strides[2] = {(cuuint64_t)nx * sizeof(E), (cuuint64_t)nx * ny * sizeof(E)};
+  if (strides[0] % 16) return false;
+  const cuuint32_t box[3] = {(cuuint32_t)bw, (cuuint32_t)bh, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return fn(m, TmaType<E>::v, 3, const_cast<void*>(base), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 template <class T_, class X_, class DT_, class A_>
 struct EngineImpl {
   typedef T_ T;
@@ -452,12 +500,55 @@ struct EngineImpl {
   }
 
   // Geometry of the pipelined sweeps at V cells per thread: the tile keeps
-  // its width in cells (fewer threads across it when V > VEC).
+  // its width in cells and its thread count, so with V > VEC it has fewer
+  // threads across and more rows (a 16-bit tile of 128 x 4 cells at 4 cells
+  // per thread becomes 128 x 8 at 8: less halo per row, and the same
+  // number of warps per block).
   static Geom step_geom(const Handle* h, int v) {
     if (v == VEC) return make_geom(h, VEC);
     Handle t = *h;
     t.tile.bx = std::max(1, h->tile.bx * VEC / v);
+    t.tile.by = std::max(1, std::min(h->ny, h->tile.by * v / VEC));
     return make_geom(&t, v);
+  }
+
+  // Tensor maps of the handle's arrays for the pipelined sweeps of geometry
+  // g at V cells per thread (see StepMaps).  TMA needs the halo'd tile's x
+  // origin, one vector left of the tile, on a 16-byte boundary: V cells of T
+  // must be 16 bytes.
+  template <int V>
+  static bool encode_step_maps(const Handle* h, const Geom& g, StepMaps* m) {
+    if (V * sizeof(T) != 16 || h->stencil != 7) return false;
+    const Workspace& w = h->ws;
+    const int TW = g.bx * V, W = TW + 2 * V, nx = h->nx, ny = h->ny, nz = h->nz;
+    bool ok = true;
+    for (int d = 0; d < 6; ++d) ok = ok && encode_box<T>(&m->c[d], h->c[d], nx, ny, nz, TW, g.by);
+    ok = ok && encode_box<T>(&m->rh, w.rh, nx, ny, nz, TW, g.by);
+    const void* ins[MAP_NIN] = {w.r, w.r2 ? w.r2 : w.r, w.p[0], w.p[1], w.s[0], w.s[1], w.y};
+    for (int k = 0; k < MAP_NIN; ++k)
+      ok = ok && encode_box<T>(&m->in[k], ins[k], nx, ny, nz, W, g.by + 2);
+    ok = ok && encode_box<X>(&m->x, w.x, nx, ny, nz, TW, g.by);
+    return ok;
+  }
+
+  // The handle's maps for geometry g at V cells per thread (host memory,
+  // built when the handle holds none for that tile); NULL when TMA does not
+  // apply.
+  template <int V>
+  static const StepMaps* maps_for(const Handle* hc, const Geom& g) {
+    Handle* h = const_cast<Handle*>(hc);
+    Workspace& w = h->ws;
+    if (!h->tma || !w.ready) return nullptr;
+    StepMaps* m = reinterpret_cast<StepMaps*>(w.maps);
+    int* key = w.maps_key;
+    if (key[0] == g.bx && key[1] == g.by && key[2] == V) return m;
+    key[0] = 0;
+    memset(m, 0, sizeof *m);
+    if (!encode_step_maps<V>(h, g, m)) return nullptr;
+    key[0] = g.bx;
+    key[1] = g.by;
+    key[2] = V;
+    return m;
   }
 
   template <int KIND, int STAGES, int V = VEC>
@@ -477,11 +568,15 @@ struct EngineImpl {
     a.rbuf[1] = (T*)w.r2;
     a.x = w.x;
     a.hist = w.hist;
+    a.maps = nullptr;
+    static const StepMaps none = {};
+    const StepMaps* maps = maps_for<V>(h, g);
     const size_t smem = step_smem_bytes<T, A, V>(g.bx, g.by, STAGES, KIND);
-    void (*kern)(Geom, StepArgs<T>, Scalars*) = k_step<T, A, V, KIND, STAGES>;
+    void (*kern)(Geom, StepArgs<T>, Scalars*, const StepMaps, int) =
+        k_step<T, A, V, KIND, STAGES>;
     if (allow_smem((const void*)kern, smem, st)) return S7_ECUDA;
     const int threads = ((g.bx * g.by + 31) / 32) * 32;
-    kern<<<s7_nblocks(g), threads, smem, st>>>(g, a, w.sc);
+    kern<<<s7_nblocks(g), threads, smem, st>>>(g, a, w.sc, maps ? *maps : none, maps ? 1 : 0);
     return cudaGetLastError() == cudaSuccess ? S7_OK : S7_ECUDA;
   }
 

@@ -12,6 +12,8 @@ namespace s7 {
 
 struct Scalars;
 
+constexpr size_t kMapsBytes = 2048;   // room for the tensor maps of one tile shape
+
 // Makes `dev` the calling thread's current device for the scope of an entry
 // point and gives the caller's current device back when the scope ends, so
 // a caller that works on several devices keeps the device it selected.
@@ -59,7 +61,14 @@ struct Workspace {
   cudaGraphExec_t graph = nullptr;
   int graph_steps = 0;
   bool ready = false;
+  // TMA tensor maps of the pipelined sweeps for the handle's own solves
+  // (host memory, passed to the kernels by value); key = (bx, by, cells per
+  // thread) they were built for, bx = 0 when not built
+  alignas(128) unsigned char maps[kMapsBytes];
+  int maps_key[3] = {0, 0, 0};
 };
+
+
 
 // Launch shape of the sweeps.
 struct Tile {
@@ -91,6 +100,7 @@ struct Handle {
   int variant;                // 0: three reductions per step; 1: two (merged passes)
   int step_vec = 0;           // cells per thread in the pipelined sweeps
   int resid_f64 = 0;          // 1: float64-accuracy residual sweeps in binary64
+  int tma = 0;                // 1: pipelined sweeps of single solves stage with TMA
   size_t bytes = 0;           // device bytes held
   void* small = nullptr;      // 256 bytes of device scratch (flags)
   cudaStream_t stream = nullptr;   // private stream (captures, solves)

@@ -27,11 +27,83 @@
 // held stage k-1 (fully consumed before the barrier), forms plane z+1 into
 // the 3-buffer vector ring, and computes plane z from the ring buffer
 // written at step k-1.
+//
+// Staging engine.  With tensor maps of the handle's arrays (StepArgs::maps,
+// a kernel parameter of the single-system sweeps), the first warp stages
+// each plane with TMA tensor copies (cp.async.bulk.tensor, one box per
+// lane: the six coefficient tiles, r0_hat, the inputs with their halo, the
+// iterate tile), completing on a per-stage mbarrier; boxes reaching past
+// the mesh are zero-filled by the copy engine.  Otherwise every thread
+// issues cp.async copies of its own vectors and halo.  Both fill the same
+// shared-memory layout with the same values, so the two give identical
+// results; TMA takes the per-thread address, predicate and copy
+// instructions off the critical path.
 #pragma once
+
+#include <cuda.h>
+
+#include <type_traits>
 
 #include "s7_sweep.cuh"
 
 namespace s7 {
+
+// Tensor maps of one handle's arrays for one tile shape (a kernel
+// parameter): coefficient and r0_hat tiles (box TW x by x 1), the
+// SpMV inputs with a one-cell halo ring (box (TW + 2 VEC) x (by + 2) x 1,
+// started one vector left of and one row below the tile), the iterate tile.
+enum { MAP_R = 0, MAP_R2, MAP_P0, MAP_P1, MAP_S0, MAP_S1, MAP_Y, MAP_NIN };
+struct StepMaps {
+  CUtensorMap c[6];
+  CUtensorMap rh;
+  CUtensorMap in[MAP_NIN];
+  CUtensorMap x;
+};
+
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() {
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Wait for phase `parity` of the mbarrier, at most about two seconds of SM
+// clock; false if the wait gave up.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity))
+    if (clock64() - t0 > (1LL << 32)) return false;
+  return true;
+}
+// Order this thread's earlier shared-memory accesses before later
+// asynchronous-proxy (TMA) writes to the same memory.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+// 3D tile load of the box at (x, y, z) of `map` into shared memory at `dst`
+// (128-byte aligned), completing on the mbarrier `bar`.
+__device__ __forceinline__ void tma_load_3d(unsigned dst, const CUtensorMap* map, int x, int y,
+                                            int z, unsigned bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];\n" ::"r"(dst),
+      "l"(map), "r"(x), "r"(y), "r"(z), "r"(bar)
+      : "memory");
+}
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
   return (unsigned)__cvta_generic_to_shared(p);
@@ -79,6 +151,8 @@ struct StepArgs {
   T* rbuf[2];
   void* x;
   double* hist;
+  const StepMaps* maps;   // tensor maps for this tile shape (kernel parameter space), or
+                          // NULL: cp.async staging
 };
 
 // The iterate's type for storage type T (float64 for float64 storage).
@@ -136,9 +210,15 @@ __device__ __forceinline__ void init_src(MergedPass<T, X, A>& p, const StepArgs<
   p.hist = a.hist;
 }
 
+// Every staged array of a stage starts on a 128-byte boundary (the
+// alignment of a TMA destination), so it is one dense box of a tensor copy.
+__host__ __device__ constexpr size_t round128(size_t b) { return (b + 127) / 128 * 128; }
+
 template <class T, int VEC>
 struct StepLayout {
   int TW, W, rows;     // tile width (elements), padded row pitch, rows incl. halo
+  int cs;              // elements from one coefficient tile to the next (r0_hat: one more)
+  int PL;              // elements from one staged input plane to the next
   int coef_sz, rh_sz, in_sz, stage_sz;  // in elements of T
 };
 
@@ -148,19 +228,21 @@ __host__ __device__ inline StepLayout<T, VEC> step_layout(int bx, int by, int ni
   L.TW = bx * VEC;
   L.W = L.TW + 2 * VEC;
   L.rows = by + 2;
-  L.coef_sz = 6 * by * L.TW;
-  L.rh_sz = rh ? by * L.TW : 0;
-  L.in_sz = nin * L.rows * L.W;
+  L.cs = (int)(round128((size_t)by * L.TW * sizeof(T)) / sizeof(T));
+  L.PL = (int)(round128((size_t)L.rows * L.W * sizeof(T)) / sizeof(T));
+  L.coef_sz = 6 * L.cs;
+  L.rh_sz = rh ? L.cs : 0;
+  L.in_sz = nin * L.PL;
   L.stage_sz = L.coef_sz + L.rh_sz + L.in_sz;
   return L;
 }
 
-// Bytes of the staged T arrays of one stage, rounded up so every stage (and
-// the iterate tile after them, and the ring after the stages) starts on a
-// 16-byte boundary (vector shared-memory accesses).
+// Bytes of the staged T arrays of one stage (a multiple of 128, so the
+// iterate tile after them, the next stage and the ring after the stages
+// stay 128-byte aligned).
 template <class T, int VEC>
 __host__ __device__ inline size_t stage_stride_bytes(const StepLayout<T, VEC>& L) {
-  return ((size_t)L.stage_sz * sizeof(T) + 15) / 16 * 16;
+  return round128((size_t)L.stage_sz * sizeof(T));
 }
 
 // Bytes of one stage of kind KIND: the T arrays, then (kind 3) the tile of
@@ -168,8 +250,8 @@ __host__ __device__ inline size_t stage_stride_bytes(const StepLayout<T, VEC>& L
 template <class T, int VEC, int KIND>
 __host__ __device__ inline size_t kind_stride_bytes(const StepLayout<T, VEC>& L) {
   if (!KindShape<KIND>::x) return stage_stride_bytes(L);
-  return (stage_stride_bytes(L) + sizeof(typename IterOf<T>::t) * L.TW * (L.rows - 2) + 15) /
-         16 * 16;
+  return stage_stride_bytes(L) +
+         round128(sizeof(typename IterOf<T>::t) * L.TW * (size_t)(L.rows - 2));
 }
 
 template <class T, int VEC, int KIND>
@@ -177,11 +259,20 @@ __host__ __device__ inline StepLayout<T, VEC> kind_layout(int bx, int by) {
   return step_layout<T, VEC>(bx, by, KindShape<KIND>::nin, KindShape<KIND>::rh);
 }
 
+// Element type of the ring of the on-the-fly vector (p or q): the storage
+// type, which holds it exactly (both are rounded to storage when formed),
+// in half the bytes of the arithmetic type for 16-bit storage.
+template <class T, class A, int KIND> struct RingOf {
+  typedef T t;
+};
+
+// Dynamic shared memory of a block: the stages, the 3-plane ring of the
+// on-the-fly vector, and 128 bytes to align the start.
 template <class T, class A, int VEC, int KIND>
 __host__ __device__ inline size_t kind_smem_bytes(int bx, int by, int stages) {
   const StepLayout<T, VEC> L = kind_layout<T, VEC, KIND>(bx, by);
-  const size_t ring = (size_t)3 * L.rows * L.W * sizeof(A);
-  return (size_t)stages * kind_stride_bytes<T, VEC, KIND>(L) + ring;
+  const size_t ring = (size_t)3 * L.rows * L.W * sizeof(typename RingOf<T, A, KIND>::t);
+  return (size_t)stages * kind_stride_bytes<T, VEC, KIND>(L) + ring + 128;
 }
 
 template <class T, class A, int VEC>
@@ -196,11 +287,12 @@ __host__ __device__ inline size_t step_smem_bytes(int bx, int by, int stages, in
 
 // Block `bid` of the `nblocks` blocks of one pipelined sweep over the mesh
 // `g` (s7_smem: the dynamic shared memory; red: 128 doubles of reduction
-// scratch).  The caller has checked the stop flag.
+// scratch; bars: STAGES mbarriers for the TMA staging).  The caller has
+// checked the stop flag.
 template <class T, class A, int VEC, int KIND, int STAGES>
 __device__ __forceinline__ void step_body(const Geom& g, const StepArgs<T>& a, Scalars* sc,
                                           int bid, int nb_total, unsigned char* s7_smem,
-                                          double* red) {
+                                          double* red, unsigned long long* bars) {
   typedef typename IterOf<T>::t X;
   const int it = sc->iter;
   const bool odd = (it & 1) != 0;
@@ -221,9 +313,13 @@ __device__ __forceinline__ void step_body(const Geom& g, const StepArgs<T>& a, S
 
   const StepLayout<T, VEC> L = kind_layout<T, VEC, KIND>(g.bx, g.by);
   const size_t sstride = kind_stride_bytes<T, VEC, KIND>(L);
-  auto stage_buf = [&](int k) { return reinterpret_cast<T*>(s7_smem + (size_t)k * sstride); };
-  A* ring = reinterpret_cast<A*>(s7_smem + (size_t)STAGES * sstride);
-  const int PL = L.rows * L.W;
+  // the stages start on a 128-byte boundary (the dynamic area has 128 bytes to spare)
+  unsigned char* sm = s7_smem + ((128u - (smem_u32(s7_smem) & 127u)) & 127u);
+  auto stage_buf = [&](int k) { return reinterpret_cast<T*>(sm + (size_t)k * sstride); };
+  typedef typename RingOf<T, A, KIND>::t R;
+  R* ring = reinterpret_cast<R*>(sm + (size_t)STAGES * sstride);
+  const int PL = L.PL;              // staged input planes
+  const int RPL = L.rows * L.W;     // ring planes
 
   const int t = threadIdx.x;
   const bool has_cell = t < g.bx * g.by;
@@ -258,7 +354,7 @@ __device__ __forceinline__ void step_body(const Geom& g, const StepArgs<T>& a, S
     const int z = z0 + k;
     const long long gi = own ? (long long)z * g.plane + row : 0;
 #pragma unroll
-    for (int d = 0; d < 6; ++d) cp_async<VB>(buf + d * g.by * L.TW + sc_own, a.c[d] + gi, own ? VB : 0);
+    for (int d = 0; d < 6; ++d) cp_async<VB>(buf + d * L.cs + sc_own, a.c[d] + gi, own ? VB : 0);
     if constexpr (KindShape<KIND>::rh) cp_async<VB>(buf + L.coef_sz + sc_own, a.rh + gi, own ? VB : 0);
     const int zi = z + 1;
     if (zi >= g.nz) return;
@@ -286,16 +382,81 @@ __device__ __forceinline__ void step_body(const Geom& g, const StepArgs<T>& a, S
     }
   };
 
+  // ---- the same stage as TMA tensor copies, issued by the first warp, one
+  // box per lane: every array of the stage is one box at the tile's origin
+  // (inputs: one vector left and one row below it, with the halo ring);
+  // lane 0 first sets the buffer's mbarrier to expect the bytes of every
+  // box, cells past the mesh included (the copy engine fills them with
+  // zeros).
+  const StepMaps* maps = a.maps;
+  const int m_in0 = KIND >= 2 ? (odd ? MAP_R2 : MAP_R) : MAP_R;
+  const int m_in1 = (KIND == 0) ? (odd ? MAP_P0 : MAP_P1) : (odd ? MAP_S1 : MAP_S0);
+  const int m_in2 = (KIND == 0) ? (odd ? MAP_S0 : MAP_S1) : MAP_Y;
+  const int m_in3 = odd ? MAP_P1 : MAP_P0;
+  constexpr int NT = 6 + (KindShape<KIND>::rh ? 1 : 0);   // tile boxes of a plane
+  auto issue_stage_tma = [&](int k, T* buf) {   // called by the 32 lanes of warp 0
+    const int lane = t & 31;
+    const int z = z0 + k;
+    const int zi = z + 1;
+    const unsigned bar = smem_u32(bars + (k % STAGES));
+    const unsigned tile_b = (unsigned)(L.TW * g.by * sizeof(T));
+    const unsigned in_b = (unsigned)(L.W * L.rows * sizeof(T));
+    const int nxb = (zi < g.nz && KindShape<KIND>::x) ? 1 : 0;   // iterate tile box
+    const int nib = zi < g.nz ? nin : 0;                           // input boxes
+    if (lane == 0)
+      mbar_expect_tx(bar, NT * tile_b + nib * in_b + nxb * (unsigned)(L.TW * g.by * sizeof(X)));
+    __syncwarp();
+    const unsigned b0 = smem_u32(buf);
+    if (lane < 6) {
+      tma_load_3d(b0 + (unsigned)(lane * L.cs * sizeof(T)), &maps->c[lane], x0, y0, z, bar);
+    } else if (KindShape<KIND>::rh && lane == 6) {
+      tma_load_3d(b0 + (unsigned)(L.coef_sz * sizeof(T)), &maps->rh, x0, y0, z, bar);
+    } else if (lane == NT && nxb) {
+      tma_load_3d(b0 + (unsigned)stage_stride_bytes(L), &maps->x, x0, y0, zi, bar);
+    } else if (lane >= NT + nxb && lane < NT + nxb + nib) {
+      const int sidx = lane - NT - nxb;
+      const int m = sidx == 0 ? m_in0 : (sidx == 1 ? m_in1 : ((KIND == 3 && sidx == 3) ? m_in3 : m_in2));
+      tma_load_3d(b0 + (unsigned)((L.coef_sz + L.rh_sz + sidx * PL) * sizeof(T)), &maps->in[m],
+                  x0 - VEC, y0 - 1, zi, bar);
+    }
+  };
+  // A wait that gave up (about two seconds) marks the solve timed out
+  // (status 5, S7_ETIMEOUT) and stops waiting: every thread still reaches
+  // every barrier, the block ends, and the host reads the status.
+  __shared__ int s_timed_out;
+  // The mbarriers of the stage buffers: one arrival (the issuing thread's,
+  // with the byte count) per phase.
+  if (maps) {
+    if (t == 0) {
+      s_timed_out = 0;
+      for (int k = 0; k < STAGES; ++k) mbar_init(smem_u32(bars + k), 1);
+      mbar_init_fence();
+    }
+    __syncthreads();
+  }
+  auto wait_stage = [&](int k) {
+    if (maps) {
+      if (!*((volatile int*)&s_timed_out) &&
+          !mbar_wait_bounded(smem_u32(bars + (k % STAGES)), (unsigned)((k / STAGES) & 1))) {
+        s_timed_out = 1;
+        sc->status = 5;
+        sc->done = 1;
+      }
+    } else {
+      cp_async_wait<STAGES - 2>();
+    }
+  };
+
   // p_{i+1} of the fused pass from r_i, s_i, y_i, p_i (as MergedPass forms it)
   auto form_merged = [&](A rv, A sv, A yv, A pv, A& q, A& rn) -> A {
-    q = q_of(rv, sv, alpha);
+    q = q_of<T>(rv, sv, alpha);
     rn = as_stored<T>(fma(-omega, yv, q));
     return as_stored<T>(fma(beta, fma(-omega, sv, pv), rn));
   };
   // value of the on-the-fly vector from staged inputs (index e in a plane)
   auto form = [&](const T* inb, int e) -> A {
     const A rv = to_acc<A>(inb[e]);
-    if constexpr (KIND == 1 || KIND == 2) return q_of(rv, to_acc<A>(inb[PL + e]), alpha);
+    if constexpr (KIND == 1 || KIND == 2) return q_of<T>(rv, to_acc<A>(inb[PL + e]), alpha);
     if constexpr (KIND == 3) {
       A q, rn;
       return form_merged(rv, to_acc<A>(inb[PL + e]), to_acc<A>(inb[2 * PL + e]),
@@ -311,7 +472,7 @@ __device__ __forceinline__ void step_body(const Geom& g, const StepArgs<T>& a, S
       A sv[VEC];
       ldv<T, VEC>(inb + PL + e, sv);
 #pragma unroll
-      for (int j = 0; j < VEC; ++j) v[j] = q_of(v[j], sv[j], alpha);
+      for (int j = 0; j < VEC; ++j) v[j] = q_of<T>(v[j], sv[j], alpha);
     } else if constexpr (KIND == 3) {
       A sv[VEC], yv[VEC], pv[VEC];
       ldv<T, VEC>(inb + PL + e, sv);
@@ -347,7 +508,7 @@ __device__ __forceinline__ void step_body(const Geom& g, const StepArgs<T>& a, S
     auto prod1 = [&](long long i) -> A { return src.produce1(i); };
     if (z0 > 0 && own) prod((long long)(z0 - 1) * g.plane + row, VEC, vm, false);
     else zero(vm);
-    A* rb = ring;
+    R* rb = ring;
     if (has_cell) {
       const long long base = (long long)z0 * g.plane + row;
       if (own) {
@@ -360,30 +521,36 @@ __device__ __forceinline__ void step_body(const Geom& g, const StepArgs<T>& a, S
       } else {
         zero(vc);
       }
-      sm_store<A, VEC>(rb + so, vc);
+      stv<R, VEC>(rb + so, vc);
       if (ty == 0) {
         A h[VEC];
         if (y0 > 0 && x < g.nx) prod(base - g.nx, VEC, h, false);
         else zero(h);
-        sm_store<A, VEC>(rb + so - L.W, h);
+        stv<R, VEC>(rb + so - L.W, h);
       }
       if (ty == g.by - 1) {
         A h[VEC];
         if (y + 1 < g.ny && x < g.nx) prod(base + g.nx, VEC, h, false);
         else zero(h);
-        sm_store<A, VEC>(rb + so + L.W, h);
+        stv<R, VEC>(rb + so + L.W, h);
       }
-      if (tx == 0) rb[so - 1] = (x0 > 0 && y < g.ny) ? prod1(base - 1) : A(0);
-      if (tx == g.bx - 1) rb[so + VEC] = (x + VEC < g.nx && y < g.ny) ? prod1(base + VEC) : A(0);
+      if (tx == 0) rb[so - 1] = from_acc<R>((x0 > 0 && y < g.ny) ? prod1(base - 1) : A(0));
+      if (tx == g.bx - 1)
+        rb[so + VEC] = from_acc<R>((x + VEC < g.nx && y < g.ny) ? prod1(base + VEC) : A(0));
     } else {
       zero(vc);
     }
   }
   const int nsteps = z1 - z0;
+  if (maps) {
+    if (t < 32)
+      for (int k = 0; k < STAGES - 1 && k < nsteps; ++k) issue_stage_tma(k, stage_buf(k));
+  } else {
 #pragma unroll
-  for (int k = 0; k < STAGES - 1; ++k) {
-    if (k < nsteps) issue_stage(k, stage_buf(k));
-    cp_async_commit();
+    for (int k = 0; k < STAGES - 1; ++k) {
+      if (k < nsteps) issue_stage(k, stage_buf(k));
+      cp_async_commit();
+    }
   }
 
   DotAcc<A, (KIND >= 2 ? 3 : 2)> acc;
@@ -391,18 +558,25 @@ __device__ __forceinline__ void step_body(const Geom& g, const StepArgs<T>& a, S
   acc.init();
   for (int k = 0; k < nsteps; ++k) {
     const int z = z0 + k;
-    cp_async_wait<STAGES - 2>();
+    wait_stage(k);
     __syncthreads();
     // refill the buffer of stage k-1 with stage k+STAGES-1
     {
       const int kn = k + STAGES - 1;
-      if (kn < nsteps) issue_stage(kn, stage_buf(kn % STAGES));
-      cp_async_commit();
+      if (maps) {
+        if (t < 32 && kn < nsteps) {
+          fence_proxy_async_smem();   // this block's reads of the buffer came first
+          issue_stage_tma(kn, stage_buf(kn % STAGES));
+        }
+      } else {
+        if (kn < nsteps) issue_stage(kn, stage_buf(kn % STAGES));
+        cp_async_commit();
+      }
     }
     const T* st = stage_buf(k % STAGES);
     const T* inb = st + L.coef_sz + L.rh_sz;
     // form plane z+1: own cells (+ ring if the next step needs it)
-    A* nb = ring + ((k + 1) % 3) * PL;
+    R* nb = ring + ((k + 1) % 3) * RPL;
     if (z + 1 < g.nz) {
       const bool ring_needed = z + 1 < z1;
       if (has_cell) {
@@ -434,20 +608,20 @@ __device__ __forceinline__ void step_body(const Geom& g, const StepArgs<T>& a, S
           else zero(vp);
         }
         if (ring_needed) {
-          sm_store<A, VEC>(nb + so, vp);
+          stv<R, VEC>(nb + so, vp);
           if (KIND == 0 && own) store_run<T, VEC, true, true>(p_out + (long long)(z + 1) * g.plane + row, VEC, vp);
           if (ty == 0) {
             A h[VEC];
             form_run(inb, so - L.W, h);
-            sm_store<A, VEC>(nb + so - L.W, h);
+            stv<R, VEC>(nb + so - L.W, h);
           }
           if (ty == g.by - 1) {
             A h[VEC];
             form_run(inb, so + L.W, h);
-            sm_store<A, VEC>(nb + so + L.W, h);
+            stv<R, VEC>(nb + so + L.W, h);
           }
-          if (tx == 0) nb[so - 1] = form(inb, so - 1);
-          if (tx == g.bx - 1) nb[so + VEC] = form(inb, so + VEC);
+          if (tx == 0) nb[so - 1] = from_acc<R>(form(inb, so - 1));
+          if (tx == g.bx - 1) nb[so + VEC] = from_acc<R>(form(inb, so + VEC));
         }
       }
     } else {
@@ -455,14 +629,14 @@ __device__ __forceinline__ void step_body(const Geom& g, const StepArgs<T>& a, S
     }
     // stencil on plane z
     if (own) {
-      const A* cb = ring + (k % 3) * PL;
+      const R* cb = ring + (k % 3) * RPL;
       A up[VEC], dn[VEC], c[6][VEC];
-      sm_load<A, VEC>(cb + so - L.W, up);
-      sm_load<A, VEC>(cb + so + L.W, dn);
-      const A lf = cb[so - 1];
-      const A rt = cb[so + VEC];
+      ldv<R, VEC>(cb + so - L.W, up);
+      ldv<R, VEC>(cb + so + L.W, dn);
+      const A lf = to_acc<A>(cb[so - 1]);
+      const A rt = to_acc<A>(cb[so + VEC]);
 #pragma unroll
-      for (int d = 0; d < 6; ++d) ldv<T, VEC>(st + d * g.by * L.TW + sc_own, c[d]);
+      for (int d = 0; d < 6; ++d) ldv<T, VEC>(st + d * L.cs + sc_own, c[d]);
       A o[VEC];
 #pragma unroll
       for (int j = 0; j < VEC; ++j) {
@@ -517,7 +691,7 @@ __device__ __forceinline__ void step_body(const Geom& g, const StepArgs<T>& a, S
       if constexpr (KIND == 3) rn_c[j] = rn_p[j];
     }
   }
-  cp_async_wait<0>();
+  if (!maps) cp_async_wait<0>();
   acc.fold();
   if constexpr (KIND >= 2) {
     double v[3] = {acc.tot[0], acc.tot[1], acc.tot[I2]}, tot[3];
@@ -561,12 +735,18 @@ __device__ __forceinline__ void step_body(const Geom& g, const StepArgs<T>& a, S
   }
 }
 
+// maps: the tensor maps of the tile (used when use_maps is 1), passed by
+// value so they sit in kernel parameter space.
 template <class T, class A, int VEC, int KIND, int STAGES>
-__global__ void __launch_bounds__(256) k_step(Geom g, StepArgs<T> a, Scalars* sc) {
+__global__ void __launch_bounds__(256) k_step(Geom g, StepArgs<T> a, Scalars* sc,
+                                              const __grid_constant__ StepMaps maps,
+                                              int use_maps) {
   extern __shared__ __align__(16) unsigned char s7_smem[];
   __shared__ double red[32 * 4];
+  __shared__ __align__(8) unsigned long long bars[STAGES];
   if (*((volatile int*)&sc->done)) return;
-  step_body<T, A, VEC, KIND, STAGES>(g, a, sc, blockIdx.x, s7_nblocks(g), s7_smem, red);
+  a.maps = use_maps ? &maps : nullptr;
+  step_body<T, A, VEC, KIND, STAGES>(g, a, sc, blockIdx.x, s7_nblocks(g), s7_smem, red, bars);
 }
 
 }  // namespace s7

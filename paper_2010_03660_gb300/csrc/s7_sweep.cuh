@@ -329,9 +329,13 @@ struct SrcPUpdate {
   }
 };
 
-// q_i = r_i - alpha_i s_i (not stored; the update kernel forms it again with
-// the same operations, so both see identical values).
-template <class A> __device__ __forceinline__ A q_of(A r, A s, A alpha) { return fma(-alpha, s, r); }
+// q_i = r_i - alpha_i s_i, rounded to the storage type like every other
+// Krylov vector (a no-op for float32 and float64 storage).  It is not
+// stored: the SpMV sweep, the update and the fused pass each form it with
+// these operations, so all of them see identical values.
+template <class T, class A> __device__ __forceinline__ A q_of(A r, A s, A alpha) {
+  return as_stored<T>(fma(-alpha, s, r));
+}
 
 template <class T, class A>
 struct SrcQ {
@@ -349,10 +353,10 @@ struct SrcQ {
     load_run<T, VEC, VL>(r + i, nv, v);
     load_run<T, VEC, VL>(s + i, nv, sv);
 #pragma unroll
-    for (int k = 0; k < VEC; ++k) v[k] = q_of(v[k], sv[k], alpha);
+    for (int k = 0; k < VEC; ++k) v[k] = q_of<T>(v[k], sv[k], alpha);
   }
   __device__ __forceinline__ A produce1(long long i) {
-    return q_of(to_acc<A>(r[i]), to_acc<A>(s[i]), alpha);
+    return q_of<T>(to_acc<A>(r[i]), to_acc<A>(s[i]), alpha);
   }
 };
 
@@ -607,10 +611,10 @@ struct SrcQ2 {
     load_run<T, VEC, VL>(r + i, nv, v);
     load_run<T, VEC, VL>(s + i, nv, sv);
 #pragma unroll
-    for (int k = 0; k < VEC; ++k) v[k] = q_of(v[k], sv[k], alpha);
+    for (int k = 0; k < VEC; ++k) v[k] = q_of<T>(v[k], sv[k], alpha);
   }
   __device__ __forceinline__ A produce1(long long i) {
-    return q_of(to_acc<A>(r[i]), to_acc<A>(s[i]), alpha);
+    return q_of<T>(to_acc<A>(r[i]), to_acc<A>(s[i]), alpha);
   }
 };
 
@@ -750,7 +754,7 @@ struct MergedPass {
     pw = pc = 0;
   }
   __device__ __forceinline__ void form(A rv, A sv, A yv, A pv, A& q, A& rn, A& pn) const {
-    q = q_of(rv, sv, alpha);
+    q = q_of<T>(rv, sv, alpha);
     rn = as_stored<T>(fma(-omega, yv, q));
     pn = as_stored<T>(fma(beta, fma(-omega, sv, pv), rn));
   }

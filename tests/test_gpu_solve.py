@@ -206,6 +206,30 @@ def test_pipeline_depth_two_reduction_variant(s7, storage, shape):
         assert np.array_equal(o.x.cpu().numpy(), outs[0].x.cpu().numpy())
 
 
+@pytest.mark.parametrize("storage", ["f64", "f32", "bf16", "f16"])
+@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("shape", [(64, 48, 40), (136, 21, 37), (8, 5, 70), (256, 8, 16)])
+def test_tma_staging_equals_cp_async(s7, storage, variant, shape):
+    """The pipelined sweeps staged by per-thread cp.async copies (the default)
+    and by TMA tensor copies fill the same shared-memory tiles with the same
+    values (zeros past the mesh edges), so the solves agree bit for bit:
+    several x tiles, odd y extents, many z chunks, a tile wider than the
+    mesh.  16-bit storage at 8 cells per thread (the width TMA applies to)."""
+    nx, ny, nz = shape
+    raw = np.float64 if storage == "f64" else np.float32
+    p = synth.varcoef(nx, ny, nz, seed=48, dtype=raw)
+    tol = 1e-6 if storage in ("f32", "f64") else 1e-3
+    outs = []
+    for tma in (False, True):
+        with s7.stencil7_create(nx, ny, nz, gu.coef_on_device(p), storage=storage,
+                                variant=variant, zchunk=7, tma=tma) as op:
+            outs.append(s7.bicgstab_solve(op, gu.to_dev(p.b), tol=tol, maxit=300))
+    assert outs[0].status == 0
+    assert outs[1].iters == outs[0].iters and outs[1].status == outs[0].status
+    assert np.array_equal(outs[1].hist, outs[0].hist)
+    assert np.array_equal(outs[1].x.cpu().numpy(), outs[0].x.cpu().numpy())
+
+
 @pytest.mark.parametrize("storage", ["bf16", "f16"])
 @pytest.mark.parametrize("variant", [0, 1])
 def test_16bit_eight_cells_per_thread(s7, storage, variant):
