@@ -351,7 +351,9 @@ typedef struct {
   int max_active;          /* at most this many admitted requests; 0 = 256         */
   int steps_per_tick;      /* batched steps between host checks; 0 = 4             */
   int threads, zchunk;     /* batched tile policy; 0 = 128 threads, 16 planes      */
-  double inner_tol;        /* inner relative residual; 0 = 1e-2                    */
+  double inner_tol;        /* inner relative residual; 0 = 1e-1 for S7_BF16 storage
+                              (its 8 significant bits cap what one refinement
+                              step gains), 1e-2 otherwise                        */
   int inner_maxit;         /* steps per inner solve; 0 = 100                       */
   int max_outer;           /* refinement steps; 0 = 60                             */
   int three_pass;          /* 1: inner steps as Algorithm 1 prints them (three

@@ -164,8 +164,11 @@ __global__ void __launch_bounds__(256) k_sweep_batched(const SysDesc<T, X>* __re
 // systems all qualify (Jacobi-scaled per-cell operators, rows of whole
 // VEC-cell vectors); each system's geometry in its descriptor is for VEC
 // cells per thread.  Kinds 2 and 3 (the two-reduction variant) need r2.
+// Two 256-thread blocks per SM bound the registers (at most 128 a thread):
+// the descriptor lookup otherwise takes the fused pass to 142 registers and
+// three 128-thread blocks per SM (served BF16 to 1e-8: 0.405 -> 0.374 s).
 template <class T, class X, class A, int VEC, int KIND, int STAGES>
-__global__ void __launch_bounds__(256) k_step_batched(const SysDesc<T, X>* __restrict__ sys,
+__global__ void __launch_bounds__(256, 2) k_step_batched(const SysDesc<T, X>* __restrict__ sys,
                                                       int nsys) {
   extern __shared__ __align__(16) unsigned char s7_smem[];
   __shared__ double red[32 * 4];
