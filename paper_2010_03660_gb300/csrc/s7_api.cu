@@ -1458,7 +1458,7 @@ extern "C" int bicgstab_solve_batched(int nsys, const stencil7_t* hs_in, const v
   }
   // batch-owned scalars, histories, partial sums, descriptors
   {
-    // partials: 2 per block, for the largest block count of any policy tried
+    // partials: up to 3 per block, for the largest block count of any policy tried
     std::vector<BatchPolicy> pols;
     for (int t : {64, 128, 256})
       for (int z : {8, 16, 32}) pols.push_back(BatchPolicy{t, z});
@@ -1475,7 +1475,8 @@ extern "C" int bicgstab_solve_batched(int nsys, const stencil7_t* hs_in, const v
         cap = std::max(cap, nb);
       }
       parts_off[j] = parts_total;
-      parts_total += 2 * (size_t)cap;
+      // up to three sums per block (the two-reduction variant's passes)
+      parts_total += 3 * (size_t)cap;
     }
     bb.h_desc.resize((size_t)nsys * eng->desc_size);
     void* p = nullptr;

@@ -339,7 +339,8 @@ int admit(s7_server* S, Req* r) {
                           ((r->in.nz + t.zchunk - 1) / t.zchunk));
   }
   const long long rb = S->eng->raw_resid_blocks(r->h, S7_F64);
-  r->parts_n = 2 * (size_t)std::max(std::max(nb, rb), 4096LL);
+  // up to three sums per block (the q/y and fused passes reduce three)
+  r->parts_n = 3 * (size_t)std::max(std::max(nb, rb), 4096LL);
   if ((e = dev_alloc(S->device, (void**)&r->parts, r->parts_n * 8, as)) != cudaSuccess) return S7_ENOMEM;
   // b (host or device, f32/f64) -> float64 (zero in the padding); x0 = 0
   const long long rows = (long long)r->in.ny * r->in.nz;
