@@ -93,6 +93,11 @@ def parse():
     ap.add_argument("--edge2d", type=int, default=22800,
                     help="solve9: edge of the square 2D mesh (Sec. IV-A's largest: 22800)")
     ap.add_argument("--systems", type=int, default=512, help="batched: number of systems")
+    ap.add_argument("--bthreads", type=int, default=0,
+                    help="batched: threads per block (0 = autotuned)")
+    ap.add_argument("--bzchunk", type=int, default=0, help="batched: z planes per block (0 = autotuned)")
+    ap.add_argument("--schedule", type=int, default=0,
+                    help="batched: 0 chosen, 1 one persistent launch, -1 one launch per kernel")
     ap.add_argument("--requests", type=int, default=20000, help="serve: requests in the stream")
     ap.add_argument("--rate", type=float, default=40.0, help="serve: arrivals per second")
     ap.add_argument("--serve-deadline", type=float, default=540.0,
@@ -723,7 +728,9 @@ def run_batched(args):
     def fn():
         for x in xs:
             x.zero_()
-        return s7.bicgstab_solve_batched(ops, bs, xs, tol=1e-6, maxit=2000)
+        return s7.bicgstab_solve_batched(ops, bs, xs, tol=1e-6, maxit=2000,
+                                         schedule=args.schedule, threads=args.bthreads,
+                                         zchunk=args.bzchunk)
     ms, outs = _timed(fn, args.steps, max(1, args.warmup))
     r = outs[-1]
     ci = sum(c * it for c, it in zip(cells, r.iters))
@@ -740,6 +747,7 @@ def run_batched(args):
     out = {"metric": "batched cell-iters/s (512 systems, edges 16..128, FP32, tol 1e-6)",
            "value": ci / (ms / 1e3), "unit": "cell-iters/s", "higher_is_better": True,
            "workload": "batched_%d%s" % (args.systems, "_merged" if args.variant else ""),
+           "schedule": {0: "chosen", 1: "persistent", -1: "launch per kernel"}[args.schedule],
            "variant": "two reductions per step" if args.variant else "Algorithm 1",
            "dtype": "f32", "data": "synthetic (seed 1)",
            "ms_per_batch_solve": ms, "systems": len(ops), "total_cells": int(sum(cells)),

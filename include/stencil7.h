@@ -304,6 +304,18 @@ typedef struct {
   int zchunk;       /* z planes per block; 0 = chosen by the autotuner       */
   int check_every;  /* steps per graph launch between host checks; 0 = 16    */
   int no_autotune;  /* 1: skip the autotuner (use threads/zchunk or 128/16)  */
+  int schedule;     /* 1: one persistent launch runs every step of every
+                       system: the blocks that fit on the device at once
+                       claim open tiles (sweep or update blocks) of any
+                       system from per-system work queues, a system's next
+                       phase opening when its previous one completes;
+                       -1: one launch per step kernel, replayed from a
+                       graph; 0: chosen (the persistent launch)             */
+  long long wait_cycles;  /* the persistent launch: longest wait of a block
+                       for an open tile, in SM clock cycles; 0 = 2^31
+                       (about a second).  A wait that runs out aborts the
+                       launch: every unfinished system stops with
+                       S7_ETIMEOUT.                                         */
 } s7_batch_opts;
 
 /* Solve nsys independent systems together (BiCGStab, Algorithm 1, on each;

@@ -85,7 +85,7 @@ class s7_opts(C.Structure):
 
 class s7_batch_opts(C.Structure):
     _fields_ = [("threads", C.c_int), ("zchunk", C.c_int), ("check_every", C.c_int),
-                ("no_autotune", C.c_int)]
+                ("no_autotune", C.c_int), ("schedule", C.c_int), ("wait_cycles", C.c_longlong)]
 
 
 class s7_server_opts(C.Structure):
@@ -487,12 +487,18 @@ class BatchResult:
 
 
 def bicgstab_solve_batched(ops, bs, xs=None, tol=1e-6, maxit=500, threads=0, zchunk=0,
-                           check_every=0, autotune=True):
-    """Solve independent systems together (one launch per kernel covers all).
+                           check_every=0, autotune=True, schedule=0, wait_cycles=0,
+                           allow_timeout=False):
+    """Solve independent systems together (one persistent launch, or one
+    launch per step kernel, covers all).
 
     ``ops``: operators (same storage type); ``bs``: right-hand sides (all the
     same dtype); ``xs``: start vectors (default zeros), overwritten with the
     results.  ``tol`` and ``maxit`` may be scalars or per-system sequences.
+    ``schedule``: 0 chosen, 1 persistent, -1 one launch per step kernel;
+    ``wait_cycles``: bound of the persistent launch's barrier waits (0 =
+    default).  With ``allow_timeout`` an S7_ETIMEOUT return is reported in
+    the result instead of raised.
     """
     n = len(ops)
     if xs is None:
@@ -514,10 +520,11 @@ def bicgstab_solve_batched(ops, bs, xs=None, tol=1e-6, maxit=500, threads=0, zch
     it = (C.c_int * n)()
     stt = (C.c_int * n)()
     rs = (C.c_double * n)()
-    o = s7_batch_opts(threads, zchunk, check_every, 0 if autotune else 1)
+    o = s7_batch_opts(threads, zchunk, check_every, 0 if autotune else 1, int(schedule),
+                      int(wait_cycles))
     rc = lib().bicgstab_solve_batched(n, H, B, X, _dtype_code(bs[0]), T, M, it, stt, rs,
                                       C.byref(o), _stream(*bs))
-    _check(rc, allow=(EBREAKDOWN, ENOTCONV))
+    _check(rc, allow=(EBREAKDOWN, ENOTCONV) + ((ETIMEOUT,) if allow_timeout else ()))
     return BatchResult(xs, list(it), list(stt), list(rs), rc)
 
 

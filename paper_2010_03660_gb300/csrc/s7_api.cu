@@ -1362,9 +1362,12 @@ struct BatchBuffers {
 static int batch_layout(int nsys, Handle* const* hs, const void* const* bdev, const Engine* eng,
                         const BatchPolicy& p, BatchBuffers& bb, const std::vector<size_t>& hist_off,
                         const std::vector<size_t>& parts_off, int* sweep_blocks, int* upd_blocks,
-                        size_t smem[8], int pipe, cudaStream_t st) {
+                        size_t smem[8], int pipe, cudaStream_t st,
+                        std::vector<int>* nbs = nullptr, std::vector<int>* ubs = nullptr) {
   int b0 = 0, u0 = 0;
   for (int k = 0; k < 8; ++k) smem[k] = 0;
+  if (nbs) nbs->assign(nsys, 0);
+  if (ubs) ubs->assign(nsys, 0);
   for (int j = 0; j < nsys; ++j) {
     const Tile t = batch_tile(hs[j], pipe ? eng->vec_wide : eng->vec, p);
     int nb = 0, ub = 0;
@@ -1373,6 +1376,8 @@ static int batch_layout(int nsys, Handle* const* hs, const void* const* bdev, co
                    pipe);
     b0 += nb;
     u0 += ub;
+    if (nbs) (*nbs)[j] = nb;
+    if (ubs) (*ubs)[j] = ub;
     for (int k = 0; k < 8; ++k)
       if (k != 4 && k != 5) smem[k] = std::max(smem[k], eng->batched_smem(hs[j], t, pipe, k));
   }
@@ -1438,6 +1443,11 @@ extern "C" int bicgstab_solve_batched(int nsys, const stencil7_t* hs_in, const v
   size_t smem[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // by launch kind
   BatchPolicy pol{128, 16};
   const int ce = opts.check_every > 0 ? opts.check_every : 16;
+  std::vector<int> sys_nb, sys_ub;   // sweep and update blocks per system
+  int pgrid = 0;                      // blocks of the persistent launch (0: not used)
+  void* d_queue = nullptr;
+  void* d_qstate = nullptr;
+  int* d_order = nullptr;
   cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
   if (e != cudaSuccess) { rc = cuda_fail(e, "event"); goto out; }
   if ((rc = join(us, st, ev))) goto out;
@@ -1461,7 +1471,7 @@ extern "C" int bicgstab_solve_batched(int nsys, const stencil7_t* hs_in, const v
     // partials: up to 3 per block, for the largest block count of any policy tried
     std::vector<BatchPolicy> pols;
     for (int t : {64, 128, 256})
-      for (int z : {8, 16, 32}) pols.push_back(BatchPolicy{t, z});
+      for (int z : {16, 32, 64}) pols.push_back(BatchPolicy{t, z});
     pols.push_back(BatchPolicy{opts.threads > 0 ? std::max(64, std::min(256, opts.threads)) : 128,
                                opts.zchunk > 0 ? opts.zchunk : 16});
     for (int j = 0; j < nsys; ++j) {
@@ -1512,7 +1522,7 @@ extern "C" int bicgstab_solve_batched(int nsys, const stencil7_t* hs_in, const v
     }
     if (!have) {
       const int cand_t[3] = {64, 128, 256};
-      const int cand_z[3] = {8, 16, 32};
+      const int cand_z[3] = {16, 32, 64};
       float best = 1e30f;
       cudaEvent_t e0, e1;
       cudaEventCreate(&e0);
@@ -1549,7 +1559,7 @@ extern "C" int bicgstab_solve_batched(int nsys, const stencil7_t* hs_in, const v
   }
   threads = pol.threads;
   if ((rc = batch_layout(nsys, hs.data(), bdev.data(), eng, pol, bb, hist_off, parts_off,
-                         &sweep_blocks, &upd_blocks, smem, pipe, st)))
+                         &sweep_blocks, &upd_blocks, smem, pipe, st, &sys_nb, &sys_ub)))
     goto out;
   if (eng->batched_prepare(*std::max_element(smem, smem + 8), pipe)) { rc = fail(S7_ECUDA, "batched kernel attributes"); goto out; }
   // scalars: tol, maxit
@@ -1569,6 +1579,68 @@ extern "C" int bicgstab_solve_batched(int nsys, const stencil7_t* hs_in, const v
     rc = fail(rc, "batched start launch failed: %s", cudaGetErrorString(cudaGetLastError()));
     goto out;
   }
+  // the schedule: one persistent launch running every step of every system
+  // from per-system work queues, on as many blocks as fit on the device at
+  // once; or one launch per step kernel replayed from a graph
+  if (opts.schedule >= 0) {
+    const size_t psm = merged ? std::max(smem[6], smem[7]) : std::max(smem[0], smem[1]);
+    int per_sm = 0;
+    if (eng->persistent_occupancy(threads, psm, pipe, merged, &per_sm) == S7_OK && per_sm > 0)
+      pgrid = per_sm * num_sms();
+    if (!pgrid && opts.schedule == 1) {
+      rc = fail(S7_EINVAL, "bicgstab_solve_batched: no block of the persistent launch fits");
+      goto out;
+    }
+  }
+  if (pgrid) {
+    const int dev = hs[0]->device;
+    // blocks look for work in the largest systems first: they set the end
+    std::vector<int> order(nsys);
+    for (int j = 0; j < nsys; ++j) order[j] = j;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return hs[a]->n > hs[b]->n; });
+    if ((e = dev_alloc(dev, &d_queue, (size_t)nsys * kQueueBytes, st)) != cudaSuccess ||
+        (e = dev_alloc(dev, &d_qstate, kQueueStateBytes, st)) != cudaSuccess ||
+        (e = dev_alloc(dev, (void**)&d_order, (size_t)nsys * sizeof(int), st)) != cudaSuccess) {
+      rc = cuda_fail(e, "persistent batch queues");
+      goto out;
+    }
+    if ((e = cudaMemsetAsync(d_qstate, 0, kQueueStateBytes, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(d_order, order.data(), (size_t)nsys * sizeof(int),
+                             cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess) {
+      rc = cuda_fail(e, "persistent batch queues");
+      goto out;
+    }
+    const long long budget = opts.wait_cycles > 0 ? opts.wait_cycles : (1LL << 31);
+    const size_t psm = merged ? std::max(smem[6], smem[7]) : std::max(smem[0], smem[1]);
+    // captured as a graph of one launch; launched directly where the capture
+    // of a cooperative launch is refused
+    cudaGraph_t g = nullptr;
+    bool captured = false;
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      const int lrc = eng->launch_persistent(bb.desc, d_order, d_queue, d_qstate, nsys, pgrid,
+                                             threads, psm, budget, st, pipe, merged);
+      e = cudaStreamEndCapture(st, &g);
+      if (lrc == S7_OK && e == cudaSuccess && g &&
+          cudaGraphInstantiate(&gexec, g, 0) == cudaSuccess)
+        captured = true;
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+    }
+    if (captured) {
+      if ((e = cudaGraphLaunch(gexec, st)) != cudaSuccess) { rc = cuda_fail(e, "persistent graph launch"); goto out; }
+    } else {
+      gexec = nullptr;
+      if ((rc = eng->launch_persistent(bb.desc, d_order, d_queue, d_qstate, nsys, pgrid, threads,
+                                       psm, budget, st, pipe, merged))) {
+        rc = fail(rc, "persistent batched launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+        goto out;
+      }
+    }
+    if ((e = cudaMemcpyAsync(bb.h_sc, bb.sc, (size_t)nsys * sizeof(Scalars), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess) { rc = cuda_fail(e, "persistent batched solve"); goto out; }
+  } else {
   // capture ce steps
   {
     cudaGraph_t g = nullptr;
@@ -1609,9 +1681,10 @@ extern "C" int bicgstab_solve_batched(int nsys, const stencil7_t* hs_in, const v
       if ((e = cudaGraphLaunch(gexec, st)) != cudaSuccess) { rc = cuda_fail(e, "graph launch"); goto out; }
     }
   }
+  }
   // results
   {
-    bool any_break = false, any_nc = false;
+    bool any_break = false, any_nc = false, any_timeout = false;
     for (int j = 0; j < nsys; ++j) {
       const Scalars& s = bb.h_sc[j];
       Handle* h = hs[j];
@@ -1624,15 +1697,20 @@ extern "C" int bicgstab_solve_batched(int nsys, const stencil7_t* hs_in, const v
       if (resid) resid[j] = s.bnorm == 0.0 ? 0.0 : s.res[2];
       any_break |= s.status == S7_EBREAKDOWN;
       any_nc |= s.status == S7_ENOTCONV;
+      any_timeout |= s.status == S7_ETIMEOUT;
     }
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) { rc = cuda_fail(e, "batched results"); goto out; }
-    if (any_break) rc = fail(S7_EBREAKDOWN, "breakdown in at least one system");
+    if (any_timeout) rc = fail(S7_ETIMEOUT, "a group-barrier wait of the persistent launch ran out");
+    else if (any_break) rc = fail(S7_EBREAKDOWN, "breakdown in at least one system");
     else if (any_nc) rc = fail(S7_ENOTCONV, "at least one system did not converge");
   }
 out:
   if (gexec) cudaGraphExecDestroy(gexec);
   if (st) {
     cudaStreamSynchronize(st);
+    dev_free(d_queue, st);
+    dev_free(d_qstate, st);
+    dev_free(d_order, st);
     if (ev && us != st) {
       cudaEventRecord(ev, st);
       cudaStreamWaitEvent(us, ev, 0);

@@ -281,6 +281,8 @@ int launch_sweep9_1(const Geom& g, const CoefView9<CT, A>& cf, const P& pol, Sca
 
 // ---- TMA tensor maps (host side) ----
 static_assert(sizeof(StepMaps) <= kMapsBytes, "tensor maps do not fit their slot");
+static_assert(sizeof(SysQueue) == kQueueBytes && sizeof(QueueState) <= kQueueStateBytes,
+              "work queue layout");
 
 typedef CUresult (*TensorMapEncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
                                            const cuuint64_t*, const cuuint64_t*,
@@ -934,6 +936,9 @@ struct EngineImpl {
     d.ublock0 = ublock0;
     const long long nvec = h->n / VEC;
     d.unblocks = (int)std::max(1LL, std::min(4096LL, (nvec + 1023) / 1024));
+    // the persistent launch claims update tiles one by one: 8192 vectors a
+    // tile keeps the claim a small part of the tile's time
+    d.punblocks = (int)std::max(1LL, std::min(4096LL, (nvec + 8191) / 8192));
     d.constant = h->constant;
     d.n = h->n;
     for (int k = 0; k < 6; ++k) {
@@ -1032,6 +1037,55 @@ struct EngineImpl {
     return cudaGetLastError() == cudaSuccess ? S7_OK : S7_ECUDA;
   }
 
+  // ---- the persistent batched solve ----
+  template <bool PIPE, bool MERGED>
+  static const void* persistent_fn() {
+    return (const void*)k_batched_persistent<T, X, DT, A, PIPE ? VW : VEC, VEC, SB, PIPE, MERGED,
+                                             kPipeQ>;
+  }
+  static const void* persistent_of(int pipe, int merged) {
+    return pipe ? (merged ? persistent_fn<true, true>() : persistent_fn<true, false>())
+                : (merged ? persistent_fn<false, true>() : persistent_fn<false, false>());
+  }
+
+  static int persistent_occupancy(int threads, size_t smem, int pipe, int merged, int* per_sm) {
+    const void* k = persistent_of(pipe, merged);
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k, threads, smem) != cudaSuccess) {
+      cudaGetLastError();
+      return S7_ECUDA;
+    }
+    return S7_OK;
+  }
+
+  static int launch_persistent(const void* descs, const int* order, void* queues, void* qstate,
+                               int nsys, int grid, int threads, size_t smem, long long budget,
+                               cudaStream_t st, int pipe, int merged) {
+    k_queue_init<T, X><<<(nsys + 255) / 256, 256, 0, st>>>((const Desc*)descs, nsys,
+                                                           (SysQueue*)queues, (QueueState*)qstate);
+    if (cudaGetLastError() != cudaSuccess) return S7_ECUDA;
+    cudaLaunchConfig_t cfg;
+    memset(&cfg, 0, sizeof cfg);
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;   // all blocks resident at once
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    void* args[6] = {(void*)&descs, (void*)&order, (void*)&nsys, (void*)&queues, (void*)&qstate,
+                     (void*)&budget};
+    const cudaError_t e = cudaLaunchKernelExC(&cfg, persistent_of(pipe, merged), args);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return S7_ECUDA;
+    }
+    return S7_OK;
+  }
+
   static const Engine* get() {
     static const Engine e = {sizeof(T), sizeof(X), sizeof(DT), VEC, VW, &scale, &scale9, &apply,
                              &init, &step_kernel,
@@ -1039,7 +1093,8 @@ struct EngineImpl {
                              &raw_resid_into, &raw_resid_blocks, &prepare_capture,
                              &merged_kernel,
                              sizeof(Desc), &batch_pipe_ok, &fill_desc, &batched_smem,
-                             &launch_batched, &batched_prepare};
+                             &launch_batched, &batched_prepare, &persistent_occupancy,
+                             &launch_persistent};
     return &e;
   }
 };

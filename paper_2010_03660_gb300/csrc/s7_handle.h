@@ -13,6 +13,8 @@ namespace s7 {
 struct Scalars;
 
 constexpr size_t kMapsBytes = 2048;   // room for the tensor maps of one tile shape
+constexpr size_t kQueueBytes = 16;     // work queue of one system (persistent batched solve)
+constexpr size_t kQueueStateBytes = 16;
 
 // Makes `dev` the calling thread's current device for the scope of an entry
 // point and gives the caller's current device back when the scope ends, so
@@ -171,6 +173,16 @@ struct Engine {
   int (*launch_batched)(int kind, const void* descs, int nsys, int blocks, int threads,
                         size_t smem, cudaStream_t st, int pipe);
   int (*batched_prepare)(size_t smem, int pipe);
+  // The persistent batched solve (s7_batch.cuh, k_batched_persistent):
+  // resident blocks per SM for `threads` threads and `smem` bytes (setting
+  // the kernel's shared-memory limit), and its cooperative launch over
+  // `grid` blocks with work queues (kQueueBytes per system, set up by the
+  // launch) and a zeroed queue state (kQueueStateBytes); `order` (device,
+  // nsys entries) lists the systems in the order blocks look for work.
+  int (*persistent_occupancy)(int threads, size_t smem, int pipe, int merged, int* per_sm);
+  int (*launch_persistent)(const void* descs, const int* order, void* queues, void* qstate,
+                           int nsys, int grid, int threads, size_t smem, long long budget,
+                           cudaStream_t st, int pipe, int merged);
 };
 
 const Engine* engine_f64();

@@ -276,3 +276,65 @@ def test_batched_variants_must_agree(s7):
     finally:
         for op in ops:
             op.close()
+
+
+@pytest.mark.parametrize("storage,variant", [("f32", 0), ("f32", 1), ("bf16", 1)])
+def test_persistent_launch_matches_launch_per_kernel(s7, storage, variant):
+    """One persistent launch (resident blocks claiming tiles from per-system
+    work queues) and one launch per step kernel: both meet the single-system
+    bars against the oracle (the update's partial sums are grouped by the
+    launch's block size, so the two are not the same bits, and float32 step
+    counts move with such regroupings); in the persistent launch a system's
+    result is the same bits alone and in the mix."""
+    shapes = SHAPES if storage == "f32" else [(16, 16, 16), (24, 20, 12), (32, 9, 30), (8, 8, 64)]
+    probs = make(shapes, 800)
+    tol = 1e-6 if storage == "f32" else 1e-2
+    ops = [s7.stencil7_create(p.nx, p.ny, p.nz, gu.coef_on_device(p), storage=storage,
+                              variant=variant) for p in probs]
+    try:
+        kw = dict(tol=tol, maxit=1000, threads=128, zchunk=16)
+        per = s7.bicgstab_solve_batched(ops, [gu.to_dev(p.b) for p in probs], schedule=1, **kw)
+        lpk = s7.bicgstab_solve_batched(ops, [gu.to_dev(p.b) for p in probs], schedule=-1, **kw)
+        for j, p in enumerate(probs):
+            assert per.status[j] == 0 and lpk.status[j] == 0
+            if storage != "f32":
+                assert rel(per.x[j].cpu().numpy(), lpk.x[j].cpu().numpy().astype(np.float64)) <= 0.1
+                continue
+            orc = (ob.bicgstab_merged if variant else ob.bicgstab)(
+                p.nx, p.ny, p.nz, p.coef, p.b, tol=tol, maxit=1000, storage="f32")
+            lo, hi = gu.fp32_step_window(p.nx, p.ny, p.nz, p.coef, p.b, tol, 1000, orc.iters)
+            if variant:   # beta from the rho recurrence: the window of that variant's tests
+                lo, hi = orc.iters - max(6, orc.iters // 4), orc.iters + max(6, orc.iters // 4)
+            for res in (per, lpk):
+                x = res.x[j].cpu().numpy()
+                assert lo <= res.iters[j] <= hi, (j, res.iters[j], lo, hi)
+                assert rel(x, orc.x) <= 100 * tol
+                assert scaled_true_residual(p, x) <= 2 * tol
+        alone = s7.bicgstab_solve_batched([ops[2]], [gu.to_dev(probs[2].b)], schedule=1, **kw)
+        assert alone.iters[0] == per.iters[2]
+        assert np.array_equal(alone.x[0].cpu().numpy(), per.x[2].cpu().numpy())
+    finally:
+        for op in ops:
+            op.close()
+
+
+def test_persistent_wait_bound_gives_timeout(s7):
+    """A wait budget of one cycle: the first block of the persistent launch
+    that finds every open tile taken gives up at once and aborts the launch;
+    the solve returns S7_ETIMEOUT with the unfinished systems' status, no
+    wait outlives its budget, and the device stays usable (the same batch
+    then solves normally)."""
+    probs = make([(64, 64, 48), (40, 31, 25)], 900)
+    ops = [s7.stencil7_create(p.nx, p.ny, p.nz, gu.coef_on_device(p), storage="f32")
+           for p in probs]
+    try:
+        kw = dict(tol=1e-6, maxit=500, threads=128, zchunk=16, schedule=1)
+        res = s7.bicgstab_solve_batched(ops, [gu.to_dev(p.b) for p in probs], wait_cycles=1,
+                                        allow_timeout=True, **kw)
+        assert res.rc == s7.ETIMEOUT
+        assert res.status[0] == s7.ETIMEOUT
+        ok = s7.bicgstab_solve_batched(ops, [gu.to_dev(p.b) for p in probs], **kw)
+        assert ok.rc == 0 and all(st == 0 for st in ok.status)
+    finally:
+        for op in ops:
+            op.close()
