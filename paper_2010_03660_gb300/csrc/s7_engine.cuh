@@ -10,6 +10,7 @@
 #include <string.h>
 
 #include "s7_handle.h"
+#include "s7_resid.cuh"
 #include "s7_step.cuh"
 #include "s7_sweep.cuh"
 #include "s7_sweep9.cuh"
@@ -740,7 +741,42 @@ struct EngineImpl {
   static bool resid_f64(const Handle* h) { return h->resid_f64 != 0; }
 
   // ||b~ - A~ x|| and ||b~|| with float64 accuracy -> sc->res[0], res[1].
+  // ---- the specialised double-word residual sweep (s7_resid.cuh) ----
+  // It applies to 7-point operators with per-cell coefficients, rows of
+  // whole 4-cell vectors and 16-byte aligned buffers, when the residual runs
+  // in double words (not for float64 storage or residual_f64).
+  static bool resid_dw_ok(const Handle* h, const void* b, const void* x, const void* r) {
+    return std::is_same<RA, dfl>::value && !resid_f64(h) && h->stencil == 7 && !h->constant &&
+           h->nx % 4 == 0 && aligned16(b) && aligned16(x) && (!r || aligned16(r));
+  }
+  template <class CT, class XT, bool UNIT>
+  static int launch_resid_dw(const Handle* h, const void* const* c, const void* diag,
+                             const void* dinv, const XT* x, const XT* b, XT* r, double* parts,
+                             Scalars* sc, cudaStream_t st) {
+    const Geom g = make_geom(h, 4);
+    ResidArgs<CT, XT, DT> a;
+    for (int d = 0; d < 6; ++d) a.c[d] = (const CT*)c[d];
+    a.diag = (const CT*)diag;
+    a.dinv = (const DT*)dinv;
+    a.x = x;
+    a.b = b;
+    a.r = r;
+    a.parts = parts;
+    a.counter = CNT_RES;
+    const size_t smem = resid_dw_smem<XT>(g);
+    void (*kern)(Geom, ResidArgs<CT, XT, DT>, Scalars*) = k_resid_dw<CT, XT, DT, UNIT>;
+    if (allow_smem((const void*)kern, smem, st)) return S7_ECUDA;
+    const int threads = ((g.bx * g.by + 31) / 32) * 32;
+    kern<<<s7_nblocks(g), threads, smem, st>>>(g, a, sc);
+    return cudaGetLastError() == cudaSuccess ? S7_OK : S7_ECUDA;
+  }
+
   static int true_resid(Handle* h, const void* b, cudaStream_t st) {
+    if (h->jacobi && resid_dw_ok(h, b, h->ws.x, nullptr)) {
+      const Workspace& w = h->ws;
+      return launch_resid_dw<T, X, true>(h, h->c, nullptr, h->d, (const X*)w.x, (const X*)b,
+                                         nullptr, w.parts, w.sc, st);
+    }
     return resid_f64(h) ? true_resid_r<double>(h, b, st) : true_resid_r<RA>(h, b, st);
   }
 
@@ -766,6 +802,9 @@ struct EngineImpl {
   template <class R, class XT>
   static int raw_resid_t(Handle* h, const XT* b, const XT* x, XT* r, cudaStream_t st) {
     Workspace& w = h->ws;
+    if (h->keep_true && resid_dw_ok(h, b, x, r))
+      return launch_resid_dw<float, XT, false>(h, (const void* const*)h->tc, h->tc[6], nullptr,
+                                               x, b, r, w.parts, w.sc, st);
     if (h->keep_true) {
       constexpr int V = 16 / (int)sizeof(XT) < 4 ? 16 / (int)sizeof(XT) : 4;
       SrcPlain<XT, R> src{x};
@@ -827,6 +866,9 @@ struct EngineImpl {
     epi.counter = CNT_RES;
     epi.mode = 1;
     SrcPlain<XT, R> src{x};
+    if (h->keep_true && resid_dw_ok(h, b, x, r))
+      return launch_resid_dw<float, XT, false>(h, (const void* const*)h->tc, h->tc[6], nullptr,
+                                               x, b, r, parts, sc, st);
     if (h->keep_true) {
       constexpr int V = 16 / (int)sizeof(XT) < 4 ? 16 / (int)sizeof(XT) : 4;
       EpiResid<XT, XT, float, R> e2;
@@ -863,9 +905,11 @@ struct EngineImpl {
                         : raw_resid_into_r<RA>(h, b, x, r, dt, parts, sc, st);
   }
 
+  // Blocks of the raw residual sweep (the noalloc entry point checks its
+  // scratch against this; either sweep may run, so the larger count).
   static long long raw_resid_blocks(const Handle* h, s7_dtype dt) {
     const int v = h->keep_true ? (dt == S7_F64 ? 2 : 4) : VEC;
-    return s7_nblocks(make_geom(h, v));
+    return std::max(s7_nblocks(make_geom(h, v)), s7_nblocks(make_geom(h, 4)));
   }
 
   static int cast(const void* src, s7_dtype sdt, void* dst, s7_dtype ddt, long long n, cudaStream_t st) {
