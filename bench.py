@@ -109,6 +109,8 @@ def parse():
     ap.add_argument("--no-speedup", action="store_true", help="default line without the speedup")
     ap.add_argument("--no-refined", action="store_true",
                     help="default line without the 512^3 refined solves")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="default line without the 512-system batched solve")
     ap.add_argument("--cpu-all-nz", type=int, default=12,
                     help="z planes of each slab of the all-core oracle baseline")
     ap.add_argument("--serve-storage", default="bf16", choices=["bf16", "f16"],
@@ -528,9 +530,9 @@ def run_ours(args):
 def run_extras(args):
     """The rest of the headline metric, measured after the main line in the
     same run: the served request stream (p50/p99 latency), the served
-    mixed-precision form against the plain FP32 form to 1e-8, and 512^3
-    refined solves with their solution error.  A failure in one of them is
-    reported in its object; the main line stands."""
+    mixed-precision form against the plain FP32 form to 1e-8, 512^3 refined
+    solves with their solution error, and the 512-system batched solve.  A
+    failure in one of them is reported in its object; the main line stands."""
     import torch
     out = {}
     blocks = []
@@ -540,6 +542,9 @@ def run_extras(args):
         blocks.append(("speedup", lambda: {s: speedup_block(args, s) for s in ("bf16", "f16")}))
     if not args.no_refined:
         blocks.append(("refined", lambda: refined_block(args)))
+    if not args.no_batched:
+        blocks.append(("batched", lambda: batched_block(args, systems=512, steps=3, variant=0,
+                                                        schedule=0)))
     for name, fn in blocks:
         t0 = time.perf_counter()
         try:
@@ -707,31 +712,39 @@ def _timed(fn, steps, warmup):
     return ev0.elapsed_time(ev1) / steps, outs
 
 
-def run_batched(args):
-    """512 systems, cube edges log-uniform in [16,128] (seed 1), FP32, tol 1e-6."""
+def batched_block(args, systems=None, steps=None, variant=None, schedule=None):
+    """512 systems, cube edges log-uniform in [16,128] (seed 1), per-system
+    coefficients of the variable-coefficient recipe, FP32, tol 1e-6: one
+    batched solve (the persistent launch by default), timed over `steps`
+    repetitions, against the same systems solved one after another.
+    Systems are generated on the device (the host generator's coefficients,
+    bit for bit)."""
     import torch
     import synth
+    from synth import device as sd
     import paper_2010_03660_gb300 as s7
-    s7.lib()
-    dev = torch.device("cuda:0")
-    edges = synth.batched_edges(args.systems, seed=1)
+    systems = args.systems if systems is None else systems
+    steps = max(1, args.steps if steps is None else steps)
+    variant = args.variant if variant is None else variant
+    schedule = args.schedule if schedule is None else schedule
+    dev = torch.device("cuda", torch.cuda.current_device())
+    edges = synth.batched_edges(systems, seed=1)
     ops, bs = [], []
     for j, e in enumerate(edges):
-        p = synth.varcoef(e, e, e, seed=synth.system_seed(1, j))
-        ops.append(s7.stencil7_create(e, e, e, {k: torch.from_numpy(v).to(dev)
-                                                for k, v in p.coef.items()}, storage="f32",
-                                      variant=args.variant))
-        bs.append(torch.from_numpy(p.b).to(dev))
+        coef, b = sd.varcoef(e, e, e, synth.system_seed(1, j), dev, b_dtype="f32")
+        torch.cuda.synchronize()   # the library reads the inputs on its own stream
+        ops.append(s7.stencil7_create(e, e, e, coef, storage="f32", variant=variant))
+        bs.append(b)
+        del coef
     cells = [e ** 3 for e in edges]
     xs = [torch.zeros_like(b) for b in bs]
 
     def fn():
         for x in xs:
             x.zero_()
-        return s7.bicgstab_solve_batched(ops, bs, xs, tol=1e-6, maxit=2000,
-                                         schedule=args.schedule, threads=args.bthreads,
-                                         zchunk=args.bzchunk)
-    ms, outs = _timed(fn, args.steps, max(1, args.warmup))
+        return s7.bicgstab_solve_batched(ops, bs, xs, tol=1e-6, maxit=2000, schedule=schedule,
+                                         threads=args.bthreads, zchunk=args.bzchunk)
+    ms, outs = _timed(fn, steps, 1)
     r = outs[-1]
     ci = sum(c * it for c, it in zip(cells, r.iters))
     # the same systems one after another through bicgstab_solve
@@ -744,19 +757,30 @@ def run_batched(args):
         seq_ci += c * rs.iters
     torch.cuda.synchronize()
     seq_s = time.perf_counter() - t0
-    out = {"metric": "batched cell-iters/s (512 systems, edges 16..128, FP32, tol 1e-6)",
-           "value": ci / (ms / 1e3), "unit": "cell-iters/s", "higher_is_better": True,
-           "workload": "batched_%d%s" % (args.systems, "_merged" if args.variant else ""),
-           "schedule": {0: "chosen", 1: "persistent", -1: "launch per kernel"}[args.schedule],
-           "variant": "two reductions per step" if args.variant else "Algorithm 1",
-           "dtype": "f32", "data": "synthetic (seed 1)",
-           "ms_per_batch_solve": ms, "systems": len(ops), "total_cells": int(sum(cells)),
-           "iters_min_max": [min(r.iters), max(r.iters)], "all_converged": r.rc == 0,
-           "hbm_gbs": 116 * ci / (ms / 1e3) / 1e9,
+    out = {"workload": "batched_%d_systems%s" % (systems, "_two_reductions" if variant else ""),
+           "value": ci / (ms / 1e3), "unit": "cell-iters/s",
+           "schedule": {0: "chosen (persistent)", 1: "persistent", -1: "launch per kernel"}[schedule],
+           "variant": "two reductions per step" if variant else "Algorithm 1",
+           "dtype": "f32", "ms_per_batch_solve": ms, "systems": len(ops),
+           "total_cells": int(sum(cells)), "iters_min_max": [min(r.iters), max(r.iters)],
+           "all_converged": r.rc == 0, "hbm_gbs": 116 * ci / (ms / 1e3) / 1e9,
            "sequential_single_solves": {"s": seq_s, "cell_iters_per_s": seq_ci / seq_s},
-           "speedup_vs_sequential": (seq_s * 1e3) / ms, "steps": args.steps}
+           "speedup_vs_sequential": (seq_s * 1e3) / ms, "repetitions": steps}
     for op in ops:
         op.close()
+    del bs, xs
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_batched(args):
+    import torch
+    import paper_2010_03660_gb300 as s7
+    s7.lib()
+    torch.cuda.set_device(0)
+    out = batched_block(args)
+    out.update({"metric": "batched cell-iters/s (512 systems, edges 16..128, FP32, tol 1e-6)",
+                "higher_is_better": True, "data": "synthetic (seed 1)"})
     print(json.dumps(out))
 
 
@@ -998,6 +1022,7 @@ def refined_block(args, edge=None, storages=("bf16", "f16"), reps=3):
     n = e ** 3
     dev = torch.device("cuda", torch.cuda.current_device())
     coef, b = sd.varcoef(e, e, e, 2, dev)
+    torch.cuda.synchronize()       # the library reads the inputs on its own stream
     # the manufactured system, on the host, by the oracle
     t0 = time.perf_counter()
     ph = synth.varcoef(e, e, e, seed=2)
