@@ -25,8 +25,11 @@
 // stage k, then __syncthreads() makes all of stage k and the vector plane z
 // (produced at step k-1) visible; it then refills the stage buffer that
 // held stage k-1 (fully consumed before the barrier), forms plane z+1 into
-// the 3-buffer vector ring, and computes plane z from the ring buffer
-// written at step k-1.
+// one buffer of a 2-buffer vector ring, and computes plane z from the other
+// (written at step k-1).  Two buffers suffice because plane z+1 is written
+// after the barrier: the buffer it overwrites held plane z-1, which every
+// thread finished reading at step k-1 (the plane z-1 values a thread keeps
+// for its own cells live in registers).
 //
 // Staging engine.  With tensor maps of the handle's arrays (StepArgs::maps,
 // a kernel parameter of the single-system sweeps), the first warp stages
@@ -266,12 +269,12 @@ template <class T, class A, int KIND> struct RingOf {
   typedef T t;
 };
 
-// Dynamic shared memory of a block: the stages, the 3-plane ring of the
+// Dynamic shared memory of a block: the stages, the 2-plane ring of the
 // on-the-fly vector, and 128 bytes to align the start.
 template <class T, class A, int VEC, int KIND>
 __host__ __device__ inline size_t kind_smem_bytes(int bx, int by, int stages) {
   const StepLayout<T, VEC> L = kind_layout<T, VEC, KIND>(bx, by);
-  const size_t ring = (size_t)3 * L.rows * L.W * sizeof(typename RingOf<T, A, KIND>::t);
+  const size_t ring = (size_t)2 * L.rows * L.W * sizeof(typename RingOf<T, A, KIND>::t);
   return (size_t)stages * kind_stride_bytes<T, VEC, KIND>(L) + ring + 128;
 }
 
@@ -576,7 +579,7 @@ __device__ __forceinline__ void step_body(const Geom& g, const StepArgs<T>& a, S
     const T* st = stage_buf(k % STAGES);
     const T* inb = st + L.coef_sz + L.rh_sz;
     // form plane z+1: own cells (+ ring if the next step needs it)
-    R* nb = ring + ((k + 1) % 3) * RPL;
+    R* nb = ring + ((k + 1) & 1) * RPL;
     if (z + 1 < g.nz) {
       const bool ring_needed = z + 1 < z1;
       if (has_cell) {
@@ -629,7 +632,7 @@ __device__ __forceinline__ void step_body(const Geom& g, const StepArgs<T>& a, S
     }
     // stencil on plane z
     if (own) {
-      const R* cb = ring + (k % 3) * RPL;
+      const R* cb = ring + (k & 1) * RPL;
       A up[VEC], dn[VEC], c[6][VEC];
       ldv<R, VEC>(cb + so - L.W, up);
       ldv<R, VEC>(cb + so + L.W, dn);
