@@ -97,7 +97,11 @@ def parse():
                     help="batched: threads per block (0 = autotuned)")
     ap.add_argument("--bzchunk", type=int, default=0, help="batched: z planes per block (0 = autotuned)")
     ap.add_argument("--schedule", type=int, default=0,
-                    help="batched: 0 chosen, 1 one persistent launch, -1 one launch per kernel")
+                    help="batched: 0 chosen by the autotuner, 1 one persistent launch, -1 one "
+                         "launch per kernel")
+    ap.add_argument("--bfixed-variant", action="store_true",
+                    help="batched: run the handles' variant (default: the autotuner may pick "
+                         "the other one)")
     ap.add_argument("--requests", type=int, default=20000, help="serve: requests in the stream")
     ap.add_argument("--rate", type=float, default=40.0, help="serve: arrivals per second")
     ap.add_argument("--serve-deadline", type=float, default=540.0,
@@ -168,7 +172,7 @@ def measured_peaks():
 # the sources that define the profiled step kernels (their device code and
 # launch configuration); host-side drivers and tile defaults are not included
 KERNEL_SOURCES = ("s7_common.cuh", "s7_sweep.cuh", "s7_sweep9.cuh", "s7_step.cuh",
-                  "s7_engine.cuh", "s7_batch.cuh")
+                  "s7_engine.cuh", "s7_batch.cuh", "s7_resid.cuh")
 
 
 def kernel_source_hash():
@@ -715,7 +719,8 @@ def _timed(fn, steps, warmup):
 def batched_block(args, systems=None, steps=None, variant=None, schedule=None):
     """512 systems, cube edges log-uniform in [16,128] (seed 1), per-system
     coefficients of the variable-coefficient recipe, FP32, tol 1e-6: one
-    batched solve (the persistent launch by default), timed over `steps`
+    batched solve (block shape and fusion schedule chosen by the library's
+    autotuner on the untimed first solve), timed over `steps`
     repetitions, against the same systems solved one after another.
     Systems are generated on the device (the host generator's coefficients,
     bit for bit)."""
@@ -743,7 +748,8 @@ def batched_block(args, systems=None, steps=None, variant=None, schedule=None):
         for x in xs:
             x.zero_()
         return s7.bicgstab_solve_batched(ops, bs, xs, tol=1e-6, maxit=2000, schedule=schedule,
-                                         threads=args.bthreads, zchunk=args.bzchunk)
+                                         threads=args.bthreads, zchunk=args.bzchunk,
+                                         choose_variant=not args.bfixed_variant)
     ms, outs = _timed(fn, steps, 1)
     r = outs[-1]
     ci = sum(c * it for c, it in zip(cells, r.iters))
@@ -757,10 +763,14 @@ def batched_block(args, systems=None, steps=None, variant=None, schedule=None):
         seq_ci += c * rs.iters
     torch.cuda.synchronize()
     seq_s = time.perf_counter() - t0
-    out = {"workload": "batched_%d_systems%s" % (systems, "_two_reductions" if variant else ""),
+    pol = r.policy
+    out = {"workload": "batched_%d_systems" % systems,
            "value": ci / (ms / 1e3), "unit": "cell-iters/s",
-           "schedule": {0: "chosen (persistent)", 1: "persistent", -1: "launch per kernel"}[schedule],
-           "variant": "two reductions per step" if variant else "Algorithm 1",
+           "schedule": {1: "persistent", -1: "launch per kernel"}[pol["schedule"]]
+           + (" (chosen by the autotuner)" if schedule == 0 else ""),
+           "variant": "two reductions per step" if pol["variant"] else "Algorithm 1",
+           "policy": dict(pol, variant_chosen_by_autotuner=not args.bfixed_variant,
+                          handles_variant=variant),
            "dtype": "f32", "ms_per_batch_solve": ms, "systems": len(ops),
            "total_cells": int(sum(cells)), "iters_min_max": [min(r.iters), max(r.iters)],
            "all_converged": r.rc == 0, "hbm_gbs": 116 * ci / (ms / 1e3) / 1e9,

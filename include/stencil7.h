@@ -310,12 +310,19 @@ typedef struct {
                        system from per-system work queues, a system's next
                        phase opening when its previous one completes;
                        -1: one launch per step kernel, replayed from a
-                       graph; 0: chosen (the persistent launch)             */
+                       graph; 0: chosen by the autotuner when it runs,
+                       else the persistent launch (one launch per kernel
+                       where no block of it fits)                           */
   long long wait_cycles;  /* the persistent launch: longest wait of a block
                        for an open tile, in SM clock cycles; 0 = 2^31
                        (about a second).  A wait that runs out aborts the
                        launch: every unfinished system stops with
                        S7_ETIMEOUT.                                         */
+  int choose_variant;  /* 1: the autotuner also times the other variant of
+                       the step (Algorithm 1's three sweeps or the
+                       two-reduction variant's two) and runs the faster;
+                       the result then follows that variant's recurrences.
+                       0: the handles' variant.                             */
 } s7_batch_opts;
 
 /* Solve nsys independent systems together (BiCGStab, Algorithm 1, on each;
@@ -332,15 +339,31 @@ typedef struct {
  *   tol[j], maxit[j]  per-system stopping rule (as in bicgstab_solve).
  *   iters[j], status[j], resid[j]  out (each array may be NULL): steps taken,
  *             S7_OK / S7_ENOTCONV / S7_EBREAKDOWN, final recurrence residual.
- * Block shape and z chunk are picked by a built-in autotuner that times
- * candidates with a batched SpMV over the batch's own operators (no change
- * to the solve) and caches the winner per batch signature.  Synchronous.
- * Returns S7_OK if every system converged, else S7_EBREAKDOWN if any broke
+ * Unless opts fixes the block shape (threads, zchunk or no_autotune), a
+ * built-in autotuner picks the policy on the first solve of each batch
+ * signature (storage, systems, total cells, options) and caches it: first the
+ * block shape and z chunk, timed with a batched SpMV over the batch's own
+ * operators; then the fusion schedule, timed over 8 steps of the solve
+ * itself from x0 with tolerance 0 (x is restored before the solve): the
+ * persistent launch or one launch per step kernel, the pipelined step
+ * sweeps (wide vectors, when every row is whole vectors) or the register
+ * sweeps, and with opts.choose_variant the other variant.  Choices other
+ * than the variant change only the summation order of the inner products.
+ * Synchronous.  Returns S7_OK if every system converged, else S7_ETIMEOUT if
+ * a wait of the persistent launch ran out, else S7_EBREAKDOWN if any broke
  * down, else S7_ENOTCONV. */
 int bicgstab_solve_batched(int nsys, const stencil7_t* hs, const void* const* b,
                            void* const* x, s7_dtype dt, const double* tol,
                            const int* maxit, int* iters, int* status, double* resid,
                            const s7_batch_opts* opts, void* stream);
+
+/* The policy the calling thread's last bicgstab_solve_batched ran with: block
+ * threads, z chunk, schedule (1 persistent, -1 launch per kernel), pipelined
+ * (1: pipelined step sweeps, 0: register sweeps) and variant (0: Algorithm 1,
+ * 1: two-reduction).  Each pointer may be NULL.  S7_EINVAL if this thread has
+ * run no batched solve. */
+int bicgstab_batched_policy(int* threads, int* zchunk, int* schedule, int* pipelined,
+                            int* variant);
 
 /* ---- serving: continuous batching of solve requests ----
  *

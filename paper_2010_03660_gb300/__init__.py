@@ -30,7 +30,8 @@ __all__ = [
     "S7_F64", "S7_F32", "S7_BF16", "S7_F16", "S7Error", "Operator", "lib", "EXPORTS",
     "stencil7_create", "stencil9_create", "stencil7_destroy", "stencil7_info", "stencil7_apply",
     "stencil7_residual", "stencil7_residual_noalloc", "bicgstab_solve",
-    "bicgstab_solve_refined", "bicgstab_solve_batched", "stencil7_profile", "s7_last_error",
+    "bicgstab_solve_refined", "bicgstab_solve_batched", "bicgstab_batched_policy",
+    "stencil7_profile", "s7_last_error",
     "s7_version", "Server", "s7_server_create", "s7_server_submit", "s7_server_poll",
     "s7_server_wait", "s7_server_release", "s7_server_get_stats", "s7_server_destroy",
     "s7_mem_stats", "s7_mem_trim", "s7_mem_set_cache",
@@ -49,7 +50,8 @@ _STORAGE = {"f64": S7_F64, "f32": S7_F32, "bf16": S7_BF16, "f16": S7_F16}
 EXPORTS = (
     "stencil7_create", "stencil9_create", "stencil7_destroy", "stencil7_info", "stencil7_apply",
     "stencil7_residual", "stencil7_residual_noalloc", "bicgstab_solve",
-    "bicgstab_solve_refined", "bicgstab_solve_batched", "stencil7_profile", "s7_last_error",
+    "bicgstab_solve_refined", "bicgstab_solve_batched", "bicgstab_batched_policy",
+    "stencil7_profile", "s7_last_error",
     "s7_version", "s7_server_create", "s7_server_submit", "s7_server_poll", "s7_server_wait",
     "s7_server_release", "s7_server_get_stats", "s7_server_destroy", "s7_mem_stats",
     "s7_mem_trim", "s7_mem_set_cache",
@@ -85,7 +87,8 @@ class s7_opts(C.Structure):
 
 class s7_batch_opts(C.Structure):
     _fields_ = [("threads", C.c_int), ("zchunk", C.c_int), ("check_every", C.c_int),
-                ("no_autotune", C.c_int), ("schedule", C.c_int), ("wait_cycles", C.c_longlong)]
+                ("no_autotune", C.c_int), ("schedule", C.c_int), ("wait_cycles", C.c_longlong),
+                ("choose_variant", C.c_int)]
 
 
 class s7_server_opts(C.Structure):
@@ -144,6 +147,7 @@ def lib():
         "stencil7_profile": (i, [vp, i, P(d), P(C.c_longlong)]),
         "bicgstab_solve_batched": (i, [i, P(vp), P(vp), P(vp), i, P(d), P(i), P(i), P(i), P(d),
                                        P(s7_batch_opts), vp]),
+        "bicgstab_batched_policy": (i, [P(i), P(i), P(i), P(i), P(i)]),
         "s7_server_create": (i, [P(vp), P(s7_server_opts)]),
         "s7_server_submit": (i, [vp, P(s7_request), P(C.c_uint64)]),
         "s7_server_poll": (i, [vp, C.c_uint64, P(s7_result)]),
@@ -220,6 +224,24 @@ def _stream(*bufs):
 
 def _numel(a):
     return a.numel() if _is_torch(a) else np.asarray(a).size
+
+
+def _vectors(what, n, first, *others, dtype=None):
+    """Check the vectors of one call: the C entry points take a single
+    element type for all of them and no sizes, so a buffer of another type
+    would be read as the wrong type and a short one past its end.  Returns
+    the common type code."""
+    code = _dtype_code(first)
+    if dtype is not None and code != dtype:
+        raise ValueError("%s: vectors must be float64" % what)
+    for a in (first,) + others:
+        if a is None:
+            continue
+        if _dtype_code(a) != code:
+            raise ValueError("%s: all vectors must have the same dtype" % what)
+        if _numel(a) != n:
+            raise ValueError("%s: a vector has %d elements, the operator %d" % (what, _numel(a), n))
+    return code
 
 
 def _empty_like(a, dtype_code=None):
@@ -369,14 +391,16 @@ def stencil7_apply(op, x, y=None):
     """``y = A~ x`` with the stored operator; returns y."""
     if y is None:
         y = _empty_like(x)
-    _check(lib().stencil7_apply(op.handle, _ptr(x), _ptr(y), _dtype_code(x), _stream(x, y)))
+    dt = _vectors("stencil7_apply", op.n, x, y)
+    _check(lib().stencil7_apply(op.handle, _ptr(x), _ptr(y), dt, _stream(x, y)))
     return y
 
 
 def stencil7_residual(op, b, x, r=None):
     """``r = b - A x`` on the raw system; returns ``(rnorm, bnorm)``."""
     rn, bn = C.c_double(), C.c_double()
-    _check(lib().stencil7_residual(op.handle, _ptr(b), _ptr(x), _ptr(r), _dtype_code(b),
+    dt = _vectors("stencil7_residual", op.n, b, x, r)
+    _check(lib().stencil7_residual(op.handle, _ptr(b), _ptr(x), _ptr(r), dt,
                                    C.byref(rn), C.byref(bn), _stream(b, x, r)))
     return rn.value, bn.value
 
@@ -411,7 +435,8 @@ def stencil7_residual_noalloc(op, b, x, r=None):
     """:func:`stencil7_residual` without any allocation (device buffers only);
     for callers that may not allocate device memory at call time."""
     rn, bn = C.c_double(), C.c_double()
-    _check(lib().stencil7_residual_noalloc(op.handle, _ptr(b), _ptr(x), _ptr(r), _dtype_code(b),
+    dt = _vectors("stencil7_residual_noalloc", op.n, b, x, r)
+    _check(lib().stencil7_residual_noalloc(op.handle, _ptr(b), _ptr(x), _ptr(r), dt,
                                            C.byref(rn), C.byref(bn), _stream(b, x, r)))
     return rn.value, bn.value
 
@@ -437,10 +462,11 @@ def bicgstab_solve(op, b, x=None, tol=1e-6, maxit=500, history=True, true_resid=
             x.zero_()
         else:
             x[...] = 0
+    dt = _vectors("bicgstab_solve", op.n, b, x)
     it = C.c_int()
     hist = np.zeros(maxit + 1) if history else None
     tr = C.c_double()
-    rc = lib().bicgstab_solve(op.handle, _ptr(b), _ptr(x), _dtype_code(b), float(tol),
+    rc = lib().bicgstab_solve(op.handle, _ptr(b), _ptr(x), dt, float(tol),
                               int(maxit), C.byref(it),
                               hist.ctypes.data_as(C.POINTER(C.c_double)) if history else None,
                               C.byref(tr) if true_resid else None, _stream(b, x))
@@ -467,6 +493,7 @@ def bicgstab_solve_refined(op, b, x=None, tol=1e-10, max_outer=30, inner_maxit=2
             x.zero_()
         else:
             x[...] = 0
+    _vectors("bicgstab_solve_refined", op.n, b, x, dtype=S7_F64)
     outer, inner = C.c_int(), C.c_int()
     hist = np.zeros(max_outer + 1)
     rc = lib().bicgstab_solve_refined(op.handle, _ptr(b), _ptr(x), float(tol), int(max_outer),
@@ -484,11 +511,12 @@ class BatchResult:
     status: list
     resid: list
     rc: int
+    policy: dict = None
 
 
 def bicgstab_solve_batched(ops, bs, xs=None, tol=1e-6, maxit=500, threads=0, zchunk=0,
                            check_every=0, autotune=True, schedule=0, wait_cycles=0,
-                           allow_timeout=False):
+                           allow_timeout=False, choose_variant=False):
     """Solve independent systems together (one persistent launch, or one
     launch per step kernel, covers all).
 
@@ -498,7 +526,9 @@ def bicgstab_solve_batched(ops, bs, xs=None, tol=1e-6, maxit=500, threads=0, zch
     ``schedule``: 0 chosen, 1 persistent, -1 one launch per step kernel;
     ``wait_cycles``: bound of the persistent launch's barrier waits (0 =
     default).  With ``allow_timeout`` an S7_ETIMEOUT return is reported in
-    the result instead of raised.
+    the result instead of raised.  ``choose_variant``: the autotuner may run
+    the other variant of the step.  ``policy`` of the result: the block
+    shape and fusion schedule the solve ran with (:func:`bicgstab_batched_policy`).
     """
     n = len(ops)
     if xs is None:
@@ -510,6 +540,12 @@ def bicgstab_solve_batched(ops, bs, xs=None, tol=1e-6, maxit=500, threads=0, zch
             else:
                 x[...] = 0
             xs.append(x)
+    if len(bs) != n or len(xs) != n:
+        raise ValueError("bicgstab_solve_batched: one b and one x per operator")
+    dt = _dtype_code(bs[0])
+    for op, b, x in zip(ops, bs, xs):
+        if _vectors("bicgstab_solve_batched", op.n, b, x) != dt:
+            raise ValueError("bicgstab_solve_batched: all vectors must have the same dtype")
     tols = [float(tol)] * n if np.isscalar(tol) else [float(t) for t in tol]
     mits = [int(maxit)] * n if np.isscalar(maxit) else [int(m) for m in maxit]
     H = (C.c_void_p * n)(*[op.handle.value for op in ops])
@@ -521,11 +557,22 @@ def bicgstab_solve_batched(ops, bs, xs=None, tol=1e-6, maxit=500, threads=0, zch
     stt = (C.c_int * n)()
     rs = (C.c_double * n)()
     o = s7_batch_opts(threads, zchunk, check_every, 0 if autotune else 1, int(schedule),
-                      int(wait_cycles))
-    rc = lib().bicgstab_solve_batched(n, H, B, X, _dtype_code(bs[0]), T, M, it, stt, rs,
+                      int(wait_cycles), int(bool(choose_variant)))
+    rc = lib().bicgstab_solve_batched(n, H, B, X, dt, T, M, it, stt, rs,
                                       C.byref(o), _stream(*bs))
     _check(rc, allow=(EBREAKDOWN, ENOTCONV) + ((ETIMEOUT,) if allow_timeout else ()))
-    return BatchResult(xs, list(it), list(stt), list(rs), rc)
+    return BatchResult(xs, list(it), list(stt), list(rs), rc, bicgstab_batched_policy())
+
+
+def bicgstab_batched_policy():
+    """Block shape and fusion schedule of this thread's last batched solve:
+    ``threads``, ``zchunk``, ``schedule`` (1 persistent, -1 launch per step
+    kernel), ``pipelined`` (pipelined step sweeps or register sweeps),
+    ``variant`` (0 Algorithm 1, 1 two-reduction)."""
+    v = [C.c_int() for _ in range(5)]
+    _check(lib().bicgstab_batched_policy(*[C.byref(a) for a in v]))
+    return dict(zip(("threads", "zchunk", "schedule", "pipelined", "variant"),
+                    [a.value for a in v]))
 
 
 def _result_dict(r):
@@ -553,7 +600,8 @@ def s7_server_submit(srv, nx, ny, nz, coef, b, x, tol):
     raw_dt = _dtype_code(coef["diag"])
     constant = 1 if nx * ny * nz > 1 and all(_numel(coef[k]) == 1 for k in names) else 0
     cs = s7_coeffs(*[_ptr(coef[k]) for k in names], raw_dt, constant)
-    req = s7_request(nx, ny, nz, cs, _ptr(b), _ptr(x), _dtype_code(b), float(tol))
+    dt = _vectors("s7_server_submit", nx * ny * nz, b, x)
+    req = s7_request(nx, ny, nz, cs, _ptr(b), _ptr(x), dt, float(tol))
     rid = C.c_uint64()
     _check(lib().s7_server_submit(srv, C.byref(req), C.byref(rid)))
     return rid.value

@@ -478,9 +478,11 @@ extern "C" int stencil7_create(stencil7_t* out, int nx, int ny, int nz, const s7
     int ce = (int)std::min(64.0, std::max(2.0, 1000.0 / est_us));
     h->check_every = opts.check_every > 0 ? opts.check_every : ce;
   }
-  // Defaults measured on GB300.  float32/float64 (600x595 planes): a
-  // 2-stage pipeline helps the p/s sweep, whose register version is limited
-  // by occupancy, and not the q/y sweep.  16-bit storage (512^2 planes):
+  // Defaults measured on GB300.  float32 (600x595 planes): a 2-stage
+  // pipeline for both sweeps (the q/y sweep 2.91 ms pipelined against 3.18 ms
+  // in registers at 600x595x1536, once the on-the-fly vector's ring held two
+  // planes); float64: the p/s sweep only, whose register version is limited
+  // by occupancy.  16-bit storage (512^2 planes):
   // both sweeps are bound by instruction issue at half the bytes per cell;
   // 8 cells (one 16-byte copy per array) per thread halve the per-cell
   // overhead, and both sweeps take a 2-stage pipeline (1.57 vs 1.84 ms per
@@ -494,7 +496,7 @@ extern "C" int stencil7_create(stencil7_t* out, int nx, int ny, int nz, const s7
   }
   const bool half = opts.storage == S7_BF16 || opts.storage == S7_F16;
   const int def_stages = 2;
-  const int def_kinds = (opts.variant == 1 || half) ? 3 : 1;
+  const int def_kinds = (opts.variant == 1 || half || opts.storage == S7_F32) ? 3 : 1;
   h->stages = opts.stages > 0 ? std::min(opts.stages, 4) : def_stages;
   h->pipe_kinds = opts.pipe_kinds > 0 ? (opts.pipe_kinds & 3) : def_kinds;
   if (opts.step_cells != 0 && opts.step_cells != eng->vec && !(half && opts.step_cells == 8)) {
@@ -1318,12 +1320,20 @@ namespace {
 struct BatchPolicy {
   int threads;
   int zchunk;
+  int sched;   // 1: one persistent launch; -1: one launch per step kernel
+  int pipe;    // the pipelined step sweeps (wide vectors), else the register sweeps
+  int merged;  // the two-reduction variant
 };
 
 // Autotuned policies by batch signature (storage, systems, log2 cells,
-// pipelined).
-std::map<std::tuple<int, int, int, int>, BatchPolicy> g_policy;
+// pipelined sweeps possible, the handles' variant, variant chosen, schedule
+// asked for).
+std::map<std::tuple<int, int, int, int, int, int, int>, BatchPolicy> g_policy;
 std::mutex g_policy_mu;
+// the policy of the calling thread's last batched solve
+thread_local BatchPolicy t_last_policy{0, 0, 0, 0, 0};
+// steps a system in each timing trial of a fusion schedule
+constexpr int kScheduleTrialSteps = 8;
 
 Tile batch_tile(const Handle* h, int vec, const BatchPolicy& p) {
   const int runs = (h->nx + vec - 1) / vec;
@@ -1345,6 +1355,7 @@ struct BatchBuffers {
   double* parts = nullptr;
   void* desc = nullptr;
   std::vector<unsigned char> h_desc;
+  int upd_blocks = 0;  // blocks of the update launch (launch per kernel)
   ~BatchBuffers() {
     dev_free(sc, nullptr);
     pinned_put(h_sc);
@@ -1361,13 +1372,10 @@ struct BatchBuffers {
 // engine's wide vector).
 static int batch_layout(int nsys, Handle* const* hs, const void* const* bdev, const Engine* eng,
                         const BatchPolicy& p, BatchBuffers& bb, const std::vector<size_t>& hist_off,
-                        const std::vector<size_t>& parts_off, int* sweep_blocks, int* upd_blocks,
-                        size_t smem[8], int pipe, cudaStream_t st,
-                        std::vector<int>* nbs = nullptr, std::vector<int>* ubs = nullptr) {
+                        const std::vector<size_t>& parts_off, int* sweep_blocks, size_t smem[8],
+                        int pipe, cudaStream_t st) {
   int b0 = 0, u0 = 0;
   for (int k = 0; k < 8; ++k) smem[k] = 0;
-  if (nbs) nbs->assign(nsys, 0);
-  if (ubs) ubs->assign(nsys, 0);
   for (int j = 0; j < nsys; ++j) {
     const Tile t = batch_tile(hs[j], pipe ? eng->vec_wide : eng->vec, p);
     int nb = 0, ub = 0;
@@ -1376,16 +1384,193 @@ static int batch_layout(int nsys, Handle* const* hs, const void* const* bdev, co
                    pipe);
     b0 += nb;
     u0 += ub;
-    if (nbs) (*nbs)[j] = nb;
-    if (ubs) (*ubs)[j] = ub;
     for (int k = 0; k < 8; ++k)
       if (k != 4 && k != 5) smem[k] = std::max(smem[k], eng->batched_smem(hs[j], t, pipe, k));
   }
   *sweep_blocks = b0;
-  *upd_blocks = u0;
+  bb.upd_blocks = u0;
   CK(cudaMemcpyAsync(bb.desc, bb.h_desc.data(), (size_t)nsys * eng->desc_size,
                      cudaMemcpyHostToDevice, st));
   return S7_OK;
+}
+
+// x0 of every system into its workspace (again after the autotuner's trial
+// runs, which advance x).
+static int stage_x0(int nsys, Handle* const* hs, void* const* x, s7_dtype dt, s7_dtype xt,
+                    const Engine* eng, cudaStream_t st) {
+  for (int j = 0; j < nsys; ++j) {
+    Handle* h = hs[j];
+    const void* xin = nullptr;
+    int rc = stage_in(h, x[j], dt, xt, h->ws.x, &xin, st);
+    if (rc) return rc;
+    if (xin != h->ws.x) {
+      const cudaError_t e =
+          cudaMemcpyAsync(h->ws.x, xin, (size_t)h->n * eng->x_size, cudaMemcpyDeviceToDevice, st);
+      if (e != cudaSuccess) return cuda_fail(e, "x0 copy");
+    }
+  }
+  return S7_OK;
+}
+
+// What one run of a laid-out batch needs.
+struct BatchRun {
+  int nsys;
+  Handle* const* hs;
+  const Engine* eng;
+  BatchBuffers* bb;
+  const double* tol;
+  const int* maxit;
+  int sweep_blocks, threads;
+  const size_t* smem;  // dynamic shared memory by launch kind (8 kinds)
+  int pipe, merged;    // pipelined step sweeps; the two-reduction variant
+  int ce;              // steps per graph launch (launch per kernel)
+  long long budget;    // wait budget of the persistent launch, SM cycles
+  cudaStream_t st;
+};
+
+// One run of a laid-out batch from the staged x0: per-system scalars, the
+// start sweeps, then the steps in one persistent launch (persistent = 1) or
+// as one launch per step kernel replayed from a captured graph.  On return
+// the host copy of the scalars holds every system's final state.  trial > 0:
+// a timing run of at most `trial` steps a system with tolerance 0, *ms the
+// device time of its steps.
+static int batch_run(const BatchRun& R, int persistent, int trial, float* ms) {
+  const int nsys = R.nsys;
+  const Engine* eng = R.eng;
+  BatchBuffers& bb = *R.bb;
+  const cudaStream_t st = R.st;
+  const int pipe = R.pipe, merged = R.merged, threads = R.threads;
+  const size_t* smem = R.smem;
+  const size_t psm = merged ? std::max(smem[6], smem[7]) : std::max(smem[0], smem[1]);
+  int rc = S7_OK;
+  cudaError_t e = cudaSuccess;
+  cudaGraphExec_t gexec = nullptr;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  void* d_queue = nullptr;
+  void* d_qstate = nullptr;
+  int* d_order = nullptr;
+  int pgrid = 0, mx = 0;
+  for (int j = 0; j < nsys; ++j) {
+    Scalars& s = bb.h_sc[j];
+    memset(&s, 0, sizeof s);
+    s.tol = trial ? 0.0 : R.tol[j];
+    s.maxit = trial ? std::min(trial, R.maxit[j]) : R.maxit[j];
+    s.status = S7_ENOTCONV;
+    mx = std::max(mx, s.maxit);
+  }
+  if (persistent) {
+    // as many blocks as are resident on the device at once
+    int per_sm = 0;
+    if (eng->persistent_occupancy(threads, psm, pipe, merged, &per_sm) == S7_OK && per_sm > 0)
+      pgrid = per_sm * num_sms();
+    if (!pgrid) return fail(S7_EINVAL, "bicgstab_solve_batched: no block of the persistent launch fits");
+  }
+  if (ms && ((e = cudaEventCreate(&ev[0])) != cudaSuccess ||
+             (e = cudaEventCreate(&ev[1])) != cudaSuccess)) { rc = cuda_fail(e, "events"); goto out; }
+  if ((e = cudaMemcpyAsync(bb.sc, bb.h_sc, (size_t)nsys * sizeof(Scalars), cudaMemcpyHostToDevice, st)) != cudaSuccess) { rc = cuda_fail(e, "scalars"); goto out; }
+  if ((rc = eng->launch_batched(2, bb.desc, nsys, R.sweep_blocks, threads, smem[2], st, pipe)) ||
+      (rc = eng->launch_batched(5, bb.desc, nsys, 0, 0, 0, st, pipe)) ||
+      // the two-reduction variant starts with s_0 = A p_0 and (r0, s_0)
+      (merged && (rc = eng->launch_batched(0, bb.desc, nsys, R.sweep_blocks, threads, smem[0], st,
+                                           pipe)))) {
+    rc = fail(rc, "batched start launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+    goto out;
+  }
+  if (persistent) {
+    const int dev = R.hs[0]->device;
+    // blocks look for work in the largest systems first: they set the end
+    std::vector<int> order(nsys);
+    for (int j = 0; j < nsys; ++j) order[j] = j;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return R.hs[a]->n > R.hs[b]->n; });
+    if ((e = dev_alloc(dev, &d_queue, (size_t)nsys * kQueueBytes, st)) != cudaSuccess ||
+        (e = dev_alloc(dev, &d_qstate, kQueueStateBytes, st)) != cudaSuccess ||
+        (e = dev_alloc(dev, (void**)&d_order, (size_t)nsys * sizeof(int), st)) != cudaSuccess ||
+        (e = cudaMemsetAsync(d_qstate, 0, kQueueStateBytes, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(d_order, order.data(), (size_t)nsys * sizeof(int),
+                             cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess) {
+      rc = cuda_fail(e, "persistent batch queues");
+      goto out;
+    }
+    // captured as a graph of one launch; launched directly where the capture
+    // of a cooperative launch is refused
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      const int lrc = eng->launch_persistent(bb.desc, d_order, d_queue, d_qstate, nsys, pgrid,
+                                             threads, psm, R.budget, st, pipe, merged);
+      e = cudaStreamEndCapture(st, &g);
+      if (lrc != S7_OK || e != cudaSuccess || !g || cudaGraphInstantiate(&gexec, g, 0) != cudaSuccess)
+        gexec = nullptr;
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+    }
+    if (ms) cudaEventRecord(ev[0], st);
+    if (gexec) {
+      if ((e = cudaGraphLaunch(gexec, st)) != cudaSuccess) { rc = cuda_fail(e, "persistent graph launch"); goto out; }
+    } else if ((rc = eng->launch_persistent(bb.desc, d_order, d_queue, d_qstate, nsys, pgrid,
+                                            threads, psm, R.budget, st, pipe, merged))) {
+      rc = fail(rc, "persistent batched launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+      goto out;
+    }
+    if (ms) cudaEventRecord(ev[1], st);
+    if ((e = cudaMemcpyAsync(bb.h_sc, bb.sc, (size_t)nsys * sizeof(Scalars), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess) { rc = cuda_fail(e, "persistent batched solve"); goto out; }
+  } else {
+    // a trial runs all its steps in one graph launch
+    const int ce = trial ? std::max(1, mx) : R.ce;
+    cudaGraph_t g = nullptr;
+    if ((e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) { rc = cuda_fail(e, "capture"); goto out; }
+    for (int k = 0; k < ce && rc == S7_OK; ++k) {
+      if (merged) {
+        // q/y pass, then the x, r updates fused with the next step's p/s pass
+        rc = eng->launch_batched(6, bb.desc, nsys, R.sweep_blocks, threads, smem[6], st, pipe);
+        if (!rc) rc = eng->launch_batched(7, bb.desc, nsys, R.sweep_blocks, threads, smem[7], st, pipe);
+        continue;
+      }
+      rc = eng->launch_batched(0, bb.desc, nsys, R.sweep_blocks, threads, smem[0], st, pipe);
+      if (!rc) rc = eng->launch_batched(1, bb.desc, nsys, R.sweep_blocks, threads, smem[1], st, pipe);
+      if (!rc) rc = eng->launch_batched(4, bb.desc, nsys, bb.upd_blocks, 256, 0, st, pipe);
+    }
+    e = cudaStreamEndCapture(st, &g);
+    if (rc || e != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      rc = rc ? fail(rc, "batched capture: launch failed") : cuda_fail(e, "cudaStreamEndCapture");
+      goto out;
+    }
+    e = cudaGraphInstantiate(&gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) { gexec = nullptr; rc = cuda_fail(e, "cudaGraphInstantiate"); goto out; }
+    if (ms) {
+      cudaEventRecord(ev[0], st);
+      if ((e = cudaGraphLaunch(gexec, st)) != cudaSuccess) { rc = cuda_fail(e, "graph launch"); goto out; }
+      cudaEventRecord(ev[1], st);
+      if ((e = cudaMemcpyAsync(bb.h_sc, bb.sc, (size_t)nsys * sizeof(Scalars), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+          (e = cudaStreamSynchronize(st)) != cudaSuccess) { rc = cuda_fail(e, "batched trial"); goto out; }
+    } else {
+      const int max_launch = mx / ce + 3;
+      for (int launches = 0;; ++launches) {
+        if ((e = cudaMemcpyAsync(bb.h_sc, bb.sc, (size_t)nsys * sizeof(Scalars), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(st)) != cudaSuccess) { rc = cuda_fail(e, "batched poll"); goto out; }
+        bool all = true;
+        for (int j = 0; j < nsys && all; ++j) all = bb.h_sc[j].done != 0;
+        if (all) break;
+        if (launches >= max_launch) { rc = fail(S7_ECUDA, "batched solve did not terminate"); goto out; }
+        if ((e = cudaGraphLaunch(gexec, st)) != cudaSuccess) { rc = cuda_fail(e, "graph launch"); goto out; }
+      }
+    }
+  }
+  if (ms) cudaEventElapsedTime(ms, ev[0], ev[1]);
+out:
+  if (gexec) cudaGraphExecDestroy(gexec);
+  cudaStreamSynchronize(st);
+  dev_free(d_queue, st);
+  dev_free(d_qstate, st);
+  dev_free(d_order, st);
+  for (cudaEvent_t x : ev)
+    if (x) cudaEventDestroy(x);
+  return rc;
 }
 
 extern "C" int bicgstab_solve_batched(int nsys, const stencil7_t* hs_in, const void* const* b,
@@ -1399,6 +1584,8 @@ extern "C" int bicgstab_solve_batched(int nsys, const stencil7_t* hs_in, const v
   s7_batch_opts opts;
   memset(&opts, 0, sizeof opts);
   if (o) opts = *o;
+  if (opts.schedule < -1 || opts.schedule > 1)
+    return fail(S7_EINVAL, "bicgstab_solve_batched: schedule must be -1, 0 or 1");
   std::vector<Handle*> hs(nsys);
   for (int j = 0; j < nsys; ++j) {
     hs[j] = hs_in[j];
@@ -1416,38 +1603,34 @@ extern "C" int bicgstab_solve_batched(int nsys, const stencil7_t* hs_in, const v
     if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end())
       return fail(S7_EINVAL, "bicgstab_solve_batched: a handle appears twice");
   }
-  // the two-reduction variant when the handles were created with it
-  const int merged = hs[0]->variant;
+  // the handles' variant (they must agree); the autotuner may pick the other
+  // one when asked to
+  const int hvar = hs[0]->variant;
   for (int j = 1; j < nsys; ++j)
-    if (hs[j]->variant != merged)
+    if (hs[j]->variant != hvar)
       return fail(S7_EINVAL, "bicgstab_solve_batched: systems created with different variants");
   DeviceScope dev_scope(hs[0]->device);
   const Engine* eng = engine_for(hs[0]->storage);
   const s7_dtype xt = xtype(hs[0]);
-  // the pipelined step sweeps when every system qualifies
-  int pipe = 1;
-  for (int j = 0; j < nsys; ++j) pipe &= eng->batch_pipe_ok(hs[j]);
-  const int bvec = pipe ? eng->vec_wide : eng->vec;
+  // the pipelined step sweeps are possible when every system qualifies
+  int pipe_ok = 1;
+  for (int j = 0; j < nsys; ++j) pipe_ok &= eng->batch_pipe_ok(hs[j]);
+  const bool explicit_policy = opts.threads > 0 || opts.zchunk > 0 || opts.no_autotune;
+  const bool try_variant = opts.choose_variant && !explicit_policy;
   cudaStream_t us = (cudaStream_t)stream;
   cudaStream_t st = nullptr;
   cudaEvent_t ev = nullptr;
   CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
   int rc = S7_OK;
-  cudaGraphExec_t gexec = nullptr;
   BatchBuffers bb;
   std::vector<const void*> bdev(nsys);
   std::vector<size_t> hist_off(nsys), parts_off(nsys);
   size_t hist_total = 0, parts_total = 0;
   long long cells = 0;
-  int sweep_blocks = 0, upd_blocks = 0, threads = 128;
   size_t smem[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // by launch kind
-  BatchPolicy pol{128, 16};
-  const int ce = opts.check_every > 0 ? opts.check_every : 16;
-  std::vector<int> sys_nb, sys_ub;   // sweep and update blocks per system
-  int pgrid = 0;                      // blocks of the persistent launch (0: not used)
-  void* d_queue = nullptr;
-  void* d_qstate = nullptr;
-  int* d_order = nullptr;
+  BatchPolicy pol{128, 16, opts.schedule >= 0 ? 1 : -1, pipe_ok, hvar};
+  BatchRun run;
+  memset(&run, 0, sizeof run);
   cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
   if (e != cudaSuccess) { rc = cuda_fail(e, "event"); goto out; }
   if ((rc = join(us, st, ev))) goto out;
@@ -1455,34 +1638,35 @@ extern "C" int bicgstab_solve_batched(int nsys, const stencil7_t* hs_in, const v
   for (int j = 0; j < nsys; ++j) {
     Handle* h = hs[j];
     if ((rc = ensure_ws(h, 0))) goto out;
+    // the second r buffer of the two-reduction variant, for the trials too
+    if ((hvar || try_variant) && !h->ws.r2 &&
+        (rc = dmalloc(h, &h->ws.r2, (size_t)h->n * eng->t_size)))
+      goto out;
     if ((rc = stage_in(h, b[j], dt, xt, h->ws.b, &bdev[j], st))) goto out;
-    const void* xin = nullptr;
-    if ((rc = stage_in(h, x[j], dt, xt, h->ws.x, &xin, st))) goto out;
-    if (xin != h->ws.x) {
-      e = cudaMemcpyAsync(h->ws.x, xin, (size_t)h->n * eng->x_size, cudaMemcpyDeviceToDevice, st);
-      if (e != cudaSuccess) { rc = cuda_fail(e, "x0 copy"); goto out; }
-    }
     hist_off[j] = hist_total;
     hist_total += (size_t)maxit[j] + 1;
     cells += h->n;
   }
+  if ((rc = stage_x0(nsys, hs.data(), x, dt, xt, eng, st))) goto out;
   // batch-owned scalars, histories, partial sums, descriptors
   {
     // partials: up to 3 per block, for the largest block count of any policy tried
     std::vector<BatchPolicy> pols;
     for (int t : {64, 128, 256})
-      for (int z : {16, 32, 64}) pols.push_back(BatchPolicy{t, z});
+      for (int z : {16, 32, 64}) pols.push_back(BatchPolicy{t, z, 0, 0, 0});
     pols.push_back(BatchPolicy{opts.threads > 0 ? std::max(64, std::min(256, opts.threads)) : 128,
-                               opts.zchunk > 0 ? opts.zchunk : 16});
+                               opts.zchunk > 0 ? opts.zchunk : 16, 0, 0, 0});
     for (int j = 0; j < nsys; ++j) {
       Handle* h = hs[j];
-      const long long runs = (h->nx + bvec - 1) / bvec;
       long long cap = 4096;  // update blocks
-      for (const BatchPolicy& q : pols) {
-        const Tile t = batch_tile(h, bvec, q);
-        const long long nb = ((runs + t.bx - 1) / t.bx) * ((h->ny + t.by - 1) / t.by) *
-                             ((h->nz + t.zchunk - 1) / t.zchunk);
-        cap = std::max(cap, nb);
+      for (int bvec : {eng->vec, eng->vec_wide}) {
+        const long long runs = (h->nx + bvec - 1) / bvec;
+        for (const BatchPolicy& q : pols) {
+          const Tile t = batch_tile(h, bvec, q);
+          const long long nb = ((runs + t.bx - 1) / t.bx) * ((h->ny + t.by - 1) / t.by) *
+                               ((h->nz + t.zchunk - 1) / t.zchunk);
+          cap = std::max(cap, nb);
+        }
       }
       parts_off[j] = parts_total;
       // up to three sums per block (the two-reduction variant's passes)
@@ -1502,13 +1686,29 @@ extern "C" int bicgstab_solve_batched(int nsys, const stencil7_t* hs_in, const v
     if ((e = dev_alloc(dev, &p, (size_t)nsys * eng->desc_size, st)) != cudaSuccess) { rc = cuda_fail(e, "batch descriptors"); goto out; }
     bb.desc = p;
   }
-  // policy: explicit, cached, or autotuned with a batched SpMV probe
+  run.nsys = nsys;
+  run.hs = hs.data();
+  run.eng = eng;
+  run.bb = &bb;
+  run.tol = tol;
+  run.maxit = maxit;
+  run.smem = smem;
+  run.ce = opts.check_every > 0 ? opts.check_every : 16;
+  run.budget = opts.wait_cycles > 0 ? opts.wait_cycles : (1LL << 31);
+  run.st = st;
+  // policy: explicit, cached, or autotuned.  The autotuner first times the
+  // block shapes with a batched SpMV probe over the batch's own operators,
+  // then the fusion schedules with a few steps of the solve itself: the
+  // persistent launch or one launch per step kernel, the pipelined step
+  // sweeps (wide vectors) or the register sweeps, and on request the
+  // two-reduction variant.
   {
     int l2 = 0;
     while ((1LL << l2) < cells) ++l2;
-    const auto key = std::make_tuple((int)hs[0]->storage, nsys, l2, pipe);
+    const auto key = std::make_tuple((int)hs[0]->storage, nsys, l2, pipe_ok, hvar,
+                                     (int)try_variant, opts.schedule);
     bool have = false;
-    if (opts.threads > 0 || opts.zchunk > 0 || opts.no_autotune) {
+    if (explicit_policy) {
       pol.threads = opts.threads > 0 ? std::max(64, std::min(256, opts.threads)) : 128;
       pol.zchunk = opts.zchunk > 0 ? opts.zchunk : 16;
       have = true;
@@ -1524,21 +1724,23 @@ extern "C" int bicgstab_solve_batched(int nsys, const stencil7_t* hs_in, const v
       const int cand_t[3] = {64, 128, 256};
       const int cand_z[3] = {16, 32, 64};
       float best = 1e30f;
-      cudaEvent_t e0, e1;
+      cudaEvent_t e0 = nullptr, e1 = nullptr;
       cudaEventCreate(&e0);
       cudaEventCreate(&e1);
       for (int ti = 0; ti < 3; ++ti)
         for (int zi = 0; zi < 3; ++zi) {
-          BatchPolicy c{cand_t[ti], cand_z[zi]};
+          BatchPolicy c = pol;
+          c.threads = cand_t[ti];
+          c.zchunk = cand_z[zi];
           if ((rc = batch_layout(nsys, hs.data(), bdev.data(), eng, c, bb, hist_off, parts_off,
-                                 &sweep_blocks, &upd_blocks, smem, pipe, st)))
+                                 &run.sweep_blocks, smem, c.pipe, st)))
             goto tune_out;
-          if (eng->batched_prepare(*std::max_element(smem, smem + 8), pipe)) { rc = fail(S7_ECUDA, "batched kernel attributes"); goto tune_out; }
+          if (eng->batched_prepare(*std::max_element(smem, smem + 8), c.pipe)) { rc = fail(S7_ECUDA, "batched kernel attributes"); goto tune_out; }
           // warm, then time two probes
-          if ((rc = eng->launch_batched(3, bb.desc, nsys, sweep_blocks, c.threads, smem[3], st, pipe))) goto tune_out;
+          if ((rc = eng->launch_batched(3, bb.desc, nsys, run.sweep_blocks, c.threads, smem[3], st, c.pipe))) goto tune_out;
           cudaEventRecord(e0, st);
           for (int r = 0; r < 2 && rc == S7_OK; ++r)
-            rc = eng->launch_batched(3, bb.desc, nsys, sweep_blocks, c.threads, smem[3], st, pipe);
+            rc = eng->launch_batched(3, bb.desc, nsys, run.sweep_blocks, c.threads, smem[3], st, c.pipe);
           cudaEventRecord(e1, st);
           if (rc) goto tune_out;
           if ((e = cudaEventSynchronize(e1)) != cudaSuccess) { rc = cuda_fail(e, "autotune"); goto tune_out; }
@@ -1549,6 +1751,45 @@ extern "C" int bicgstab_solve_batched(int nsys, const stencil7_t* hs_in, const v
             pol = c;
           }
         }
+      // the fusion schedules, each timed over a few steps of every system
+      {
+        std::vector<BatchPolicy> scheds;
+        for (int pp : {1, 0}) {
+          if (pp && !pipe_ok) continue;
+          for (int mg : {hvar, 1 - hvar}) {
+            if (mg != hvar && !try_variant) continue;
+            for (int sc : {1, -1}) {
+              if (opts.schedule && sc != opts.schedule) continue;
+              BatchPolicy c = pol;
+              c.pipe = pp;
+              c.merged = mg;
+              c.sched = sc;
+              scheds.push_back(c);
+            }
+          }
+        }
+        float sbest = 1e30f;
+        const BatchPolicy tile = pol;
+        for (const BatchPolicy& c : scheds) {
+          if ((rc = batch_layout(nsys, hs.data(), bdev.data(), eng, c, bb, hist_off, parts_off,
+                                 &run.sweep_blocks, smem, c.pipe, st)))
+            goto tune_out;
+          if (eng->batched_prepare(*std::max_element(smem, smem + 8), c.pipe)) { rc = fail(S7_ECUDA, "batched kernel attributes"); goto tune_out; }
+          run.threads = c.threads;
+          run.pipe = c.pipe;
+          run.merged = c.merged;
+          float ms = 0.f;
+          const int trc = batch_run(run, c.sched > 0, kScheduleTrialSteps, &ms);
+          if (trc == S7_EINVAL && c.sched > 0) continue;  // the persistent launch does not fit
+          if (trc) { rc = trc; goto tune_out; }
+          if (ms < sbest) {
+            sbest = ms;
+            pol = c;
+          }
+          if ((rc = stage_x0(nsys, hs.data(), x, dt, xt, eng, st))) goto tune_out;
+        }
+        if (sbest == 1e30f) pol = tile;
+      }
     tune_out:
       cudaEventDestroy(e0);
       cudaEventDestroy(e1);
@@ -1557,130 +1798,28 @@ extern "C" int bicgstab_solve_batched(int nsys, const stencil7_t* hs_in, const v
       g_policy[key] = pol;
     }
   }
-  threads = pol.threads;
+  t_last_policy = pol;
   if ((rc = batch_layout(nsys, hs.data(), bdev.data(), eng, pol, bb, hist_off, parts_off,
-                         &sweep_blocks, &upd_blocks, smem, pipe, st, &sys_nb, &sys_ub)))
+                         &run.sweep_blocks, smem, pol.pipe, st)))
     goto out;
-  if (eng->batched_prepare(*std::max_element(smem, smem + 8), pipe)) { rc = fail(S7_ECUDA, "batched kernel attributes"); goto out; }
-  // scalars: tol, maxit
-  for (int j = 0; j < nsys; ++j) {
-    Scalars& s = bb.h_sc[j];
-    memset(&s, 0, sizeof s);
-    s.tol = tol[j];
-    s.maxit = maxit[j];
-    s.status = S7_ENOTCONV;
-  }
-  if ((e = cudaMemcpyAsync(bb.sc, bb.h_sc, (size_t)nsys * sizeof(Scalars), cudaMemcpyHostToDevice, st)) != cudaSuccess) { rc = cuda_fail(e, "scalars"); goto out; }
-  if ((rc = eng->launch_batched(2, bb.desc, nsys, sweep_blocks, threads, smem[2], st, pipe)) ||
-      (rc = eng->launch_batched(5, bb.desc, nsys, 0, 0, 0, st, pipe)) ||
-      // the two-reduction variant starts with s_0 = A p_0 and (r0, s_0)
-      (merged && (rc = eng->launch_batched(0, bb.desc, nsys, sweep_blocks, threads, smem[0], st,
-                                           pipe)))) {
-    rc = fail(rc, "batched start launch failed: %s", cudaGetErrorString(cudaGetLastError()));
-    goto out;
-  }
-  // the schedule: one persistent launch running every step of every system
-  // from per-system work queues, on as many blocks as fit on the device at
-  // once; or one launch per step kernel replayed from a graph
-  if (opts.schedule >= 0) {
-    const size_t psm = merged ? std::max(smem[6], smem[7]) : std::max(smem[0], smem[1]);
-    int per_sm = 0;
-    if (eng->persistent_occupancy(threads, psm, pipe, merged, &per_sm) == S7_OK && per_sm > 0)
-      pgrid = per_sm * num_sms();
-    if (!pgrid && opts.schedule == 1) {
-      rc = fail(S7_EINVAL, "bicgstab_solve_batched: no block of the persistent launch fits");
-      goto out;
-    }
-  }
-  if (pgrid) {
-    const int dev = hs[0]->device;
-    // blocks look for work in the largest systems first: they set the end
-    std::vector<int> order(nsys);
-    for (int j = 0; j < nsys; ++j) order[j] = j;
-    std::stable_sort(order.begin(), order.end(),
-                     [&](int a, int b) { return hs[a]->n > hs[b]->n; });
-    if ((e = dev_alloc(dev, &d_queue, (size_t)nsys * kQueueBytes, st)) != cudaSuccess ||
-        (e = dev_alloc(dev, &d_qstate, kQueueStateBytes, st)) != cudaSuccess ||
-        (e = dev_alloc(dev, (void**)&d_order, (size_t)nsys * sizeof(int), st)) != cudaSuccess) {
-      rc = cuda_fail(e, "persistent batch queues");
-      goto out;
-    }
-    if ((e = cudaMemsetAsync(d_qstate, 0, kQueueStateBytes, st)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(d_order, order.data(), (size_t)nsys * sizeof(int),
-                             cudaMemcpyHostToDevice, st)) != cudaSuccess ||
-        (e = cudaStreamSynchronize(st)) != cudaSuccess) {
-      rc = cuda_fail(e, "persistent batch queues");
-      goto out;
-    }
-    const long long budget = opts.wait_cycles > 0 ? opts.wait_cycles : (1LL << 31);
-    const size_t psm = merged ? std::max(smem[6], smem[7]) : std::max(smem[0], smem[1]);
-    // captured as a graph of one launch; launched directly where the capture
-    // of a cooperative launch is refused
-    cudaGraph_t g = nullptr;
-    bool captured = false;
-    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
-      const int lrc = eng->launch_persistent(bb.desc, d_order, d_queue, d_qstate, nsys, pgrid,
-                                             threads, psm, budget, st, pipe, merged);
-      e = cudaStreamEndCapture(st, &g);
-      if (lrc == S7_OK && e == cudaSuccess && g &&
-          cudaGraphInstantiate(&gexec, g, 0) == cudaSuccess)
-        captured = true;
-      if (g) cudaGraphDestroy(g);
-      cudaGetLastError();
-    }
-    if (captured) {
-      if ((e = cudaGraphLaunch(gexec, st)) != cudaSuccess) { rc = cuda_fail(e, "persistent graph launch"); goto out; }
-    } else {
-      gexec = nullptr;
-      if ((rc = eng->launch_persistent(bb.desc, d_order, d_queue, d_qstate, nsys, pgrid, threads,
-                                       psm, budget, st, pipe, merged))) {
-        rc = fail(rc, "persistent batched launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+  if (eng->batched_prepare(*std::max_element(smem, smem + 8), pol.pipe)) { rc = fail(S7_ECUDA, "batched kernel attributes"); goto out; }
+  run.threads = pol.threads;
+  run.pipe = pol.pipe;
+  run.merged = pol.merged;
+  {
+    int prc = S7_EINVAL;
+    if (pol.sched > 0) {
+      prc = batch_run(run, 1, 0, nullptr);
+      // schedule 0: one launch per kernel where the persistent launch does not fit
+      if (prc == S7_EINVAL && opts.schedule == 0) {
+        pol.sched = -1;
+        t_last_policy = pol;
+      } else if (prc) {
+        rc = prc;
         goto out;
       }
     }
-    if ((e = cudaMemcpyAsync(bb.h_sc, bb.sc, (size_t)nsys * sizeof(Scalars), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
-        (e = cudaStreamSynchronize(st)) != cudaSuccess) { rc = cuda_fail(e, "persistent batched solve"); goto out; }
-  } else {
-  // capture ce steps
-  {
-    cudaGraph_t g = nullptr;
-    if ((e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) { rc = cuda_fail(e, "capture"); goto out; }
-    for (int k = 0; k < ce && rc == S7_OK; ++k) {
-      if (merged) {
-        // q/y pass, then the x, r updates fused with the next step's p/s pass
-        rc = eng->launch_batched(6, bb.desc, nsys, sweep_blocks, threads, smem[6], st, pipe);
-        if (!rc) rc = eng->launch_batched(7, bb.desc, nsys, sweep_blocks, threads, smem[7], st, pipe);
-        continue;
-      }
-      rc = eng->launch_batched(0, bb.desc, nsys, sweep_blocks, threads, smem[0], st, pipe);
-      if (!rc) rc = eng->launch_batched(1, bb.desc, nsys, sweep_blocks, threads, smem[1], st, pipe);
-      if (!rc) rc = eng->launch_batched(4, bb.desc, nsys, upd_blocks, 256, 0, st, pipe);
-    }
-    e = cudaStreamEndCapture(st, &g);
-    if (rc || e != cudaSuccess) {
-      if (g) cudaGraphDestroy(g);
-      cudaGetLastError();
-      rc = rc ? fail(rc, "batched capture: launch failed") : cuda_fail(e, "cudaStreamEndCapture");
-      goto out;
-    }
-    e = cudaGraphInstantiate(&gexec, g, 0);
-    cudaGraphDestroy(g);
-    if (e != cudaSuccess) { gexec = nullptr; rc = cuda_fail(e, "cudaGraphInstantiate"); goto out; }
-  }
-  {
-    int mx = 0;
-    for (int j = 0; j < nsys; ++j) mx = std::max(mx, maxit[j]);
-    const int max_launch = mx / ce + 3;
-    for (int launches = 0;; ++launches) {
-      if ((e = cudaMemcpyAsync(bb.h_sc, bb.sc, (size_t)nsys * sizeof(Scalars), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
-          (e = cudaStreamSynchronize(st)) != cudaSuccess) { rc = cuda_fail(e, "batched poll"); goto out; }
-      bool all = true;
-      for (int j = 0; j < nsys && all; ++j) all = bb.h_sc[j].done != 0;
-      if (all) break;
-      if (launches >= max_launch) { rc = fail(S7_ECUDA, "batched solve did not terminate"); goto out; }
-      if ((e = cudaGraphLaunch(gexec, st)) != cudaSuccess) { rc = cuda_fail(e, "graph launch"); goto out; }
-    }
-  }
+    if (pol.sched < 0 && (rc = batch_run(run, 0, 0, nullptr))) goto out;
   }
   // results
   {
@@ -1705,12 +1844,8 @@ extern "C" int bicgstab_solve_batched(int nsys, const stencil7_t* hs_in, const v
     else if (any_nc) rc = fail(S7_ENOTCONV, "at least one system did not converge");
   }
 out:
-  if (gexec) cudaGraphExecDestroy(gexec);
   if (st) {
     cudaStreamSynchronize(st);
-    dev_free(d_queue, st);
-    dev_free(d_qstate, st);
-    dev_free(d_order, st);
     if (ev && us != st) {
       cudaEventRecord(ev, st);
       cudaStreamWaitEvent(us, ev, 0);
@@ -1719,4 +1854,16 @@ out:
   if (ev) cudaEventDestroy(ev);
   if (st) cudaStreamDestroy(st);
   return rc;
+}
+
+extern "C" int bicgstab_batched_policy(int* threads, int* zchunk, int* schedule, int* pipelined,
+                                       int* variant) {
+  const BatchPolicy& p = t_last_policy;
+  if (!p.threads) return fail(S7_EINVAL, "bicgstab_batched_policy: no batched solve on this thread");
+  if (threads) *threads = p.threads;
+  if (zchunk) *zchunk = p.zchunk;
+  if (schedule) *schedule = p.sched;
+  if (pipelined) *pipelined = p.pipe;
+  if (variant) *variant = p.merged;
+  return S7_OK;
 }

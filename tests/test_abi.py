@@ -7,6 +7,7 @@ import os
 import re
 import subprocess
 
+import numpy as np
 import pytest
 
 from tests.conftest import ROOT
@@ -86,3 +87,28 @@ def test_product_path_has_no_oracle_dependency():
         if path.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
             text = open(path).read()
             assert "import oracle" not in text and "from oracle" not in text, path
+
+
+def test_binding_rejects_mismatched_vectors_without_gpu():
+    """The entry points take one element type for all vectors of a call and
+    no sizes: the binding refuses vectors of mixed types or of the wrong
+    length before anything reaches the library."""
+    import paper_2010_03660_gb300 as s7
+    op = s7.Operator(0, 4, 3, 2, s7.S7_F32)
+    b32 = np.zeros(24, np.float32)
+    x64 = np.zeros(24)
+    short = np.zeros(23, np.float32)
+    calls = [lambda: s7.bicgstab_solve(op, b32, x64),
+             lambda: s7.bicgstab_solve(op, b32, short),
+             lambda: s7.stencil7_residual(op, b32, x64),
+             lambda: s7.stencil7_residual_noalloc(op, b32, b32, x64),
+             lambda: s7.stencil7_apply(op, short),
+             lambda: s7.stencil7_apply(op, b32, x64),
+             lambda: s7.bicgstab_solve_refined(op, b32, b32.copy()),
+             lambda: s7.bicgstab_solve_batched([op], [b32], [x64]),
+             lambda: s7.bicgstab_solve_batched([op, op], [b32], [b32]),
+             lambda: s7.s7_server_submit(None, 4, 3, 2, {k: b32 for k in ("diag",) + s7.DIRS},
+                                         b32, x64, 1e-6)]
+    for call in calls:
+        with pytest.raises(ValueError):
+            call()

@@ -338,3 +338,71 @@ def test_persistent_wait_bound_gives_timeout(s7):
     finally:
         for op in ops:
             op.close()
+
+
+def test_autotuner_picks_fusion_schedule(s7):
+    """Without a fixed block shape the autotuner also times the fusion
+    schedules (the persistent launch or one launch per step kernel, the
+    pipelined step sweeps or the register sweeps) over a few steps of the solve
+    from x0, and puts x0 back before solving: the solve is bit for bit an
+    explicit-policy solve with the block shape and schedule it reports (in
+    float32 the pipelined and register sweeps give the same bits), and every
+    system, started from a nonzero x0, meets the oracle bars."""
+    probs = make([(16, 12, 20), (40, 31, 24), (64, 20, 12), (8, 8, 64), (32, 32, 32)], 1000)
+    ops = [s7.stencil7_create(p.nx, p.ny, p.nz, gu.coef_on_device(p), storage="f32")
+           for p in probs]
+    x0 = [(0.3 * np.cos(0.01 * np.arange(p.nx * p.ny * p.nz))).astype(p.b.dtype) for p in probs]
+    tol = 1e-6
+    try:
+        def solve(**kw):
+            return s7.bicgstab_solve_batched(ops, [gu.to_dev(p.b) for p in probs],
+                                             xs=[gu.to_dev(v) for v in x0], tol=tol, maxit=1000,
+                                             **kw)
+        auto = solve()
+        pol = auto.policy
+        assert pol["schedule"] in (1, -1) and pol["pipelined"] in (0, 1) and pol["variant"] == 0
+        assert pol["threads"] in (64, 128, 256) and pol["zchunk"] in (16, 32, 64)
+        again = solve()
+        assert again.policy == pol and again.iters == auto.iters
+        fixed = solve(threads=pol["threads"], zchunk=pol["zchunk"], schedule=pol["schedule"])
+        assert fixed.iters == auto.iters
+        for j, p in enumerate(probs):
+            xa = auto.x[j].cpu().numpy()
+            assert np.array_equal(xa, fixed.x[j].cpu().numpy())
+            assert np.array_equal(xa, again.x[j].cpu().numpy())
+            assert auto.status[j] == 0
+            orc = ob.bicgstab(p.nx, p.ny, p.nz, p.coef, p.b, x0=x0[j].astype(np.float64),
+                              tol=tol, maxit=1000, storage="f32")
+            assert rel(xa, orc.x) <= 100 * tol
+            assert scaled_true_residual(p, xa) <= 2 * tol
+    finally:
+        for op in ops:
+            op.close()
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+def test_autotuner_may_choose_the_variant(s7, storage):
+    """With choose_variant the autotuner times both variants of the step (the
+    handles were created with Algorithm 1) and runs the faster; either way
+    each system meets the bars of the variant it ran."""
+    shapes = [(16, 16, 16), (24, 20, 12), (32, 9, 30), (8, 8, 64), (48, 40, 24)]
+    probs = make(shapes, 1100)
+    tol = 1e-6 if storage == "f32" else 1e-2
+    ops = [s7.stencil7_create(p.nx, p.ny, p.nz, gu.coef_on_device(p), storage=storage)
+           for p in probs]
+    try:
+        res = s7.bicgstab_solve_batched(ops, [gu.to_dev(p.b) for p in probs], tol=tol,
+                                        maxit=1000, choose_variant=True)
+        pol = res.policy
+        assert pol["variant"] in (0, 1) and pol["schedule"] in (1, -1)
+        for j, p in enumerate(probs):
+            assert res.status[j] == 0 and res.resid[j] <= tol
+            x = res.x[j].cpu().numpy().astype(np.float64)
+            assert scaled_true_residual(p, x, storage) <= (2 * tol if storage == "f32" else 3e-2)
+            if storage == "f32":
+                orc = (ob.bicgstab_merged if pol["variant"] else ob.bicgstab)(
+                    p.nx, p.ny, p.nz, p.coef, p.b, tol=tol, maxit=1000, storage="f32")
+                assert rel(x, orc.x) <= 100 * tol
+    finally:
+        for op in ops:
+            op.close()
