@@ -171,8 +171,10 @@ def measured_peaks():
 
 # the sources that define the profiled step kernels (their device code and
 # launch configuration); host-side drivers and tile defaults are not included
+# the sources of the kernels profiles/traffic.json holds (the single-system step
+# sweeps, the update and the true residual; the batched kernels are not among them)
 KERNEL_SOURCES = ("s7_common.cuh", "s7_sweep.cuh", "s7_sweep9.cuh", "s7_step.cuh",
-                  "s7_engine.cuh", "s7_batch.cuh", "s7_resid.cuh")
+                  "s7_engine.cuh", "s7_resid.cuh")
 
 
 def kernel_source_hash():

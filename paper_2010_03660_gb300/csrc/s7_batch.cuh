@@ -280,9 +280,15 @@ __global__ void k_queue_init(const SysDesc<T, X>* __restrict__ sys, int nsys, Sy
 // sweep of float32/float64 storage in its register form, as in the
 // launch-per-kernel batches).  MERGED: the two-reduction variant.  VU: the
 // update's cells per thread.  order: the systems, largest first.
+// Registers: the blocks hide load latency by their number (the register
+// sweeps keep their loads in registers), so Algorithm 1's form is bounded to
+// 85 registers (three 256-thread blocks per SM: 5-6 blocks of 128 threads,
+// a few spilled words), measured 4.66e10 against 4.01e10 cell-iters/s at 128
+// registers on 512 mixed systems; the two-reduction form spills too much
+// below 128 registers (3.36e10 at 85 against 3.95-4.11e10).
 template <class T, class X, class DT, class A, int VEC, int VU, int STAGES, bool PIPE,
           bool MERGED, bool PIPE_Q>
-__global__ void __launch_bounds__(256, 2)
+__global__ void __launch_bounds__(256, MERGED ? 2 : 3)
     k_batched_persistent(const SysDesc<T, X>* __restrict__ sys, const int* __restrict__ order,
                          int nsys, SysQueue* q, QueueState* qs, long long budget) {
   extern __shared__ __align__(16) unsigned char s7_smem[];
