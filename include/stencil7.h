@@ -246,9 +246,11 @@ int stencil7_residual(stencil7_t h, const void* b, const void* x, void* r,
  *             (S7_F64 or S7_F32); host buffers are rejected with S7_EINVAL.
  *   Sizes whose sweep needs more than S7_NOALLOC_MAX_BLOCKS blocks are
  *   rejected with S7_EINVAL (a larger opts.zchunk lowers the count).
- * Set-up: the first call on each device looks up the device address of the
- * scratch array (once per device, under a lock); make that first call
- * before any stream capture.  The address is kept for the rest of the
+ * Synchronous: the call waits on the host for its norms, so it may never be
+ * made on a stream that is being captured into a graph (S7_EINVAL, the
+ * capture left untouched).  The first call on each device looks up the
+ * device address of the scratch array (once per device, under a lock).  The
+ * address is kept for the rest of the
  * process: do not use the library across a reset of the device or of its
  * primary context (cudaDeviceReset), after which it would be stale.  All calls share the one array, which keeps
  * the last call's contents; each call clears the part that must start at

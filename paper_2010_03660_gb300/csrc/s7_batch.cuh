@@ -245,8 +245,10 @@ __global__ void __launch_bounds__(256) k_update_batched(const SysDesc<T, X>* __r
 // with them the phase's grid combine) opens the next phase by exchanging the
 // word, or marks the system finished (a word whose tile count no claim can
 // reach).  The first warp of a block looks for an open tile 32 systems at
-// a time, the largest systems first (they set the end of the batch), and
-// claims one tile at a time.  A block that finds no open tile waits at most
+// a time, starting from the system of its last claim (so a block stays with
+// a system while it has open tiles instead of rescanning the batch from the
+// top; the first scan starts at the largest systems, which set the end of
+// the batch), and claims one tile at a time.  A block that finds no open tile waits at most
 // `budget` SM clock cycles for one; when a wait runs out it aborts the
 // launch: every unfinished system stops with status 5 (S7_ETIMEOUT) and
 // every block leaves after its current tile, so nothing can hang the device.
@@ -299,6 +301,7 @@ __global__ void __launch_bounds__(256, MERGED ? 2 : 3)
   auto tiles_of = [&](int j, unsigned int ph) -> unsigned int {
     return (unsigned int)((!MERGED && ph == 2) ? sys[j].punblocks : sys[j].nblocks);
   };
+  int pos = 0;   // (first warp) where in `order` the next scan starts: the last claim's system
   for (;;) {
     // ---- the first warp claims a tile, or finds that none is left
     if (threadIdx.x < 32) {
@@ -312,10 +315,11 @@ __global__ void __launch_bounds__(256, MERGED ? 2 : 3)
           break;
         }
         for (int base = 0; base < nsys && got == 0; base += 32) {
-          const int idx = base + lane;
+          const int k = base + lane;
+          const int idx = pos + k < nsys ? pos + k : pos + k - nsys;
           int j = -1;
           bool open = false;
-          if (idx < nsys) {
+          if (k < nsys) {
             j = order[idx];
             const unsigned long long w = *((volatile unsigned long long*)&q[j].word);
             open = (unsigned int)(w & 0xffffffffull) < tiles_of(j, (unsigned int)((w >> 32) % NPH));
@@ -337,6 +341,7 @@ __global__ void __launch_bounds__(256, MERGED ? 2 : 3)
             }
             if (__shfl_sync(0xffffffffu, ok, src)) {
               got = 1;
+              pos = __shfl_sync(0xffffffffu, idx, src);
               break;
             }
             mask &= mask - 1u;

@@ -76,6 +76,17 @@ extern "C" int stencil7_residual_noalloc(stencil7_t h, const void* b, const void
   if (!h || !b || !x) return set_error(S7_EINVAL, "stencil7_residual_noalloc: NULL argument");
   if (dt != S7_F64 && dt != S7_F32)
     return set_error(S7_EINVAL, "stencil7_residual_noalloc: dt must be S7_F64 or S7_F32");
+  cudaStream_t st = (cudaStream_t)stream;
+  // the call waits for its norms on the host: a capturing stream cannot
+  // run it (the capture would be invalidated), so refuse before touching it
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) {
+    cudaGetLastError();
+    return set_error(S7_EINVAL, "stencil7_residual_noalloc: bad stream");
+  }
+  if (cap != cudaStreamCaptureStatusNone)
+    return set_error(S7_EINVAL,
+                     "stencil7_residual_noalloc: synchronous call on a capturing stream");
   DeviceScope dev_scope(h->device);
   if (!device_memory(b) || !device_memory(x) || (r && !device_memory(r)))
     return set_error(S7_EINVAL,
@@ -94,7 +105,6 @@ extern "C" int stencil7_residual_noalloc(stencil7_t h, const void* b, const void
   void* base = nullptr;
   int rc = scratch_address(h->device, &base);
   if (rc) return rc;
-  cudaStream_t st = (cudaStream_t)stream;
   Scalars* sc = (Scalars*)base;
   double* parts = (double*)((char*)base + kScalarsBytes);
   // the arrival counters (and totals) must start at zero; the partials are

@@ -99,3 +99,30 @@ def test_noalloc_rejects_host_buffers_and_oversize(s7):
         with pytest.raises(s7.S7Error) as e:
             s7.stencil7_residual_noalloc(op, b, b)
         assert e.value.code == s7.EINVAL and "blocks" in str(e.value)
+
+
+def test_noalloc_refuses_a_capturing_stream(s7):
+    """The call waits on the host for its norms, so on a stream that is being
+    captured it returns S7_EINVAL before any other CUDA call on that stream,
+    and the capture stays valid."""
+    import torch
+    nx, ny, nz = 16, 8, 8
+    p = synth.varcoef(nx, ny, nz, seed=54)
+    with s7.stencil7_create(nx, ny, nz, gu.coef_on_device(p), storage="f32") as op:
+        b = gu.to_dev(p.b)
+        x = gu.to_dev(p.b)
+        s7.stencil7_residual_noalloc(op, b, x)          # set-up outside any capture
+        torch.cuda.synchronize()
+        y = torch.zeros(4, device=b.device)
+        g = torch.cuda.CUDAGraph()
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            with torch.cuda.graph(g, stream=s):
+                y.add_(1)
+                with pytest.raises(s7.S7Error) as e:
+                    s7.stencil7_residual_noalloc(op, b, x)
+                y.add_(1)
+        assert e.value.code == s7.EINVAL and "capturing" in str(e.value)
+        g.replay()
+        torch.cuda.synchronize()
+        assert float(y[0]) == 2.0
