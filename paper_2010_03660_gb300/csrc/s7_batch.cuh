@@ -94,8 +94,8 @@ __device__ __forceinline__ void batched_sweep(const SysDesc<T, X>& d, int bid, u
     epi.sbuf[1] = d.s[1];
     epi.rh = d.rh;
     epi.parts = d.parts;
-    if (d.vl) sweep_body<T, A, VEC, true>(g, cf, src, epi, sc, bid, d.nblocks, sm, red);
-    else sweep_body<T, A, VEC, false>(g, cf, src, epi, sc, bid, d.nblocks, sm, red);
+    if (d.vl) sweep_body<T, A, VEC, true, true>(g, cf, src, epi, sc, bid, d.nblocks, sm, red);
+    else sweep_body<T, A, VEC, false, true>(g, cf, src, epi, sc, bid, d.nblocks, sm, red);
   } else if (KIND == 1) {
     SrcQ<T, A> src;
     src.r = d.r;
@@ -104,8 +104,8 @@ __device__ __forceinline__ void batched_sweep(const SysDesc<T, X>& d, int bid, u
     EpiY<T, A> epi;
     epi.y_out = d.y;
     epi.parts = d.parts;
-    if (d.vl) sweep_body<T, A, VEC, true>(g, cf, src, epi, sc, bid, d.nblocks, sm, red);
-    else sweep_body<T, A, VEC, false>(g, cf, src, epi, sc, bid, d.nblocks, sm, red);
+    if (d.vl) sweep_body<T, A, VEC, true, true>(g, cf, src, epi, sc, bid, d.nblocks, sm, red);
+    else sweep_body<T, A, VEC, false, true>(g, cf, src, epi, sc, bid, d.nblocks, sm, red);
   } else if (KIND == 2) {
     SrcPlain<X, A> src{d.x};
     EpiResid<X, T, DT, A> epi;
@@ -119,13 +119,13 @@ __device__ __forceinline__ void batched_sweep(const SysDesc<T, X>& d, int bid, u
     epi.parts = d.parts;
     epi.counter = CNT_INIT;
     epi.mode = 0;
-    if (d.vl) sweep_body<T, A, VEC, true>(g, cf, src, epi, sc, bid, d.nblocks, sm, red);
-    else sweep_body<T, A, VEC, false>(g, cf, src, epi, sc, bid, d.nblocks, sm, red);
+    if (d.vl) sweep_body<T, A, VEC, true, true>(g, cf, src, epi, sc, bid, d.nblocks, sm, red);
+    else sweep_body<T, A, VEC, false, true>(g, cf, src, epi, sc, bid, d.nblocks, sm, red);
   } else if (KIND == 3) {
     SrcPlain<T, A> src{d.r};
     EpiStore<T, A> epi{d.y};
-    if (d.vl) sweep_body<T, A, VEC, true>(g, cf, src, epi, nullptr, bid, d.nblocks, sm, red);
-    else sweep_body<T, A, VEC, false>(g, cf, src, epi, nullptr, bid, d.nblocks, sm, red);
+    if (d.vl) sweep_body<T, A, VEC, true, true>(g, cf, src, epi, nullptr, bid, d.nblocks, sm, red);
+    else sweep_body<T, A, VEC, false, true>(g, cf, src, epi, nullptr, bid, d.nblocks, sm, red);
   } else if (KIND == 4) {
     SrcQ2<T, A> src;
     src.rbuf[0] = d.r;
@@ -136,8 +136,8 @@ __device__ __forceinline__ void batched_sweep(const SysDesc<T, X>& d, int bid, u
     epi.y_out = d.y;
     epi.rh = d.rh;
     epi.parts = d.parts;
-    if (d.vl) sweep_body<T, A, VEC, true>(g, cf, src, epi, sc, bid, d.nblocks, sm, red);
-    else sweep_body<T, A, VEC, false>(g, cf, src, epi, sc, bid, d.nblocks, sm, red);
+    if (d.vl) sweep_body<T, A, VEC, true, true>(g, cf, src, epi, sc, bid, d.nblocks, sm, red);
+    else sweep_body<T, A, VEC, false, true>(g, cf, src, epi, sc, bid, d.nblocks, sm, red);
   } else {
     MergedPass<T, X, A> m;
     m.rbuf[0] = d.r;
@@ -151,8 +151,8 @@ __device__ __forceinline__ void batched_sweep(const SysDesc<T, X>& d, int bid, u
     m.x = d.x;
     m.parts = d.parts;
     m.hist = d.hist;
-    if (d.vl) sweep_body<T, A, VEC, true>(g, cf, m, m, sc, bid, d.nblocks, sm, red);
-    else sweep_body<T, A, VEC, false>(g, cf, m, m, sc, bid, d.nblocks, sm, red);
+    if (d.vl) sweep_body<T, A, VEC, true, true>(g, cf, m, m, sc, bid, d.nblocks, sm, red);
+    else sweep_body<T, A, VEC, false, true>(g, cf, m, m, sc, bid, d.nblocks, sm, red);
   }
 }
 
